@@ -1,0 +1,885 @@
+/*
+ * Plain FP64 CPU oracle for the sparse hot path: SpMV in every storage
+ * format, the format conversions, conjugate gradients (plain, mixed-precision
+ * with iterative refinement, batched), dense Cholesky, compensated dot
+ * products and the matrix statistics of the format selector.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may link or call
+ * this file; only the tests, the package's smoke check and the benchmark's
+ * CPU-baseline leg use it.  It shares no code with the CUDA library.
+ *
+ * Every routine follows the plain definition of what it computes, with
+ * loops in the order of that definition and no blocking, fusion or
+ * reordering.  Floating-point multiply and add are separate operations:
+ * the file is compiled with -ffp-contract=off so that no multiply-add is
+ * fused and results are identical on every host.
+ *
+ * Sources: the paper (Cojean, Tsai, Anzt, "Ginkgo - A Math Library designed
+ * for Platform Portability", Sec. 6.1 for SpMV and its COO/CSR byte bounds,
+ * Sec. 6.2 for Krylov solvers built on SpMV); the formats it refers to but
+ * does not define follow their standard definitions: ELL and hybrid ELL+COO
+ * (Bell and Garland, SC'09), SELL-P (Anzt, Tomov and Dongarra, 2014);
+ * CG is the method of Hestenes and Stiefel (1952); Dot2 is Algorithm 5.3 of
+ * Ogita, Rump and Oishi, "Accurate sum and dot product" (SISC 2005).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_OK 0
+#define ORC_NOT_CONVERGED 6
+#define ORC_BREAKDOWN 7
+#define ORC_INVALID 1
+
+/* ------------------------------------------------------------------ SpMV */
+
+/* y_i = alpha * sum_k val_k x_{col_k} + beta * y_i over the stored entries
+ * k of row i in ascending position (= ascending column) order.  beta == 0
+ * means y is not read (BLAS convention), so NaN in y does not propagate.
+ * Sec. 6.1: the product y = A x of a CSR matrix. */
+void orc_spmv_csr(int64_t n, const int32_t *row_ptr, const int32_t *col,
+                  const double *val, const double *x, double alpha, double beta,
+                  double *y)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        double s = 0.0;
+        for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
+            double p = val[k] * x[col[k]];
+            s = s + p;
+        }
+        double out = alpha * s;
+        if (beta != 0.0) {
+            double t = beta * y[i];
+            out = out + t;
+        }
+        y[i] = out;
+    }
+}
+
+/* Error-free transformations (Ogita-Rump-Oishi 2005, Algorithms 3.1, 3.3):
+ * TwoSum gives s + e = a + b exactly; TwoProduct gives p + e = a * b
+ * exactly, with the error term taken from the correctly rounded C99 fma(). */
+static void two_sum(double a, double b, double *s, double *e)
+{
+    double x = a + b;
+    double z = x - a;
+    double t1 = a - (x - z);
+    double t2 = b - z;
+    *s = x;
+    *e = t1 + t2;
+}
+
+static void two_prod(double a, double b, double *p, double *e)
+{
+    double x = a * b;
+    *p = x;
+    *e = fma(a, b, -x);
+}
+
+/* Near-exact reference of orc_spmv_csr with Dot2 (compensated dot product,
+ * result as accurate as if computed in twice the working precision), plus
+ * the magnitude mag_i = |alpha| sum_k |val_k x_{col_k}| + |beta| |y_i| that
+ * scales the per-entry tolerance.  y_in may be NULL when beta == 0. */
+void orc_spmv_csr_dot2(int64_t n, const int32_t *row_ptr, const int32_t *col,
+                       const double *val, const double *x, double alpha, double beta,
+                       const double *y_in, double *y_out, double *mag)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        double s = 0.0, c = 0.0, m = 0.0;
+        for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
+            double p, e1, e2;
+            two_prod(val[k], x[col[k]], &p, &e1);
+            two_sum(s, p, &s, &e2);
+            c = c + (e1 + e2);
+            m = m + fabs(val[k] * x[col[k]]);
+        }
+        /* alpha * (s + c) and beta * y, again compensated */
+        double r = 0.0, rc = 0.0, p, e1, e2;
+        two_prod(alpha, s, &p, &e1);
+        two_sum(r, p, &r, &e2);
+        rc = rc + e1 + e2 + alpha * c;
+        double mm = fabs(alpha) * m;
+        if (beta != 0.0) {
+            two_prod(beta, y_in[i], &p, &e1);
+            two_sum(r, p, &r, &e2);
+            rc = rc + e1 + e2;
+            mm = mm + fabs(beta) * fabs(y_in[i]);
+        }
+        y_out[i] = r + rc;
+        if (mag)
+            mag[i] = mm;
+    }
+}
+
+/* COO: entries (row_k, col_k, val_k) in (row, col) order; each row's sum
+ * is formed over its entries in that order.  Sec. 6.1 (COO format). */
+void orc_spmv_coo(int64_t n, int64_t nnz, const int32_t *row, const int32_t *col,
+                  const double *val, const double *x, double alpha, double beta,
+                  double *y)
+{
+    double *s = (double *)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+    for (int64_t k = 0; k < nnz; ++k) {
+        double p = val[k] * x[col[k]];
+        s[row[k]] = s[row[k]] + p;
+    }
+    for (int64_t i = 0; i < n; ++i) {
+        double out = alpha * s[i];
+        if (beta != 0.0) {
+            double t = beta * y[i];
+            out = out + t;
+        }
+        y[i] = out;
+    }
+    free(s);
+}
+
+/* ELL: K slots per row, column-major with leading dimension n_pad:
+ * slot (i, k) is at k * n_pad + i; a padding slot has col == -1 and is
+ * skipped.  (Bell and Garland 2009.) */
+void orc_spmv_ell(int64_t n, int64_t n_pad, int64_t K, const int32_t *col,
+                  const double *val, const double *x, double alpha, double beta,
+                  double *y)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        double s = 0.0;
+        for (int64_t k = 0; k < K; ++k) {
+            int32_t c = col[k * n_pad + i];
+            if (c < 0)
+                continue;
+            double p = val[k * n_pad + i] * x[c];
+            s = s + p;
+        }
+        double out = alpha * s;
+        if (beta != 0.0) {
+            double t = beta * y[i];
+            out = out + t;
+        }
+        y[i] = out;
+    }
+}
+
+/* SELL-P: rows in slices of S; slice s has width slice_len[s] and starts at
+ * column offset slice_set[s] (in units of S-slot columns); row r = s*S + l,
+ * slot k of the row is at (slice_set[s] + k) * S + l.  Padding col == -1.
+ * (Anzt, Tomov, Dongarra 2014.) */
+void orc_spmv_sellp(int64_t n, int64_t S, const int32_t *slice_len,
+                    const int32_t *slice_set, const int32_t *col, const double *val,
+                    const double *x, double alpha, double beta, double *y)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t s_id = i / S, l = i % S;
+        double s = 0.0;
+        for (int64_t k = 0; k < slice_len[s_id]; ++k) {
+            int64_t slot = ((int64_t)slice_set[s_id] + k) * S + l;
+            int32_t c = col[slot];
+            if (c < 0)
+                continue;
+            double p = val[slot] * x[c];
+            s = s + p;
+        }
+        double out = alpha * s;
+        if (beta != 0.0) {
+            double t = beta * y[i];
+            out = out + t;
+        }
+        y[i] = out;
+    }
+}
+
+/* Hybrid ELL + COO: row i's sum is its ELL slots (in slot order) followed
+ * by its COO entries (in order), i.e. its entries in column order. */
+void orc_spmv_hybrid(int64_t n, int64_t n_pad, int64_t K, const int32_t *ell_col,
+                     const double *ell_val, int64_t coo_nnz, const int32_t *coo_row,
+                     const int32_t *coo_col, const double *coo_val, const double *x,
+                     double alpha, double beta, double *y)
+{
+    double *s = (double *)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t k = 0; k < K; ++k) {
+            int32_t c = ell_col[k * n_pad + i];
+            if (c < 0)
+                continue;
+            double p = ell_val[k * n_pad + i] * x[c];
+            s[i] = s[i] + p;
+        }
+    for (int64_t k = 0; k < coo_nnz; ++k) {
+        double p = coo_val[k] * x[coo_col[k]];
+        s[coo_row[k]] = s[coo_row[k]] + p;
+    }
+    for (int64_t i = 0; i < n; ++i) {
+        double out = alpha * s[i];
+        if (beta != 0.0) {
+            double t = beta * y[i];
+            out = out + t;
+        }
+        y[i] = out;
+    }
+    free(s);
+}
+
+/* ----------------------------------------------------------- conversions */
+
+/* CSR -> COO: row index of every entry, entries in CSR order. */
+void orc_csr_to_coo(int64_t n, const int32_t *row_ptr, const int32_t *col,
+                    const double *val, int32_t *row_out, int32_t *col_out,
+                    double *val_out)
+{
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
+            row_out[k] = (int32_t)i;
+            col_out[k] = col[k];
+            val_out[k] = val[k];
+        }
+}
+
+/* COO (sorted by row) -> CSR: row_ptr by counting entries per row. */
+void orc_coo_to_csr(int64_t n, int64_t nnz, const int32_t *row, const int32_t *col,
+                    const double *val, int32_t *row_ptr, int32_t *col_out,
+                    double *val_out)
+{
+    for (int64_t i = 0; i <= n; ++i)
+        row_ptr[i] = 0;
+    for (int64_t k = 0; k < nnz; ++k)
+        row_ptr[row[k] + 1] += 1;
+    for (int64_t i = 0; i < n; ++i)
+        row_ptr[i + 1] += row_ptr[i];
+    for (int64_t k = 0; k < nnz; ++k) {
+        col_out[k] = col[k];
+        val_out[k] = val[k];
+    }
+}
+
+/* Maximum row length. */
+int64_t orc_max_row_len(int64_t n, const int32_t *row_ptr)
+{
+    int64_t K = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t L = row_ptr[i + 1] - row_ptr[i];
+        if (L > K)
+            K = L;
+    }
+    return K;
+}
+
+/* n rounded up to a multiple of 32: the ELL leading dimension. */
+int64_t orc_ell_n_pad(int64_t n) { return (n + 31) / 32 * 32; }
+
+/* CSR -> ELL of width K (K >= max row length): row i's entries fill its
+ * first slots in column order, the rest are padding (col -1, val +0.0). */
+void orc_csr_to_ell(int64_t n, int64_t n_pad, int64_t K, const int32_t *row_ptr,
+                    const int32_t *col, const double *val, int32_t *ell_col,
+                    double *ell_val)
+{
+    for (int64_t k = 0; k < K; ++k)
+        for (int64_t i = 0; i < n_pad; ++i) {
+            ell_col[k * n_pad + i] = -1;
+            ell_val[k * n_pad + i] = 0.0;
+        }
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
+            int64_t slot = (k - row_ptr[i]) * n_pad + i;
+            ell_col[slot] = col[k];
+            ell_val[slot] = val[k];
+        }
+}
+
+/* ELL -> CSR: drop padding slots (col == -1), keep slot order.  row_ptr
+ * must have n+1 entries; col_out/val_out room for all non-padding slots. */
+void orc_ell_to_csr(int64_t n, int64_t n_pad, int64_t K, const int32_t *ell_col,
+                    const double *ell_val, int32_t *row_ptr, int32_t *col_out,
+                    double *val_out)
+{
+    int64_t nz = 0;
+    row_ptr[0] = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        for (int64_t k = 0; k < K; ++k) {
+            int64_t slot = k * n_pad + i;
+            if (ell_col[slot] < 0)
+                continue;
+            col_out[nz] = ell_col[slot];
+            val_out[nz] = ell_val[slot];
+            ++nz;
+        }
+        row_ptr[i + 1] = (int32_t)nz;
+    }
+}
+
+/* SELL-P sizes: slice s (rows s*S .. s*S+S-1, clipped to n) has width
+ * slice_len[s] = max row length in the slice rounded up to a multiple of the
+ * stride factor f; slice_set is the exclusive prefix sum of the widths
+ * (n_slices + 1 entries).  Returns the total number of slots
+ * slice_set[n_slices] * S. */
+int64_t orc_sellp_sizes(int64_t n, const int32_t *row_ptr, int64_t S, int64_t f,
+                        int32_t *slice_len, int32_t *slice_set)
+{
+    int64_t n_slices = (n + S - 1) / S;
+    int64_t acc = 0;
+    for (int64_t s = 0; s < n_slices; ++s) {
+        int64_t w = 0;
+        for (int64_t i = s * S; i < (s + 1) * S && i < n; ++i) {
+            int64_t L = row_ptr[i + 1] - row_ptr[i];
+            if (L > w)
+                w = L;
+        }
+        w = (w + f - 1) / f * f;
+        slice_len[s] = (int32_t)w;
+        slice_set[s] = (int32_t)acc;
+        acc += w;
+    }
+    slice_set[n_slices] = (int32_t)acc;
+    return acc * S;
+}
+
+/* CSR -> SELL-P with the sizes of orc_sellp_sizes. */
+void orc_csr_to_sellp(int64_t n, int64_t S, const int32_t *row_ptr, const int32_t *col,
+                      const double *val, const int32_t *slice_len,
+                      const int32_t *slice_set, int32_t *s_col, double *s_val)
+{
+    int64_t n_slices = (n + S - 1) / S;
+    int64_t total = (int64_t)slice_set[n_slices] * S;
+    (void)slice_len; /* widths are implied by slice_set */
+    for (int64_t t = 0; t < total; ++t) {
+        s_col[t] = -1;
+        s_val[t] = 0.0;
+    }
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t s_id = i / S, l = i % S;
+        for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
+            int64_t slot = ((int64_t)slice_set[s_id] + (k - row_ptr[i])) * S + l;
+            s_col[slot] = col[k];
+            s_val[slot] = val[k];
+        }
+    }
+}
+
+/* SELL-P -> CSR: drop padding, keep slot order. */
+void orc_sellp_to_csr(int64_t n, int64_t S, const int32_t *slice_len,
+                      const int32_t *slice_set, const int32_t *s_col,
+                      const double *s_val, int32_t *row_ptr, int32_t *col_out,
+                      double *val_out)
+{
+    int64_t nz = 0;
+    row_ptr[0] = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t s_id = i / S, l = i % S;
+        for (int64_t k = 0; k < slice_len[s_id]; ++k) {
+            int64_t slot = ((int64_t)slice_set[s_id] + k) * S + l;
+            if (s_col[slot] < 0)
+                continue;
+            col_out[nz] = s_col[slot];
+            val_out[nz] = s_val[slot];
+            ++nz;
+        }
+        row_ptr[i + 1] = (int32_t)nz;
+    }
+}
+
+/* Hybrid width: K_h = argmin over K in [0, max row length] of the bytes
+ * n_pad * K * (s_v + 4) + overflow(K) * (s_v + 8), overflow(K) =
+ * sum_i max(0, len_i - K); ties go to the smaller K.  s_v is the value size
+ * in bytes. */
+int64_t orc_hybrid_width(int64_t n, const int32_t *row_ptr, int64_t s_v)
+{
+    int64_t kmax = orc_max_row_len(n, row_ptr);
+    int64_t n_pad = orc_ell_n_pad(n);
+    int64_t best_k = 0;
+    double best = -1.0;
+    for (int64_t K = 0; K <= kmax; ++K) {
+        int64_t over = 0;
+        for (int64_t i = 0; i < n; ++i) {
+            int64_t L = row_ptr[i + 1] - row_ptr[i];
+            if (L > K)
+                over += L - K;
+        }
+        double bytes = (double)n_pad * (double)K * (double)(s_v + 4) +
+                       (double)over * (double)(s_v + 8);
+        if (best < 0.0 || bytes < best) {
+            best = bytes;
+            best_k = K;
+        }
+    }
+    return best_k;
+}
+
+/* Number of entries that overflow an ELL part of width K. */
+int64_t orc_hybrid_coo_nnz(int64_t n, const int32_t *row_ptr, int64_t K)
+{
+    int64_t over = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t L = row_ptr[i + 1] - row_ptr[i];
+        if (L > K)
+            over += L - K;
+    }
+    return over;
+}
+
+/* CSR -> hybrid: row i's first min(len_i, K) entries go to the ELL part,
+ * the remaining ones, in order, to the COO part (sorted by (row, col)). */
+void orc_csr_to_hybrid(int64_t n, int64_t n_pad, int64_t K, const int32_t *row_ptr,
+                       const int32_t *col, const double *val, int32_t *ell_col,
+                       double *ell_val, int32_t *coo_row, int32_t *coo_col,
+                       double *coo_val)
+{
+    for (int64_t k = 0; k < K; ++k)
+        for (int64_t i = 0; i < n_pad; ++i) {
+            ell_col[k * n_pad + i] = -1;
+            ell_val[k * n_pad + i] = 0.0;
+        }
+    int64_t nz = 0;
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
+            int64_t j = k - row_ptr[i];
+            if (j < K) {
+                ell_col[j * n_pad + i] = col[k];
+                ell_val[j * n_pad + i] = val[k];
+            } else {
+                coo_row[nz] = (int32_t)i;
+                coo_col[nz] = col[k];
+                coo_val[nz] = val[k];
+                ++nz;
+            }
+        }
+}
+
+/* hybrid -> CSR: per row, its ELL slots (padding dropped) then its COO
+ * entries. */
+void orc_hybrid_to_csr(int64_t n, int64_t n_pad, int64_t K, const int32_t *ell_col,
+                       const double *ell_val, int64_t coo_nnz, const int32_t *coo_row,
+                       const int32_t *coo_col, const double *coo_val, int32_t *row_ptr,
+                       int32_t *col_out, double *val_out)
+{
+    int64_t nz = 0, q = 0;
+    row_ptr[0] = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        for (int64_t k = 0; k < K; ++k) {
+            int64_t slot = k * n_pad + i;
+            if (ell_col[slot] < 0)
+                continue;
+            col_out[nz] = ell_col[slot];
+            val_out[nz] = ell_val[slot];
+            ++nz;
+        }
+        while (q < coo_nnz && coo_row[q] == i) {
+            col_out[nz] = coo_col[q];
+            val_out[nz] = coo_val[q];
+            ++nz;
+            ++q;
+        }
+        row_ptr[i + 1] = (int32_t)nz;
+    }
+}
+
+/* ---------------------------------------------------------------- BLAS-1 */
+
+/* Plain dot product, summed in index order. */
+double orc_dot(int64_t n, const double *a, const double *b)
+{
+    double s = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        double p = a[i] * b[i];
+        s = s + p;
+    }
+    return s;
+}
+
+/* Dot2 of Ogita-Rump-Oishi (compensated dot product). */
+double orc_dot2(int64_t n, const double *a, const double *b)
+{
+    double s = 0.0, c = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        double p, e1, e2;
+        two_prod(a[i], b[i], &p, &e1);
+        two_sum(s, p, &s, &e2);
+        c = c + (e1 + e2);
+    }
+    return s + c;
+}
+
+static double nrm2(int64_t n, const double *a) { return sqrt(orc_dot(n, a, a)); }
+
+/* ||b - A x||_2 / ||b||_2 with the residual formed in FP64. */
+double orc_true_rel_residual(int64_t n, const int32_t *row_ptr, const int32_t *col,
+                             const double *val, const double *b, const double *x)
+{
+    double *r = (double *)malloc((size_t)(n > 0 ? n : 1) * sizeof(double));
+    for (int64_t i = 0; i < n; ++i)
+        r[i] = b[i];
+    orc_spmv_csr(n, row_ptr, col, val, x, -1.0, 1.0, r);
+    double nb = nrm2(n, b);
+    double res = nb > 0.0 ? nrm2(n, r) / nb : nrm2(n, r);
+    free(r);
+    return res;
+}
+
+/* ------------------------------------------------------------------- CG */
+
+/* Conjugate gradients (Hestenes and Stiefel 1952), the Krylov solver of
+ * Sec. 6.2 built on SpMV:
+ *   r = b - A x0, p = r, rho = r.r
+ *   repeat: q = A p; alpha = rho / (p.q); x += alpha p; r -= alpha q;
+ *           rho' = r.r; beta = rho' / rho; p = r + beta p; rho = rho'.
+ * Stopping: when the recursive residual satisfies sqrt(rho') <= tol ||b||,
+ * the true residual ||b - A x|| / ||b|| is formed in FP64; if it is <= tol
+ * the solve has converged, otherwise iteration continues; after the fourth
+ * failed confirmation the solve stops with ORC_NOT_CONVERGED, as it does at
+ * maxit.  p.q <= 0 (or NaN) is a breakdown (A not SPD).  ||b|| = 0 gives
+ * x = 0 at once.  x holds the initial guess on entry.  *iters counts the
+ * products q = A p. */
+int orc_cg(int64_t n, const int32_t *row_ptr, const int32_t *col, const double *val,
+           const double *b, double *x, double tol, int maxit, int *iters,
+           double *rel_res)
+{
+    double nb = nrm2(n, b);
+    *iters = 0;
+    if (nb == 0.0) {
+        for (int64_t i = 0; i < n; ++i)
+            x[i] = 0.0;
+        *rel_res = 0.0;
+        return ORC_OK;
+    }
+    size_t bytes = (size_t)(n > 0 ? n : 1) * sizeof(double);
+    double *r = (double *)malloc(bytes), *p = (double *)malloc(bytes),
+           *q = (double *)malloc(bytes);
+    for (int64_t i = 0; i < n; ++i)
+        r[i] = b[i];
+    orc_spmv_csr(n, row_ptr, col, val, x, -1.0, 1.0, r);
+    for (int64_t i = 0; i < n; ++i)
+        p[i] = r[i];
+    double rho = orc_dot(n, r, r);
+    int status = ORC_NOT_CONVERGED, checks = 0;
+    if (sqrt(rho) <= tol * nb) {
+        status = ORC_OK;
+        maxit = 0;
+    }
+    for (int it = 0; it < maxit; ++it) {
+        orc_spmv_csr(n, row_ptr, col, val, p, 1.0, 0.0, q);
+        *iters = it + 1;
+        double pq = orc_dot(n, p, q);
+        if (!(pq > 0.0)) {
+            status = ORC_BREAKDOWN;
+            break;
+        }
+        double alpha = rho / pq;
+        for (int64_t i = 0; i < n; ++i) {
+            double t = alpha * p[i];
+            x[i] = x[i] + t;
+            double u = alpha * q[i];
+            r[i] = r[i] - u;
+        }
+        double rho_new = orc_dot(n, r, r);
+        if (!(rho_new == rho_new)) {
+            status = ORC_BREAKDOWN;
+            break;
+        }
+        if (sqrt(rho_new) <= tol * nb) {
+            double t = orc_true_rel_residual(n, row_ptr, col, val, b, x);
+            ++checks;
+            if (t <= tol) {
+                status = ORC_OK;
+                break;
+            }
+            if (checks >= 4)
+                break;
+        }
+        double beta = rho_new / rho;
+        for (int64_t i = 0; i < n; ++i) {
+            double t = beta * p[i];
+            p[i] = r[i] + t;
+        }
+        rho = rho_new;
+    }
+    *rel_res = orc_true_rel_residual(n, row_ptr, col, val, b, x);
+    free(r);
+    free(p);
+    free(q);
+    return status;
+}
+
+/* Batched CG: systems s = 0..count-1 with rows [row_off[s], row_off[s+1])
+ * of one concatenated CSR whose row_ptr is global and whose column indices
+ * are local to the system.  Each system is solved by orc_cg. */
+int orc_cg_batched(int64_t count, const int64_t *row_off, const int32_t *row_ptr,
+                   const int32_t *col, const double *val, const double *b, double *x,
+                   double tol, int maxit, int *iters, double *rel_res, int *status)
+{
+    int worst = ORC_OK;
+    for (int64_t s = 0; s < count; ++s) {
+        int64_t r0 = row_off[s], n = row_off[s + 1] - row_off[s];
+        int32_t *rp = (int32_t *)malloc((size_t)(n + 1) * sizeof(int32_t));
+        for (int64_t i = 0; i <= n; ++i)
+            rp[i] = row_ptr[r0 + i] - row_ptr[r0];
+        status[s] = orc_cg(n, rp, col + row_ptr[r0], val + row_ptr[r0], b + r0, x + r0,
+                           tol, maxit, &iters[s], &rel_res[s]);
+        if (status[s] != ORC_OK)
+            worst = status[s];
+        free(rp);
+    }
+    return worst;
+}
+
+/* ------------------------------------------------- mixed precision + IR */
+
+/* Round a double to the nearest bfloat16 (8 significant bits), ties to
+ * even, returned as a double; up != 0 rounds toward +infinity instead.
+ * Written from the definition: scale the significand to 8 bits with frexp,
+ * round to an integer, scale back.  Values are assumed inside the normal
+ * bfloat16 range. */
+double orc_round_bf16(double v, int up)
+{
+    if (v == 0.0 || !isfinite(v))
+        return v;
+    int e;
+    double m = frexp(v, &e); /* v = m * 2^e, 0.5 <= |m| < 1 */
+    double sig = ldexp(m, 8);
+    double r = up ? ceil(sig) : nearbyint(sig); /* default mode: ties-to-even */
+    return ldexp(r, e - 8);
+}
+
+/* The same for binary32 (24 significant bits). */
+double orc_round_fp32(double v, int up)
+{
+    if (v == 0.0 || !isfinite(v))
+        return v;
+    int e;
+    double m = frexp(v, &e);
+    double sig = ldexp(m, 24);
+    double r = up ? ceil(sig) : nearbyint(sig);
+    return ldexp(r, e - 24);
+}
+
+/* Low-precision copy of an SPD matrix (prec 1 = FP32, 2 = BF16): every
+ * off-diagonal entry is rounded to nearest-even; the diagonal becomes
+ * a_ii + sum_j (|rn(a_ij)| - |a_ij|) formed in FP64 and rounded toward
+ * +infinity, so the margin of diagonal dominance a_ii - sum_j |a_ij| never
+ * shrinks and a diagonally dominant SPD matrix stays SPD after rounding. */
+void orc_round_matrix(int64_t n, const int32_t *row_ptr, const int32_t *col,
+                      const double *val, int prec, double *val_lo)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        double shift = 0.0;
+        int64_t kd = -1;
+        for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
+            if (col[k] == i) {
+                kd = k;
+                continue;
+            }
+            double r = prec == 2 ? orc_round_bf16(val[k], 0) : orc_round_fp32(val[k], 0);
+            val_lo[k] = r;
+            double d = fabs(r) - fabs(val[k]);
+            shift = shift + d;
+        }
+        if (kd >= 0) {
+            double d = val[kd] + shift;
+            val_lo[kd] = prec == 2 ? orc_round_bf16(d, 1) : orc_round_fp32(d, 1);
+        }
+    }
+}
+
+/* Mixed-precision CG with FP64 iterative refinement.
+ * Outer loop (FP64): r = b - A x with the FP64 matrix; stop when
+ * ||r|| / ||b|| <= tol; otherwise solve A_lo d = r / ||r|| approximately by
+ * an inner CG in FP32 arithmetic (FP32 vectors, FP32 products and row sums on
+ * the rounded matrix val_lo, dot products accumulated in FP64 and rounded
+ * to FP32) to relative recursive residual inner_tol or inner_maxit steps;
+ * then x += ||r|| d in FP64.  x holds the initial guess.  Counts outer
+ * corrections in *outer and inner CG steps in *inner. */
+int orc_cg_mixed(int64_t n, const int32_t *row_ptr, const int32_t *col,
+                 const double *val, const double *val_lo, const double *b, double *x,
+                 double tol, int maxit_outer, double inner_tol, int inner_maxit,
+                 int *outer, int *inner, double *rel_res)
+{
+    double nb = nrm2(n, b);
+    *outer = 0;
+    *inner = 0;
+    if (nb == 0.0) {
+        for (int64_t i = 0; i < n; ++i)
+            x[i] = 0.0;
+        *rel_res = 0.0;
+        return ORC_OK;
+    }
+    size_t nn = (size_t)(n > 0 ? n : 1);
+    double *r = (double *)malloc(nn * sizeof(double));
+    float *rl = (float *)malloc(nn * sizeof(float)), *d = (float *)malloc(nn * sizeof(float)),
+          *p = (float *)malloc(nn * sizeof(float)), *q = (float *)malloc(nn * sizeof(float)),
+          *vl = (float *)malloc((size_t)(row_ptr[n] > 0 ? row_ptr[n] : 1) * sizeof(float));
+    for (int64_t k = 0; k < row_ptr[n]; ++k)
+        vl[k] = (float)val_lo[k]; /* exact: val_lo holds FP32/BF16 values */
+    int status = ORC_NOT_CONVERGED;
+    for (int o = 0; o <= maxit_outer; ++o) {
+        for (int64_t i = 0; i < n; ++i)
+            r[i] = b[i];
+        orc_spmv_csr(n, row_ptr, col, val, x, -1.0, 1.0, r);
+        double nr = nrm2(n, r);
+        if (nr <= tol * nb) {
+            status = ORC_OK;
+            break;
+        }
+        if (o == maxit_outer)
+            break;
+        *outer = o + 1;
+        /* inner CG on A_lo d = r / ||r||, d0 = 0 */
+        for (int64_t i = 0; i < n; ++i) {
+            rl[i] = (float)(r[i] / nr);
+            d[i] = 0.0f;
+            p[i] = rl[i];
+        }
+        double rho_d = 0.0;
+        for (int64_t i = 0; i < n; ++i)
+            rho_d = rho_d + (double)rl[i] * (double)rl[i];
+        float rho = (float)rho_d;
+        float rho0 = rho;
+        for (int it = 0; it < inner_maxit; ++it) {
+            for (int64_t i = 0; i < n; ++i) {
+                float s = 0.0f;
+                for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
+                    float t = vl[k] * p[col[k]];
+                    s = s + t;
+                }
+                q[i] = s;
+            }
+            *inner += 1;
+            double pq_d = 0.0;
+            for (int64_t i = 0; i < n; ++i)
+                pq_d = pq_d + (double)p[i] * (double)q[i];
+            float pq = (float)pq_d;
+            if (!(pq > 0.0f))
+                break;
+            float alpha = rho / pq;
+            for (int64_t i = 0; i < n; ++i) {
+                float t = alpha * p[i];
+                d[i] = d[i] + t;
+                float u = alpha * q[i];
+                rl[i] = rl[i] - u;
+            }
+            double rn_d = 0.0;
+            for (int64_t i = 0; i < n; ++i)
+                rn_d = rn_d + (double)rl[i] * (double)rl[i];
+            float rho_new = (float)rn_d;
+            if (sqrtf(rho_new) <= (float)inner_tol * sqrtf(rho0))
+                break;
+            float beta = rho_new / rho;
+            for (int64_t i = 0; i < n; ++i) {
+                float t = beta * p[i];
+                p[i] = rl[i] + t;
+            }
+            rho = rho_new;
+        }
+        for (int64_t i = 0; i < n; ++i) {
+            double t = nr * (double)d[i];
+            x[i] = x[i] + t;
+        }
+    }
+    *rel_res = orc_true_rel_residual(n, row_ptr, col, val, b, x);
+    free(r);
+    free(rl);
+    free(d);
+    free(p);
+    free(q);
+    free(vl);
+    return status;
+}
+
+/* ------------------------------------------------------- dense Cholesky */
+
+/* Solve A x = b for a dense SPD A (row-major n x n) by Cholesky A = L L^T,
+ * forward and back substitution.  Returns ORC_BREAKDOWN if a pivot is not
+ * positive.  A is not modified. */
+int orc_cholesky_solve(int64_t n, const double *A, const double *b, double *x)
+{
+    double *L = (double *)calloc((size_t)(n * n > 0 ? n * n : 1), sizeof(double));
+    for (int64_t j = 0; j < n; ++j) {
+        double s = A[j * n + j];
+        for (int64_t k = 0; k < j; ++k) {
+            double t = L[j * n + k] * L[j * n + k];
+            s = s - t;
+        }
+        if (!(s > 0.0)) {
+            free(L);
+            return ORC_BREAKDOWN;
+        }
+        L[j * n + j] = sqrt(s);
+        for (int64_t i = j + 1; i < n; ++i) {
+            double t = A[i * n + j];
+            for (int64_t k = 0; k < j; ++k) {
+                double u = L[i * n + k] * L[j * n + k];
+                t = t - u;
+            }
+            L[i * n + j] = t / L[j * n + j];
+        }
+    }
+    for (int64_t i = 0; i < n; ++i) { /* L y = b */
+        double t = b[i];
+        for (int64_t k = 0; k < i; ++k) {
+            double u = L[i * n + k] * x[k];
+            t = t - u;
+        }
+        x[i] = t / L[i * n + i];
+    }
+    for (int64_t i = n - 1; i >= 0; --i) { /* L^T x = y */
+        double t = x[i];
+        for (int64_t k = i + 1; k < n; ++k) {
+            double u = L[k * n + i] * x[k];
+            t = t - u;
+        }
+        x[i] = t / L[i * n + i];
+    }
+    free(L);
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------- features */
+
+/* The 12 matrix statistics of the format selector, in order:
+ *  0 log10(n)            1 log10(max(nnz, 1))     2 mean row length
+ *  3 std of row lengths  4 max row length         5 min row length
+ *  6 max / mean (0 if mean is 0)                  7 fraction of empty rows
+ *  8 max |i - j| / n     9 mean |i - j| / n over stored entries (0 if none)
+ * 10 fraction of rows that store their diagonal
+ * 11 SELL-P slots / nnz with slices of 32 rows, stride factor 1 (0 if nnz 0)
+ * n = number of rows (> 0).  Standard deviation is the population one. */
+void orc_features(int64_t n, const int32_t *row_ptr, const int32_t *col, double *f)
+{
+    int64_t nnz = row_ptr[n];
+    double mean = (double)nnz / (double)n;
+    double var = 0.0, maxd = 0.0, sumd = 0.0;
+    int64_t lmax = 0, lmin = -1, empty = 0, diag = 0, slots = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t L = row_ptr[i + 1] - row_ptr[i];
+        double dev = (double)L - mean;
+        var = var + dev * dev;
+        if (L > lmax)
+            lmax = L;
+        if (lmin < 0 || L < lmin)
+            lmin = L;
+        if (L == 0)
+            ++empty;
+        for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
+            double dd = fabs((double)col[k] - (double)i);
+            if (dd > maxd)
+                maxd = dd;
+            sumd = sumd + dd;
+            if (col[k] == i)
+                ++diag;
+        }
+    }
+    for (int64_t s = 0; s * 32 < n; ++s) {
+        int64_t w = 0;
+        for (int64_t i = s * 32; i < s * 32 + 32 && i < n; ++i)
+            if (row_ptr[i + 1] - row_ptr[i] > w)
+                w = row_ptr[i + 1] - row_ptr[i];
+        slots += 32 * w;
+    }
+    f[0] = log10((double)n);
+    f[1] = log10((double)(nnz > 0 ? nnz : 1));
+    f[2] = mean;
+    f[3] = sqrt(var / (double)n);
+    f[4] = (double)lmax;
+    f[5] = (double)lmin;
+    f[6] = mean > 0.0 ? (double)lmax / mean : 0.0;
+    f[7] = (double)empty / (double)n;
+    f[8] = maxd / (double)n;
+    f[9] = nnz > 0 ? sumd / (double)nnz / (double)n : 0.0;
+    f[10] = (double)diag / (double)n;
+    f[11] = nnz > 0 ? (double)slots / (double)nnz : 0.0;
+}

@@ -1,0 +1,423 @@
+"""Pins of the CPU oracle against facts that do not come from the oracle itself:
+dense brute force, closed forms of the 5-point Laplacian, exact rational
+arithmetic, a textbook dense solver, exhaustive enumeration and finite
+differences.  Each pin is chosen so that a plausible slip in the oracle (a
+dropped term, a wrong index, a transposed operand) fails it."""
+import math
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import synthetic as syn
+
+
+def small_mats():
+    out = []
+    for seed, (n, m, k, e) in enumerate([(1, 1, 1, 0.0), (7, 5, 5, 0.3), (33, 40, 9, 0.2),
+                                         (64, 64, 20, 0.1), (65, 17, 17, 0.5), (50, 80, 0, 0.0),
+                                         (96, 96, 31, 0.05)]):
+        out.append(syn.random_csr(n, m, k, seed=100 + seed, empty_frac=e))
+    return out
+
+
+def dense(A):
+    D = np.zeros((A["n_rows"], A["n_cols"]))
+    rp = A["row_ptr"]
+    for i in range(A["n_rows"]):
+        for k in range(rp[i], rp[i + 1]):
+            D[i, A["col_idx"][k]] += A["val"][k]
+    return D
+
+
+# ---------------------------------------------------------------- SpMV pins
+
+@pytest.mark.parametrize("alpha,beta", [(1.0, 0.0), (-1.0, 1.0), (2.5, -0.5), (0.0, 2.0)])
+def test_every_format_matches_dense_matvec(orc, alpha, beta):
+    for A in small_mats():
+        n, m = A["n_rows"], A["n_cols"]
+        x = syn.vector(m, 5)
+        y0 = syn.vector(n, 6)
+        ref = alpha * (dense(A) @ x) + beta * y0
+        mag = abs(alpha) * (np.abs(dense(A)) @ np.abs(x)) + abs(beta) * np.abs(y0)
+        tol = 1e-14 * mag + 1e-300
+        outs = {
+            "csr": orc.spmv_csr(A, x, alpha, beta, y0),
+            "coo": orc.spmv_coo(n, orc.to_coo(A), x, alpha, beta, y0),
+            "ell": orc.spmv_ell(n, orc.to_ell(A), x, alpha, beta, y0),
+            "sellp32": orc.spmv_sellp(n, orc.to_sellp(A, 32), x, alpha, beta, y0),
+            "sellp64f4": orc.spmv_sellp(n, orc.to_sellp(A, 64, 4), x, alpha, beta, y0),
+            "hybrid": orc.spmv_hybrid(n, orc.to_hybrid(A), x, alpha, beta, y0),
+            "hybrid_k1": orc.spmv_hybrid(n, orc.to_hybrid(A, K=1), x, alpha, beta, y0),
+        }
+        for name, y in outs.items():
+            assert np.all(np.abs(y - ref) <= tol), (name, n, m)
+
+
+def test_beta_zero_does_not_read_y(orc):
+    A = small_mats()[3]
+    x = syn.vector(A["n_cols"], 1)
+    y = np.full(A["n_rows"], np.nan)
+    out = orc.spmv_csr(A, x, 1.0, 0.0, y)
+    assert np.all(np.isfinite(out))
+
+
+def test_integer_values_make_every_format_exact(orc):
+    """Integer-valued A and x: every partial sum is an exactly representable
+    integer, so each format equals the exact integer product bit for bit."""
+    for A in small_mats() + [syn.powerlaw(3000, 20.0, 1.5, 400, seed=9)]:
+        A = dict(A)
+        A["val"] = np.round(A["val"] * 8.0)
+        n, m = A["n_rows"], A["n_cols"]
+        xi = np.round(syn.vector(m, 3) * 16.0)
+        exact = np.zeros(n, dtype=np.int64)
+        rp = A["row_ptr"]
+        for i in range(n):
+            for k in range(rp[i], rp[i + 1]):
+                exact[i] += int(A["val"][k]) * int(xi[A["col_idx"][k]])
+        ys = [orc.spmv_csr(A, xi), orc.spmv_coo(n, orc.to_coo(A), xi),
+              orc.spmv_sellp(n, orc.to_sellp(A, 64), xi), orc.spmv_hybrid(n, orc.to_hybrid(A), xi)]
+        if orc.max_row_len(A) <= 64:
+            ys.append(orc.spmv_ell(n, orc.to_ell(A), xi))
+        for y in ys:
+            assert np.array_equal(y, exact.astype(np.float64))
+
+
+def test_laplacian_row_sums_closed_form(orc):
+    """A * 1 for the 5-point Dirichlet Laplacian: 0 inside, 1 on an edge, 2 at a corner."""
+    nx = 128
+    A = syn.laplace2d(nx)
+    y = orc.spmv_csr(A, np.ones(nx * nx))
+    idx = np.arange(nx * nx)
+    i, j = idx % nx, idx // nx
+    boundary_sides = (i == 0).astype(int) + (i == nx - 1) + (j == 0) + (j == nx - 1)
+    assert np.array_equal(y, boundary_sides.astype(np.float64))
+    assert A["row_ptr"][-1] == 5 * nx * nx - 4 * nx
+
+
+@pytest.mark.parametrize("jk", [(1, 1), (3, 7), (64, 2), (127, 127), (100, 33)])
+def test_laplacian_eigenpairs(orc, jk):
+    """v(p,q) = sin(j p pi/(nx+1)) sin(k q pi/(nx+1)), lambda = 4 - 2cos(j pi/(nx+1)) - 2cos(k pi/(nx+1))."""
+    nx = 128
+    jj, kk = jk
+    A = syn.laplace2d(nx)
+    idx = np.arange(nx * nx)
+    p, q = idx % nx + 1, idx // nx + 1
+    v = np.sin(jj * p * np.pi / (nx + 1)) * np.sin(kk * q * np.pi / (nx + 1))
+    lam = 4 - 2 * math.cos(jj * math.pi / (nx + 1)) - 2 * math.cos(kk * math.pi / (nx + 1))
+    Av = orc.spmv_csr(A, v)
+    assert np.linalg.norm(Av - lam * v) <= 1e-13 * np.linalg.norm(v)
+
+
+def test_dot2_matches_exact_rational_sum(orc):
+    rng = np.random.default_rng(0)
+    for n in (1, 10, 1000):
+        a = rng.standard_normal(n) * 10.0 ** rng.integers(-8, 8, n)
+        b = rng.standard_normal(n)
+        exact = sum(Fraction(float(u)) * Fraction(float(w)) for u, w in zip(a, b))
+        d2 = orc.dot2(a, b)
+        mag = float(np.sum(np.abs(a * b)))
+        assert abs(Fraction(d2) - exact) <= Fraction(2.0 ** -52) * abs(exact) + Fraction(mag * 2.0 ** -100)
+        # and the plain dot is the sequential definition
+        s = 0.0
+        for u, w in zip(a, b):
+            s = s + u * w
+        assert orc.dot(a, b) == s
+
+
+def test_spmv_dot2_reference_is_near_exact(orc):
+    A = syn.powerlaw(2000, 20.0, 1.5, 2000, seed=11)
+    x = syn.vector(2000, 12)
+    y0 = syn.vector(2000, 13)
+    yref, mag = orc.spmv_dot2(A, x, 1.5, -0.25, y0)
+    rp = A["row_ptr"]
+    for i in range(0, 2000, 97):
+        ex = Fraction(1.5) * sum(Fraction(float(A["val"][k])) * Fraction(float(x[A["col_idx"][k]]))
+                                 for k in range(rp[i], rp[i + 1])) + Fraction(-0.25) * Fraction(float(y0[i]))
+        assert abs(Fraction(float(yref[i])) - ex) <= Fraction(2.0 ** -52) * abs(ex) + Fraction(float(mag[i]) * 2.0 ** -104)
+        m_ex = 1.5 * sum(abs(A["val"][k] * x[A["col_idx"][k]]) for k in range(rp[i], rp[i + 1])) + 0.25 * abs(y0[i])
+        assert abs(mag[i] - m_ex) <= 1e-13 * m_ex
+
+
+# ---------------------------------------------------------- format layouts
+
+def test_round_trips_are_bit_exact(orc):
+    mats = small_mats() + [syn.powerlaw(5000, 20.0, 1.5, 3000, seed=21), syn.laplace2d(20)]
+    for A in mats:
+        A = dict(A)
+        A["val"] = A["val"].copy()
+        if len(A["val"]) > 3:
+            A["val"][::3] = 0.0  # explicit stored zeros must survive
+            A["val"][1::7] = -0.0
+        n, m = A["n_rows"], A["n_cols"]
+        back = [orc.coo_to_csr(n, orc.to_coo(A), m),
+                orc.sellp_to_csr(n, orc.to_sellp(A, 32), m),
+                orc.sellp_to_csr(n, orc.to_sellp(A, 64, 8), m),
+                orc.hybrid_to_csr(n, orc.to_hybrid(A), m),
+                orc.hybrid_to_csr(n, orc.to_hybrid(A, K=0), m),
+                orc.hybrid_to_csr(n, orc.to_hybrid(A, K=3), m)]
+        if orc.max_row_len(A) <= 64:
+            back.append(orc.ell_to_csr(n, orc.to_ell(A), m))
+        for B in back:
+            assert np.array_equal(B["row_ptr"], A["row_ptr"])
+            assert np.array_equal(B["col_idx"], A["col_idx"])
+            assert B["val"].tobytes() == A["val"].tobytes()
+
+
+def test_ell_layout_brute_force(orc):
+    A = small_mats()[2]
+    E = orc.to_ell(A)
+    n = A["n_rows"]
+    assert E["n_pad"] == 64 and E["K"] == int(np.diff(A["row_ptr"]).max())
+    col = E["col"].reshape(E["K"], E["n_pad"])
+    val = E["val"].reshape(E["K"], E["n_pad"])
+    for i in range(E["n_pad"]):
+        L = A["row_ptr"][i + 1] - A["row_ptr"][i] if i < n else 0
+        for k in range(E["K"]):
+            if k < L:
+                assert col[k, i] == A["col_idx"][A["row_ptr"][i] + k]
+                assert val[k, i] == A["val"][A["row_ptr"][i] + k]
+            else:
+                assert col[k, i] == -1 and val[k, i] == 0.0 and not np.signbit(val[k, i])
+
+
+def test_sellp_layout_brute_force(orc):
+    A = syn.random_csr(150, 150, 12, seed=31, empty_frac=0.2)
+    for S, f in ((32, 1), (64, 1), (32, 4)):
+        s = orc.to_sellp(A, S, f)
+        L = np.diff(A["row_ptr"])
+        ns = -(-150 // S)
+        acc = 0
+        for t in range(ns):
+            w = int(L[t * S:(t + 1) * S].max())
+            w = -(-w // f) * f
+            assert s["slice_len"][t] == w and s["slice_set"][t] == acc
+            acc += w
+        assert s["slice_set"][ns] == acc and len(s["col"]) == acc * S
+        for i in range(150):
+            t, l = divmod(i, S)
+            for k in range(s["slice_len"][t]):
+                slot = (s["slice_set"][t] + k) * S + l
+                if k < L[i]:
+                    assert s["col"][slot] == A["col_idx"][A["row_ptr"][i] + k]
+                else:
+                    assert s["col"][slot] == -1
+
+
+def test_hybrid_width_is_byte_argmin(orc):
+    for A in small_mats() + [syn.powerlaw(4000, 20.0, 1.5, 2000, seed=41)]:
+        L = np.diff(A["row_ptr"]).astype(np.int64)
+        n_pad = -(-A["n_rows"] // 32) * 32
+        for s_v in (8, 4, 2):
+            costs = [n_pad * K * (s_v + 4) + int(np.maximum(L - K, 0).sum()) * (s_v + 8)
+                     for K in range(int(L.max(initial=0)) + 1)]
+            assert orc.hybrid_width(A, s_v) == int(np.argmin(costs))
+
+
+# ----------------------------------------------------------------- solvers
+
+def test_cholesky_matches_numpy(orc):
+    rng = np.random.default_rng(3)
+    for n in (1, 5, 40):
+        G = rng.standard_normal((n, n))
+        A = G @ G.T + n * np.eye(n)
+        b = rng.standard_normal(n)
+        x, st = orc.cholesky_solve(A, b)
+        assert st == 0
+        assert np.allclose(x, np.linalg.solve(A, b), rtol=1e-12, atol=1e-12)
+    x, st = orc.cholesky_solve(np.array([[1.0, 2.0], [2.0, 1.0]]), np.ones(2))
+    assert st == orc.BREAKDOWN
+
+
+def test_cg_manufactured_solution_laplace(orc):
+    A = syn.laplace2d(128)
+    n = A["n_rows"]
+    xt = syn.vector(n, 1)
+    b = orc.spmv_csr(A, xt)
+    x, st, it, res = orc.cg(A, b, tol=1e-10)
+    assert st == orc.OK and res <= 1e-10
+    assert 350 <= it <= 420
+    lam_min = 4 - 4 * math.cos(math.pi / 129)
+    lam_max = 4 + 4 * math.cos(math.pi / 129)
+    kappa = lam_max / lam_min
+    assert 6700 < kappa < 6800
+    assert np.linalg.norm(x - xt) <= kappa * 1e-10 * np.linalg.norm(xt)
+
+
+def test_cg_small_spd_vs_cholesky(orc):
+    B = syn.batched_spd(6, seed=5, n_min=8, n_max=60)
+    for s in range(6):
+        r0, r1 = B["row_off"][s], B["row_off"][s + 1]
+        k0, k1 = B["row_ptr"][r0], B["row_ptr"][r1]
+        A = dict(n_rows=r1 - r0, n_cols=r1 - r0, row_ptr=B["row_ptr"][r0:r1 + 1] - k0,
+                 col_idx=B["col_idx"][k0:k1], val=B["val"][k0:k1])
+        D = dense(A)
+        assert np.array_equal(D, D.T)
+        b = B["rhs"][r0:r1]
+        xc, st = orc.cholesky_solve(D, b)
+        assert st == 0
+        x, st, it, res = orc.cg(A, b, tol=1e-12)
+        assert st == orc.OK
+        assert np.linalg.norm(x - xc) <= 1e-10 * np.linalg.norm(xc)
+        assert it <= r1 - r0 + 5
+
+
+def test_cg_special_cases(orc):
+    A = syn.laplace2d(8)
+    n = A["n_rows"]
+    x, st, it, res = orc.cg(A, np.zeros(n), x0=np.ones(n))
+    assert st == orc.OK and it == 0 and np.all(x == 0)
+    b = orc.spmv_csr(A, syn.vector(n, 2))
+    x, st, it, res = orc.cg(A, b, maxit=1)
+    assert st == orc.NOT_CONVERGED and it == 1
+    Aneg = dict(A)
+    Aneg["val"] = -A["val"]
+    x, st, it, res = orc.cg(Aneg, b)
+    assert st == orc.BREAKDOWN
+    # an exact initial guess needs no iteration
+    xt = syn.vector(n, 2)
+    x, st, it, res = orc.cg(A, b, x0=xt)
+    assert st == orc.OK and it == 0
+
+
+def test_cg_matches_scipy_solution(orc):
+    sp = pytest.importorskip("scipy.sparse")
+    spl = pytest.importorskip("scipy.sparse.linalg")
+    A = syn.diffusion7(12, 1.0, seed=6)
+    n = A["n_rows"]
+    M = sp.csr_matrix((A["val"], A["col_idx"], A["row_ptr"]), shape=(n, n))
+    b = syn.vector(n, 4)
+    x, st, it, res = orc.cg(A, b, tol=1e-12)
+    xs = spl.spsolve(M.tocsc(), b)
+    assert st == orc.OK
+    assert np.linalg.norm(x - xs) <= 1e-9 * np.linalg.norm(xs)
+
+
+def test_batched_cg(orc):
+    B = syn.batched_spd(12, seed=8)
+    x, st, it, res = orc.cg_batched(B, B["rhs"], tol=1e-10)
+    assert np.all(st == 0) and np.all(res <= 1e-10)
+    assert np.all(it > 0)
+
+
+# --------------------------------------------------------- mixed precision
+
+def _bf16_neighbours(v):
+    """All bfloat16 values adjacent to v, by enumeration of float32 bit patterns."""
+    f = np.float32(v)
+    bits = int(np.array(f, dtype=np.float32).view(np.uint32)) & 0xFFFF0000
+    cands = []
+    for dlt in (-2, -1, 0, 1, 2):
+        bb = (bits + dlt * 0x10000) & 0xFFFFFFFF
+        cands.append(float(np.array(bb, dtype=np.uint32).view(np.float32)))
+    return sorted(set(cands))
+
+
+def test_round_bf16_by_enumeration(orc):
+    rng = np.random.default_rng(7)
+    vals = list(rng.standard_normal(400) * 10.0 ** rng.integers(-5, 5, 400))
+    vals += [1.0, 1.00390625, 1.001953125, 1.005859375, -1.001953125, 3.0 + 2 ** -7, 255.5]
+    for v in vals:
+        c = _bf16_neighbours(v)
+        dist = [abs(Fraction(u) - Fraction(v)) for u in c]
+        best = min(dist)
+        winners = [u for u, d in zip(c, dist) if d == best]
+        if len(winners) > 1:  # tie: the even significand (low bit of the bf16 pattern clear)
+            winners = [u for u in winners
+                       if (int(np.array(np.float32(u)).view(np.uint32)) >> 16) % 2 == 0]
+        assert orc.round_bf16(v) == winners[0], v
+        up = min(u for u in c if u >= v)
+        assert orc.round_bf16(v, up=True) == up, v
+
+
+def test_round_fp32_matches_ieee_cast(orc):
+    rng = np.random.default_rng(8)
+    for v in rng.standard_normal(1000) * 10.0 ** rng.integers(-20, 20, 1000):
+        assert orc.round_fp32(v) == float(np.float32(v))
+        u = orc.round_fp32(v, up=True)
+        assert u >= v and float(np.nextafter(np.float32(u), np.float32(-np.inf))) < v
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_round_matrix_keeps_diagonal_dominance(orc, prec):
+    A = syn.diffusion7(10, 1.0, seed=6)
+    lo = orc.round_matrix(A, prec)
+    rp, ci = A["row_ptr"], A["col_idx"]
+    for i in range(A["n_rows"]):
+        ks = range(rp[i], rp[i + 1])
+        off = [k for k in ks if ci[k] != i]
+        kd = [k for k in ks if ci[k] == i][0]
+        margin = A["val"][kd] - sum(abs(A["val"][k]) for k in off)
+        margin_lo = lo[kd] - sum(abs(lo[k]) for k in off)
+        assert margin_lo >= margin - 1e-12 * A["val"][kd]
+        for k in off:
+            r = orc.round_bf16(A["val"][k]) if prec == "bf16" else float(np.float32(A["val"][k]))
+            assert lo[k] == r
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_mixed_cg_reaches_fp64_accuracy(orc, prec):
+    A = syn.diffusion7(16, 1.0, seed=6)
+    n = A["n_rows"]
+    xt = syn.vector(n, 6)
+    b = orc.spmv_csr(A, xt)
+    x64, st, it, res = orc.cg(A, b, tol=1e-10)
+    x, st, outer, inner, res = orc.cg_mixed(A, b, prec, tol=1e-10, inner_tol=1e-3)
+    assert st == orc.OK and res <= 1e-10
+    assert 1 <= outer <= 30
+    assert np.linalg.norm(x - x64) <= 1e-8 * np.linalg.norm(x64)
+
+
+# ---------------------------------------------------------------- features
+
+def test_features_brute_force(orc):
+    for A in small_mats() + [syn.laplace2d(16), syn.banded(500, 64, 16, seed=3)]:
+        n = A["n_rows"]
+        L = [int(A["row_ptr"][i + 1] - A["row_ptr"][i]) for i in range(n)]
+        nnz = sum(L)
+        mean = nnz / n
+        ent = [(i, int(A["col_idx"][k])) for i in range(n) for k in range(A["row_ptr"][i], A["row_ptr"][i + 1])]
+        slots = sum(32 * max(L[s:s + 32]) for s in range(0, n, 32))
+        exp = [math.log10(n), math.log10(max(nnz, 1)), mean,
+               math.sqrt(sum((l - mean) ** 2 for l in L) / n), max(L), min(L),
+               max(L) / mean if mean else 0.0, sum(l == 0 for l in L) / n,
+               max((abs(i - j) for i, j in ent), default=0) / n,
+               (sum(abs(i - j) for i, j in ent) / nnz / n) if nnz else 0.0,
+               sum(1 for i, j in ent if i == j) / n, slots / nnz if nnz else 0.0]
+        f = orc.features(A)
+        assert np.allclose(f, exp, rtol=1e-12, atol=0), (f, exp)
+
+
+# ---------------------------------------------------------------------- MLP
+
+def test_mlp_gradient_central_differences():
+    from oracle import mlp
+    rng = np.random.default_rng(1)
+    C = 5
+    P = {k: rng.standard_normal(s) * 0.3 for k, s in mlp.shapes(12, 64, C).items()}
+    X = rng.standard_normal((16, 12))
+    Y = rng.standard_normal((16, C))
+    M = (rng.random((16, C)) > 0.2).astype(float)
+    L, g = mlp.loss_and_grad(P, X, Y, M)
+    h = 1e-6
+    for k in mlp.NAMES:
+        flat = P[k].reshape(-1)
+        for t in rng.choice(flat.size, size=min(6, flat.size), replace=False):
+            old = flat[t]
+            flat[t] = old + h
+            lp = mlp.loss(P, X, Y, M)
+            flat[t] = old - h
+            lm = mlp.loss(P, X, Y, M)
+            flat[t] = old
+            fd = (lp - lm) / (2 * h)
+            assert abs(fd - g[k].reshape(-1)[t]) <= 1e-6 * max(1.0, abs(fd)), (k, t)
+
+
+def test_adam_first_step_moves_by_lr():
+    """At t = 1 Adam moves every parameter by lr * sign(g) (up to eps)."""
+    from oracle import mlp
+    P = {k: np.zeros(s) for k, s in mlp.shapes(12, 64, 3).items()}
+    g = {k: np.full(s, 0.5) for k, s in mlp.shapes(12, 64, 3).items()}
+    g["b3"][:] = -2.0
+    P = mlp.adam_step(P, g, {}, 1, lr=0.01)
+    assert np.allclose(P["W1"], -0.01, rtol=1e-6) and np.allclose(P["b3"], 0.01, rtol=1e-6)
