@@ -650,9 +650,14 @@ double orc_round_fp32(double v, int up)
 
 /* Low-precision copy of an SPD matrix (prec 1 = FP32, 2 = BF16): every
  * off-diagonal entry is rounded to nearest-even; the diagonal becomes
- * a_ii + sum_j (|rn(a_ij)| - |a_ij|) formed in FP64 and rounded toward
- * +infinity, so the margin of diagonal dominance a_ii - sum_j |a_ij| never
- * shrinks and a diagonally dominant SPD matrix stays SPD after rounding. */
+ * a_ii + sum_j (|rn(a_ij)| - |a_ij|), formed in FP64 (for a matrix with
+ * non-positive off-diagonals this keeps every row sum of the copy equal to
+ * the original's), then rounded to nearest-even.  Rounding the diagonal to
+ * nearest keeps the perturbation zero-mean: an upward rounding would add a
+ * one-sided shift of up to one BF16 ulp (~0.4 % of a_ii) to every row,
+ * which exceeds the smallest eigenvalue of ill-conditioned diffusion
+ * operators and stalls the refinement.  SPD-ness of the copy is therefore
+ * not guaranteed by construction; the inner CG detects a breakdown. */
 void orc_round_matrix(int64_t n, const int32_t *row_ptr, const int32_t *col,
                       const double *val, int prec, double *val_lo)
 {
@@ -671,7 +676,7 @@ void orc_round_matrix(int64_t n, const int32_t *row_ptr, const int32_t *col,
         }
         if (kd >= 0) {
             double d = val[kd] + shift;
-            val_lo[kd] = prec == 2 ? orc_round_bf16(d, 1) : orc_round_fp32(d, 1);
+            val_lo[kd] = prec == 2 ? orc_round_bf16(d, 0) : orc_round_fp32(d, 0);
         }
     }
 }

@@ -339,20 +339,29 @@ def test_round_fp32_matches_ieee_cast(orc):
 
 
 @pytest.mark.parametrize("prec", ["fp32", "bf16"])
-def test_round_matrix_keeps_diagonal_dominance(orc, prec):
+def test_round_matrix_preserves_row_sums(orc, prec):
+    """Off-diagonals are the nearest low-precision values; the diagonal is
+    the nearest value to the row-sum-preserving target, so every row sum of
+    the copy is within half an ulp of the diagonal of the original's."""
     A = syn.diffusion7(10, 1.0, seed=6)
     lo = orc.round_matrix(A, prec)
     rp, ci = A["row_ptr"], A["col_idx"]
+    bits = 8 if prec == "bf16" else 24
     for i in range(A["n_rows"]):
         ks = range(rp[i], rp[i + 1])
         off = [k for k in ks if ci[k] != i]
         kd = [k for k in ks if ci[k] == i][0]
-        margin = A["val"][kd] - sum(abs(A["val"][k]) for k in off)
-        margin_lo = lo[kd] - sum(abs(lo[k]) for k in off)
-        assert margin_lo >= margin - 1e-12 * A["val"][kd]
         for k in off:
             r = orc.round_bf16(A["val"][k]) if prec == "bf16" else float(np.float32(A["val"][k]))
             assert lo[k] == r
+        target = Fraction(A["val"][kd]) + sum(Fraction(abs(lo[k])) - Fraction(abs(A["val"][k])) for k in off)
+        half_ulp = Fraction(2) ** (math.frexp(float(target))[1] - bits - 1)
+        # the target itself is formed in FP64: allow a few FP64 ulps on top
+        slack = Fraction(8) * Fraction(2) ** -52 * abs(target)
+        assert abs(Fraction(lo[kd]) - target) <= half_ulp + slack
+        row_sum = sum(Fraction(A["val"][k]) for k in ks)
+        row_sum_lo = sum(Fraction(lo[k]) for k in ks)
+        assert abs(row_sum_lo - row_sum) <= half_ulp + slack
 
 
 @pytest.mark.parametrize("prec", ["fp32", "bf16"])
