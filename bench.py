@@ -1,0 +1,482 @@
+#!/usr/bin/env python3
+"""Benchmark of the sparse hot path on GB300.
+
+One step = one FP64 SpMV (y = A x) in every available format (CSR, COO,
+ELL, SELL-P, hybrid) on each matrix of the SpMV sweep: a 27-point stencil on
+a 128^3 grid, a random banded matrix (4M rows, bandwidth 64, 16/row), a
+power-law matrix (2M rows, Pareto tail 1.5, mean 20/row, max 20k) and a
+block-diagonal matrix (1M rows, 8x8 blocks).  L2 is flushed (a 512 MB
+write) before every SpMV and only the SpMV kernels are timed, with CUDA
+events on the launching stream.  value = algorithmic bytes (values +
+indices + x + y) of all SpMVs / their total time.
+
+Extras in the same JSON line: the same metric end to end through
+gko_spmv_host (host buffers, copies inside the timed region), the roofline
+of the dominant kernel, the oracle timed on the host cores, CG time to a
+1e-10 relative residual (5-point Laplacian 128^2; 7-point diffusion 160^3
+in FP64 vs FP32/BF16 + FP64 refinement) and batched CG on 4096 systems.
+
+--impl reference times the CPU oracle on the same workload (bounded
+sample per step).  Multi-GPU (torchrun): every rank runs its own replica.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synthetic as syn  # noqa: E402
+
+SWEEP = syn.SPMV_SWEEP
+FORMATS = ("csr", "coo", "ell", "sellp", "hybrid")
+L2_FLUSH_BYTES = 512 << 20
+CACHE = os.environ.get("GKO_BENCH_CACHE", "/tmp/gko_gb300_bench_cache")
+
+
+# ------------------------------------------------------------------ inputs
+
+def load_workload(name):
+    """Synthetic workload, cached as .npz between runs of one session."""
+    os.makedirs(CACHE, exist_ok=True)
+    path = os.path.join(CACHE, name + ".npz")
+    if os.path.exists(path):
+        z = np.load(path)
+        return {k: (z[k].item() if z[k].ndim == 0 else z[k]) for k in z.files}
+    A = syn.workload(name)
+    keep = {k: v for k, v in A.items() if isinstance(v, (np.ndarray, int, float))}
+    np.savez(path + ".tmp.npz", **keep)
+    os.replace(path + ".tmp.npz", path)
+    return A
+
+
+# ------------------------------------------------------------- byte model
+
+def spmv_bytes(fmt, info, n, m, nnz, s_v=8):
+    """Algorithmic bytes of one y = A x (beta = 0: y written once, x read
+    once): values + indices + x + y.  Padding slots count (they are moved)."""
+    x_y = s_v * m + s_v * n
+    if fmt == "csr":
+        return (s_v + 4) * nnz + 4 * (n + 1) + x_y
+    if fmt == "coo":
+        return (s_v + 8) * nnz + x_y
+    if fmt == "ell":
+        return (s_v + 4) * info[6] + x_y
+    if fmt == "sellp":
+        return (s_v + 4) * info[6] + 4 * (2 * info[5] + 1) + x_y
+    if fmt == "hybrid":
+        return (s_v + 4) * info[4] * info[5] + (s_v + 8) * info[6] + x_y
+    raise KeyError(fmt)
+
+
+def kernel_launches(fmt, nnz_or_coo, tile=3840):
+    """Launches of this library per SpMV (load-balanced kernels add a fix-up
+    launch when they span more than one tile)."""
+    seg = 1 + (1 if nnz_or_coo > tile else 0)
+    return {"csr": seg, "coo": seg, "ell": 1, "sellp": 1, "hybrid": 1 + (seg if nnz_or_coo else 0)}[fmt]
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def profile_traffic():
+    """DRAM bytes per launch from the committed ncu summary, if present:
+    lines 'traffic <matrix>/<format> <bytes>'."""
+    out = {}
+    path = os.path.join(ROOT, "profiles", "spmv_dram_traffic.txt")
+    if os.path.exists(path):
+        for line in open(path):
+            parts = line.split()
+            if len(parts) == 3 and parts[0] == "traffic":
+                out[parts[1]] = float(parts[2])
+    return out
+
+
+# ----------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+
+    def __init__(self, index):
+        self.index = index
+        self.samples = []
+        self.proc = None
+
+    def __enter__(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            p = [s.strip() for s in line.split(",")]
+            if len(p) == 7:
+                self.samples.append(p)
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4) if s[3 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+# ------------------------------------------------------------ CPU baseline
+
+def cpu_baseline(mats, budget_s=20.0):
+    """The oracle's plain CSR SpMV (one host thread) on the sweep matrices,
+    as many passes as fit in the budget (at least one per matrix)."""
+    import oracle
+    oracle.build()
+    total_b, total_t, passes = 0.0, 0.0, 0
+    start = time.perf_counter()
+    while True:
+        for name, A in mats.items():
+            x = syn.vector(A["n_cols"], 99)
+            t0 = time.perf_counter()
+            oracle.spmv_csr(A, x)
+            total_t += time.perf_counter() - t0
+            total_b += spmv_bytes("csr", None, A["n_rows"], A["n_cols"], len(A["val"]))
+        passes += 1
+        if time.perf_counter() - start > budget_s:
+            break
+    return {"value": total_b / total_t / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "sample": "%d pass(es) of the oracle's single-thread CSR SpMV over the 4 sweep matrices" % passes}
+
+
+# -------------------------------------------------------------------- GPU
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def run_gpu(args):
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2011_08879_gb300 as gko
+
+    stream = torch.cuda.current_stream()
+    st = stream.cuda_stream
+    mats, handles = {}, {}
+    sweep = [m for m in SWEEP if not args.only or any(c.split("/")[0] == m for c in args.only.split(","))]
+    for name in sweep:
+        A = load_workload(name)
+        mats[name] = A
+        M = gko.Matrix(A, stream=st)
+        for f in FORMATS[1:]:
+            try:
+                M.convert(f, stream=st)
+            except gko.GkoError as e:
+                if e.status != gko.binding.ERR_FORMAT_TOO_LARGE:
+                    raise
+        handles[name] = M
+    # (matrix, format) cases with byte counts
+    cases = []
+    for name, M in handles.items():
+        A = mats[name]
+        n, m, nnz = A["n_rows"], A["n_cols"], len(A["val"])
+        for f in FORMATS:
+            if not M.has(f):
+                continue
+            if args.only and "%s/%s" % (name, f) not in args.only.split(","):
+                continue
+            info = M.info(f)
+            nb = spmv_bytes(f, info, n, m, nnz)
+            coo_part = nnz if f in ("csr", "coo") else (info[6] if f == "hybrid" else 0)
+            cases.append(dict(matrix=name, fmt=f, bytes=nb, flops=2 * nnz, launches=kernel_launches(f, coo_part)))
+    xs = {name: torch.from_numpy(syn.vector(mats[name]["n_cols"], 7)).to(dev) for name in sweep}
+    ys = {name: torch.empty(mats[name]["n_rows"], dtype=torch.float64, device=dev) for name in sweep}
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def one_step(times):
+        for c in cases:
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            handles[c["matrix"]].spmv(xs[c["matrix"]], ys[c["matrix"]], fmt=c["fmt"], stream=st)
+            e1.record(stream)
+            times.append((c, e0, e1))
+
+    for _ in range(args.warmup):
+        one_step([])
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    times = []
+    with ClockSampler(local) as clk:
+        w0 = time.perf_counter()
+        for _ in range(args.steps):
+            one_step(times)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - w0
+    if world > 1:
+        torch.distributed.barrier()
+    per_case = {}
+    for c, e0, e1 in times:
+        k = (c["matrix"], c["fmt"])
+        per_case.setdefault(k, []).append(e0.elapsed_time(e1) * 1e-3)
+    kern_s = sum(sum(v) for v in per_case.values())
+    bytes_tot = sum(c["bytes"] for c in cases) * args.steps
+    if world > 1:
+        t = torch.tensor([kern_s], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        kern_s = float(t.item())
+    value = bytes_tot * world / kern_s / 1e9
+    peak, peak_kind = measured_peaks()
+    detail = {}
+    for c in cases:
+        ts = per_case[(c["matrix"], c["fmt"])]
+        med = statistics.median(ts)
+        detail["%s/%s" % (c["matrix"], c["fmt"])] = {
+            "GBs": round(c["bytes"] / med / 1e9, 1), "pct_hbm": round(100 * c["bytes"] / med / 1e9 / peak, 1),
+            "GFLOPs": round(c["flops"] / med / 1e9, 1), "us": round(med * 1e6, 1)}
+    dom = max(cases, key=lambda c: sum(per_case[(c["matrix"], c["fmt"])]))
+    dts = per_case[(dom["matrix"], dom["fmt"])]
+    achieved = dom["bytes"] / (sum(dts) / len(dts)) / 1e9
+    traffic = profile_traffic().get("%s/%s" % (dom["matrix"], dom["fmt"]))
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": traffic,
+                "kernel": "%s SpMV on %s" % (dom["fmt"], dom["matrix"]), "peak_kind": peak_kind,
+                "bytes_per_launch": dom["bytes"]}
+
+    # end to end through gko_spmv_host with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        hx = {n: torch.from_numpy(syn.vector(mats[n]["n_cols"], 7)).pin_memory() for n in sweep}
+        hy = {n: torch.empty(mats[n]["n_rows"], dtype=torch.float64).pin_memory() for n in sweep}
+        for c in cases:  # warm-up (allocates the staging buffers)
+            handles[c["matrix"]].spmv_host(hx[c["matrix"]], hy[c["matrix"]], fmt=c["fmt"], stream=st)
+        t_e2e, h2d, d2h = 0.0, 0, 0
+        for _ in range(args.steps):
+            for c in cases:
+                flush.fill_(1.0)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                handles[c["matrix"]].spmv_host(hx[c["matrix"]], hy[c["matrix"]], fmt=c["fmt"], stream=st)
+                t_e2e += time.perf_counter() - t0
+                h2d += 8 * mats[c["matrix"]]["n_cols"]
+                d2h += 8 * mats[c["matrix"]]["n_rows"]
+        e2e = {"value": round(bytes_tot / t_e2e / 1e9, 1), "unit": "GB/s",
+               "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h // args.steps}
+
+    extra = {}
+    if not args.no_extras and rank == 0:
+        extra = run_extras(gko, torch, dev, st)
+    launches = sum(c["launches"] for c in cases) * args.steps
+    line = {
+        "metric": "FP64 SpMV GB/s (algorithmic bytes: values + indices + x + y), all formats x 4 sweep matrices",
+        "value": round(value, 1), "unit": "GB/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(kern_s / args.steps * 1e3, 4), "wall_ms_per_step_incl_flush": round(wall / args.steps * 1e3, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded SplitMix64 matrices shaped like the sweep configuration)",
+        "config": {"workload": "SpMV sweep: stencil27 128^3 (2.1M rows, 55.7M nnz), banded 4M (bw 64, 16/row), "
+                               "power-law 2M (Pareto 1.5, mean 20, max 20k), block-diagonal 1M (8x8)",
+                   "formats": "csr (load-balanced), coo, ell (refused where padding > 4 nnz), sellp (S=64), hybrid",
+                   "l2": "flushed (512 MB write) before every timed SpMV; inputs also larger than L2 except blockdiag",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": roofline, "gpu_launches": launches, "e2e": e2e, "detail": detail,
+    }
+    if rank == 0:
+        line["clocks"] = clk.summary()
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(mats, budget_s=args.cpu_budget)
+        line["extra"] = extra
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def _time_call(torch, fn):
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    r = fn()
+    torch.cuda.synchronize()
+    return time.perf_counter() - t0, r
+
+
+def run_extras(gko, torch, dev, st):
+    """CG time to 1e-10 (FP64 and mixed) and batched CG; outside the timed
+    SpMV region.  Each solve runs once untimed first."""
+    out = {}
+    L = load_workload("laplace2d_128")
+    n = L["n_rows"]
+    M = gko.Matrix(L, stream=st)
+    xt = torch.from_numpy(syn.vector(n, 1)).to(dev)
+    b = torch.empty_like(xt)
+    M.spmv(xt, b, stream=st)
+    for _ in range(2):
+        x = torch.zeros_like(b)
+        t, info = _time_call(torch, lambda: M.cg(b, x, tol=1e-10, maxit=10000, stream=st))
+    out["cg_laplace2d_128"] = {"s": round(t, 5), "iterations": info.iterations, "rel_residual": info.rel_residual,
+                               "status": info.status}
+    D = load_workload("diffusion7_160")
+    n = D["n_rows"]
+    M = gko.Matrix(D, stream=st)
+    xt = torch.from_numpy(syn.vector(n, 6)).to(dev)
+    b = torch.empty_like(xt)
+    M.spmv(xt, b, stream=st)
+    res = {}
+    for _ in range(2):
+        x = torch.zeros_like(b)
+        t, info = _time_call(torch, lambda: M.cg(b, x, tol=1e-10, maxit=20000, stream=st))
+    res["fp64"] = {"s": round(t, 4), "iterations": info.iterations, "rel_residual": info.rel_residual,
+                   "status": info.status}
+    for prec in ("fp32", "bf16"):
+        for _ in range(2):
+            x = torch.zeros_like(b)
+            t, info = _time_call(torch, lambda: M.cg_mixed(b, x, inner=prec, tol=1e-10, inner_tol=1e-3,
+                                                           maxit_outer=60, stream=st))
+        err = float(torch.linalg.vector_norm(x - xt) / torch.linalg.vector_norm(xt))
+        res[prec] = {"s": round(t, 4), "outer": info.outer_iterations, "inner_iterations": info.iterations,
+                     "rel_residual": info.rel_residual, "status": info.status, "rel_error_vs_x_true": err}
+    res["speedup_fp32_vs_fp64"] = round(res["fp64"]["s"] / res["fp32"]["s"], 3)
+    res["speedup_bf16_vs_fp64"] = round(res["fp64"]["s"] / res["bf16"]["s"], 3)
+    out["cg_diffusion7_160"] = res
+    B = load_workload("batched_4096")
+    G = gko.Batch(B, stream=st)
+    rhs = torch.from_numpy(B["rhs"]).to(dev)
+    x = torch.zeros_like(rhs)
+    best = G.autotune(rhs, x, stream=st)
+    for _ in range(2):
+        x = torch.zeros_like(rhs)
+        t, (s, infos) = _time_call(torch, lambda: G.cg(rhs, x, tol=1e-10, maxit=1000, stream=st))
+    its = [i.iterations for i in infos]
+    out["batched_cg_4096"] = {"s": round(t, 5), "status": s, "block_size": best,
+                              "max_rel_residual": max(i.rel_residual for i in infos),
+                              "iterations_mean": round(float(np.mean(its)), 2)}
+    return out
+
+
+# -------------------------------------------------------- reference arm
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    mats = {name: load_workload(name) for name in SWEEP}
+    # one step = the oracle's SpMV of every format on a bounded row sample of
+    # each matrix (the first rows holding ~2M entries)
+    sample = {}
+    for name, A in mats.items():
+        rp = A["row_ptr"]
+        r1 = int(np.searchsorted(rp, 2_000_000))
+        r1 = max(1, min(r1, A["n_rows"]))
+        sub = dict(n_rows=r1, n_cols=A["n_cols"], row_ptr=rp[:r1 + 1].copy(), col_idx=A["col_idx"][:rp[r1]],
+                   val=A["val"][:rp[r1]])
+        conv = {"csr": None, "coo": oracle.to_coo(sub), "sellp": oracle.to_sellp(sub, 64), "hybrid": oracle.to_hybrid(sub)}
+        if oracle.max_row_len(sub) * oracle.ell_n_pad(r1) <= max(4 * len(sub["val"]), 1 << 22):
+            conv["ell"] = oracle.to_ell(sub)
+        sample[name] = (sub, conv)
+
+    def step():
+        b = 0.0
+        for name, (sub, conv) in sample.items():
+            n, m, nnz = sub["n_rows"], sub["n_cols"], len(sub["val"])
+            x = syn.vector(m, 7)
+            for f, c in conv.items():
+                if f == "csr":
+                    oracle.spmv_csr(sub, x)
+                    info = None
+                elif f == "coo":
+                    oracle.spmv_coo(n, c, x)
+                    info = None
+                elif f == "ell":
+                    oracle.spmv_ell(n, c, x)
+                    info = [1, n, m, nnz, c["K"], c["n_pad"], c["K"] * c["n_pad"], 0]
+                elif f == "sellp":
+                    oracle.spmv_sellp(n, c, x)
+                    info = [1, n, m, nnz, 64, len(c["slice_len"]), len(c["col"]), 1]
+                else:
+                    oracle.spmv_hybrid(n, c, x)
+                    info = [1, n, m, nnz, c["K"], c["n_pad"], len(c["coo_val"]), 0]
+                b += spmv_bytes(f, info, n, m, nnz)
+        return b
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    tot = 0.0
+    for _ in range(args.steps):
+        tot += step()
+    dt = time.perf_counter() - t0
+    v = tot / dt / 1e9
+    line = {"impl": "reference", "metric": "FP64 SpMV GB/s (algorithmic bytes: values + indices + x + y), "
+            "all formats x 4 sweep matrices", "value": round(v, 3), "unit": "GB/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 2),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "SpMV sweep (same matrices); each step runs every format on the first rows "
+                                   "of each matrix holding ~2M stored entries"},
+            "cpu_baseline": {"value": round(v, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
+                             "sample": "first ~2M stored entries of each sweep matrix, every format"},
+            "e2e": {"value": round(v, 3), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gko", choices=["gko", "reference"])
+    ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--only", default="", help="comma list of matrix/format cases to time (profiling runs)")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "gko":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

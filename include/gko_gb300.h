@@ -1,0 +1,288 @@
+/*
+ * gko_gb300.h -- C ABI of the GB300 (sm_103a) sparse hot path: SpMV in the
+ * CSR, COO, ELL, SELL-P and hybrid ELL+COO formats, bit-exact conversions
+ * between them, conjugate gradients (FP64; mixed FP32/BF16 storage with FP64
+ * iterative refinement; batched over many small systems) and the learned
+ * format selector.
+ *
+ * The operations follow Cojean, Tsai and Anzt, "Ginkgo - A Math Library
+ * designed for Platform Portability": Sec. 6.1 (SpMV y = A x on sparse
+ * formats, whose COO and CSR byte bounds it states) and Sec. 6.2 (Krylov
+ * solvers built on SpMV).  Formats the paper names only through its
+ * citations follow their standard definitions (ELL and hybrid: Bell and
+ * Garland, SC'09; SELL-P: Anzt, Tomov and Dongarra, 2014).
+ *
+ * Conventions for every call:
+ *  - Return value: a gko_status code (GKO_OK == 0).  No call aborts, traps
+ *    or exits the process.  gko_last_error() gives a message for the last
+ *    failing call of the calling thread.
+ *  - Indices are int32, values IEEE binary64 unless stated.  Matrices are
+ *    square or rectangular (n_rows x n_cols).
+ *  - stream is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Calls are asynchronous on that stream unless documented as
+ *    synchronising (the solvers and the query/export calls).
+ *  - Vectors passed to compute calls are caller-owned DEVICE pointers
+ *    (except gko_spmv_host), 16-byte aligned is fastest but 8 suffices.
+ *  - A gko_matrix handle owns device copies of every format materialised
+ *    in it; the caller's input arrays are copied and may be freed after
+ *    the creating call returns.
+ *  - Every entry point needs a current CUDA device (the one of the stream);
+ *    a handle must be used on the device it was created on.
+ */
+#ifndef GKO_GB300_H
+#define GKO_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Storage formats. */
+enum {
+    GKO_FMT_CSR = 0,    /* row_ptr[n+1], col[nnz], val[nnz]; columns ascending per row */
+    GKO_FMT_COO = 1,    /* row[nnz], col[nnz], val[nnz]; sorted by (row, col) */
+    GKO_FMT_ELL = 2,    /* col[K*n_pad], val[K*n_pad]; slot (i,k) at k*n_pad+i; n_pad = n rounded up to 32;
+                           K = max row length; padding col = -1, val = +0.0 */
+    GKO_FMT_SELLP = 3,  /* slices of S rows; slice_len[n_slices] = slice width (max row length in the
+                           slice rounded up to the stride factor f); slice_set[n_slices+1] = exclusive
+                           prefix sum of widths; slot k of row s*S+l at (slice_set[s]+k)*S+l; padding
+                           col = -1, val = +0.0 */
+    GKO_FMT_HYBRID = 4, /* ELL part of width K_h (row i's first min(len_i, K_h) entries) + COO part
+                           (the remaining entries, sorted by (row, col)).  K_h minimises
+                           n_pad*K*(s_v+4) + overflow(K)*(s_v+8) bytes, s_v = 8, ties to smaller K */
+    GKO_FMT_AUTO = 5    /* learned selector's choice (gko_spmv only) */
+};
+
+/* Status codes. */
+enum {
+    GKO_OK = 0,
+    GKO_ERR_INVALID_ARG = 1,        /* null pointer, negative size, unknown enum value */
+    GKO_ERR_DIM_MISMATCH = 2,       /* sizes of the operands disagree */
+    GKO_ERR_FORMAT_UNAVAILABLE = 3, /* the format is not materialised in the handle */
+    GKO_ERR_FORMAT_TOO_LARGE = 4,   /* padded format would exceed its size limit */
+    GKO_ERR_OUT_OF_MEMORY = 5,      /* a device allocation failed */
+    GKO_ERR_NOT_CONVERGED = 6,      /* solver stopped at its iteration limit */
+    GKO_ERR_BREAKDOWN = 7,          /* p.q <= 0 or NaN in CG: matrix not SPD or data not finite */
+    GKO_ERR_INVALID_MATRIX = 8,     /* CSR input not valid (row_ptr not monotone, column out of range or
+                                       columns not strictly ascending within a row) */
+    GKO_ERR_TIMEOUT = 9,            /* a bounded device wait gave up (see gko_matrix_errors) */
+    GKO_ERR_CUDA = 10               /* a CUDA runtime call failed (message in gko_last_error) */
+};
+
+/* Value types. */
+enum { GKO_F64 = 0, GKO_F32 = 1, GKO_BF16 = 2 };
+
+/* Kernel configurations accepted by gko_spmv_config (the candidates of the
+ * exhaustive sweep / selector).  GKO_CFG_DEFAULT lets the library choose. */
+enum {
+    GKO_CFG_DEFAULT = 0,
+    GKO_CFG_CSR_SUBWARP_1 = 1,  /* CSR, classical: subwarp of 1,2,4,8,16,32 lanes per row */
+    GKO_CFG_CSR_SUBWARP_2 = 2,
+    GKO_CFG_CSR_SUBWARP_4 = 3,
+    GKO_CFG_CSR_SUBWARP_8 = 4,
+    GKO_CFG_CSR_SUBWARP_16 = 5,
+    GKO_CFG_CSR_SUBWARP_32 = 6,
+    GKO_CFG_CSR_NNZSPLIT = 7,   /* CSR, load-balanced equal-nnz split with segmented reduction */
+    GKO_CFG_CSR_BANDED = 8      /* CSR, x window staged in shared memory (banded matrices) */
+};
+
+typedef struct gko_matrix gko_matrix;
+typedef struct gko_batch gko_batch;
+
+/* Result of a solve.  status repeats the call's return code. */
+typedef struct {
+    int32_t iterations;       /* CG steps (products with A); for mixed CG: inner steps in total */
+    int32_t outer_iterations; /* mixed CG: refinement corrections; 0 otherwise */
+    double rel_residual;      /* true ||b - A x||_2 / ||b||_2 formed in FP64 at exit */
+    int32_t status;
+    int32_t reserved;
+} gko_solve_info;
+
+/* Message of the last failing call on this thread ("" if none). */
+const char* gko_last_error(void);
+/* Name of a status code. */
+const char* gko_status_string(int status);
+/* Library version string. */
+const char* gko_version(void);
+
+/* ----------------------------------------------------------- matrices */
+
+/* Create a handle from a CSR matrix (Sec. 6.1).  row_ptr[n_rows+1],
+ * col[nnz], val[nnz] are host pointers (on_device = 0) or device pointers
+ * (on_device = 1); they are copied.  The input is validated on the device
+ * (GKO_ERR_INVALID_MATRIX).  nnz == row_ptr[n_rows] must hold and fit int32.
+ * Synchronises the stream.  On success *out owns the CSR copy and the
+ * analysis data of the load-balanced kernels. */
+int gko_matrix_create_csr(int64_t n_rows, int64_t n_cols, int64_t nnz, const int32_t* row_ptr,
+                          const int32_t* col, const double* val, int on_device, void* stream,
+                          gko_matrix** out);
+
+/* Free a handle and every device array it owns (NULL is a no-op). */
+int gko_matrix_destroy(gko_matrix* A);
+
+/* Set SELL-P parameters used by the next conversion to SELL-P: slice size
+ * S in {1,2,4,8,16,32,64,128} (default 64) and stride factor f >= 1
+ * (default 1).  Also sets the padding limit of the padded formats: ELL
+ * (K*n_pad slots) and SELL-P (total slots) are refused with
+ * GKO_ERR_FORMAT_TOO_LARGE when their slots exceed
+ * max(ell_factor * nnz, 2^22) (ell_factor default 4; <= 0 keeps it).  The
+ * hybrid format chooses its ELL width itself and is never refused. */
+int gko_matrix_set_params(gko_matrix* A, int sellp_slice, int sellp_stride, double ell_factor);
+
+/* Materialise format dst from format src inside the handle (src must be
+ * materialised; one of them is CSR).  Indices and values are moved bit for
+ * bit; padding follows the format definitions above.  Runs on the device;
+ * synchronises the stream (sizes are read back). */
+int gko_convert(gko_matrix* A, int src, int dst, void* stream);
+
+/* Drop a materialised format (frees its arrays).  Dropping CSR is allowed
+ * only if another format remains; gko_convert(A, X, GKO_FMT_CSR) rebuilds
+ * it bit-exactly. */
+int gko_matrix_release(gko_matrix* A, int fmt);
+
+/* Sizes of a format: info[0] = 1 if materialised else 0, info[1] = n_rows,
+ * info[2] = n_cols, info[3] = nnz (stored entries, padding excluded),
+ * info[4] = K (ELL width; hybrid ELL width; SELL-P slice size S),
+ * info[5] = n_pad (ELL, hybrid) or n_slices (SELL-P), info[6] = total
+ * padded slots (ELL, SELL-P) or COO-part nnz (hybrid), info[7] = SELL-P
+ * stride factor.  info must hold 8 int64. */
+int gko_matrix_info(const gko_matrix* A, int fmt, int64_t* info);
+
+/* Copy one array of a materialised format into dst (host if to_host,
+ * else device), bytes = exact array size.  Arrays: CSR 0 row_ptr, 1 col,
+ * 2 val; COO 0 row, 1 col, 2 val; ELL 0 col, 1 val; SELL-P 0 slice_len,
+ * 1 slice_set, 2 col, 3 val; HYBRID 0 ell_col, 1 ell_val, 2 coo_row,
+ * 3 coo_col, 4 coo_val.  Synchronises the stream. */
+int gko_matrix_export(const gko_matrix* A, int fmt, int array, void* dst, int64_t bytes,
+                      int to_host, void* stream);
+
+/* Sticky device error bits of the handle's kernels (bit 0 bounded wait
+ * timed out, bit 1 bad index, bit 2 int32 overflow); clears them when
+ * clear != 0.  Synchronises the stream. */
+int gko_matrix_errors(gko_matrix* A, uint32_t* bits, int clear, void* stream);
+
+/* ---------------------------------------------------------------- SpMV */
+
+/* y = alpha * A * x + beta * y with the named format (Sec. 6.1).  x has
+ * n_cols entries, y n_rows (device pointers, caller-owned, not aliased).
+ * beta == 0 means y is not read (NaN/Inf in y are overwritten).  FP64
+ * arithmetic throughout; each y_i is within 1e-12 * (|alpha||A||x| +
+ * |beta||y|)_i of the exact result.  GKO_FMT_AUTO uses the selector loaded
+ * with gko_selector_load (CSR when none is loaded).  Asynchronous. */
+int gko_spmv(int fmt, const gko_matrix* A, const double* x, double* y, double alpha, double beta,
+             void* stream);
+
+/* gko_spmv with an explicit kernel configuration (GKO_CFG_*); used by the
+ * exhaustive sweep.  A configuration that does not apply to fmt returns
+ * GKO_ERR_INVALID_ARG. */
+int gko_spmv_config(int fmt, int config, const gko_matrix* A, const double* x, double* y,
+                    double alpha, double beta, void* stream);
+
+/* gko_spmv on HOST vectors: copies x (and y if beta != 0) host -> device,
+ * runs the product, copies y back.  x_host/y_host should be pinned for
+ * speed.  Device staging buffers are owned by the handle (allocated on first
+ * use).  Synchronises the stream. */
+int gko_spmv_host(int fmt, const gko_matrix* A, const double* x_host, double* y_host, double alpha,
+                  double beta, void* stream);
+
+/* ----------------------------------------------------------- solvers */
+
+/* Conjugate gradients (Hestenes-Stiefel; the Krylov solvers of Sec. 6.2)
+ * on A x = b using format fmt for the products.  b, x device vectors of
+ * n_rows (square A).  x holds the initial guess on entry and the solution
+ * on exit.  Stops when the recursive residual satisfies ||r|| <= tol ||b||
+ * and the FP64 true residual confirms it (up to four confirmations), at
+ * maxit (GKO_ERR_NOT_CONVERGED) or on breakdown (GKO_ERR_BREAKDOWN).
+ * ||b|| = 0 returns x = 0.  Work vectors are allocated stream-ordered for
+ * the call.  Synchronises the stream; info (host) may be NULL. */
+int gko_cg(const gko_matrix* A, int fmt, const double* b, double* x, double tol, int maxit,
+           void* stream, gko_solve_info* info);
+
+/* Mixed-precision CG with FP64 iterative refinement.  The inner CG runs on
+ * a copy of A stored in inner_dtype (GKO_F32 or GKO_BF16; off-diagonals
+ * rounded to nearest-even, the diagonal a_ii + sum_j(|rn(a_ij)| - |a_ij|)
+ * rounded up, which keeps diagonal dominance) with FP32 vectors and FP32
+ * accumulation, to relative residual inner_tol.  The outer loop forms
+ * r = b - A x, x += correction and the norms in FP64 and stops at
+ * ||r|| <= tol ||b||.  The low-precision copy is cached in the handle.
+ * Synchronises the stream. */
+int gko_cg_mixed(gko_matrix* A, int inner_dtype, const double* b, double* x, double tol,
+                 int maxit_outer, double inner_tol, int inner_maxit, void* stream,
+                 gko_solve_info* info);
+
+/* ------------------------------------------------------------- batched */
+
+/* Create a batch of count independent square systems: rows of system s
+ * are [row_off[s], row_off[s+1]) of one concatenated CSR (global row_ptr of
+ * row_off[count]+1 entries, column indices local to the system).  Host or
+ * device inputs as for gko_matrix_create_csr; copied.  Systems may have
+ * 1..4096 rows. */
+int gko_batch_create(int64_t count, const int64_t* row_off, const int32_t* row_ptr,
+                     const int32_t* col, const double* val, int on_device, void* stream,
+                     gko_batch** out);
+int gko_batch_destroy(gko_batch* B);
+
+/* Solve all systems of the batch by CG, one thread block per system taken
+ * from a device work queue (largest systems first), vectors in shared
+ * memory, launched as one persistent kernel inside a CUDA graph.
+ * block_size 0 = autotuned choice.  b, x device vectors of row_off[count]
+ * entries (x: initial guess in, solution out).  infos: host array of count
+ * entries or NULL.  Returns the worst status.  Synchronises the stream. */
+int gko_cg_batched(gko_batch* B, const double* b, double* x, double tol, int maxit, int block_size,
+                   void* stream, gko_solve_info* infos);
+
+/* Run the batched-CG autotuner: times every candidate block size on this
+ * batch and keeps the fastest for block_size 0.  *best receives it. */
+int gko_batch_autotune(gko_batch* B, const double* b, double* x, double tol, int maxit,
+                       void* stream, int* best);
+
+/* ------------------------------------------------------------ selector */
+
+/* The 12 matrix statistics the selector uses, computed on the device from
+ * the CSR arrays: log10 n, log10 max(nnz,1), mean/std/max/min row length,
+ * max/mean, fraction of empty rows, max|i-j|/n, mean|i-j|/n, fraction of
+ * rows storing their diagonal, SELL-P(32) slots/nnz.  out: 12 host doubles.
+ * Synchronises the stream. */
+int gko_features(const gko_matrix* A, double* out, void* stream);
+
+/* MLP 12 -> 64 -> 64 -> n_out (ReLU), FP32, parameters packed in one
+ * device array in the order W1[64x12], b1[64], W2[64x64], b2[64],
+ * W3[n_out x 64], b3[n_out] (row-major, output-major).
+ * gko_mlp_param_count gives the packed length. */
+int64_t gko_mlp_param_count(int n_out);
+
+/* Forward pass for a batch: X[batch x 12] -> out[batch x n_out] (device,
+ * FP32, row-major). */
+int gko_mlp_forward(const float* params, int n_out, const float* X, int batch, float* out,
+                    void* stream);
+
+/* Loss and gradient of the masked mean squared error
+ * sum M (out - Y)^2 / sum M over a batch (X[batch x 12], Y and M
+ * [batch x n_out], device FP32).  grad receives d loss / d params (packed
+ * like params); loss (device, 1 float) may be NULL. */
+int gko_mlp_grad(const float* params, int n_out, const float* X, const float* Y, const float* M,
+                 int batch, float* grad, float* loss, void* stream);
+
+/* One Adam step on the packed parameters: m, v are the moment arrays
+ * (same length, zero at t = 1), t is the 1-based step number. */
+int gko_mlp_adam(float* params, const float* grad, float* m, float* v, int64_t count, int t,
+                 float lr, float beta1, float beta2, float eps, void* stream);
+
+/* Install a trained selector used by GKO_FMT_AUTO: packed FP32 params
+ * (host), feature normalisation mean[12], scale[12] (host doubles), and
+ * the n_out (format, config) pairs the outputs stand for (host ints,
+ * fmts[i], cfgs[i]).  The prediction is argmin of the outputs. */
+int gko_selector_load(const float* params_host, int n_out, const double* feat_mean,
+                      const double* feat_scale, const int* fmts, const int* cfgs);
+
+/* The selector's choice for A (features computed on the device, cached in
+ * the handle).  Synchronises the stream. */
+int gko_select_format(gko_matrix* A, int* fmt, int* config, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GKO_GB300_H */

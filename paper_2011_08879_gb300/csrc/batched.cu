@@ -1,0 +1,391 @@
+// Batched CG: many independent small SPD systems solved by one persistent
+// kernel.  Each thread block repeatedly takes the next system from a device
+// work queue (systems ordered by decreasing size, so the largest start
+// first and the tail is short), keeps x, r, p, q of that system in shared
+// memory, streams the system's CSR through L1/L2 every step and runs the
+// Hestenes-Stiefel recurrence (the Krylov solver of the paper's Sec. 6.2)
+// to its own tolerance.  Dots are block-wide reductions in a fixed order;
+// there is no inter-block communication except the queue ticket.  The
+// queue reset and the kernel are replayed as one CUDA graph.
+#include <algorithm>
+#include <cmath>
+#include <numeric>
+#include <vector>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace gko {
+
+constexpr int kBatchMaxRows = 4096;
+
+template <int BS>
+__device__ __forceinline__ double block_dot_sum(double v, double* red)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int o = 16; o; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    __syncthreads();  // red may still be read by the previous call
+    if (lane == 0) red[w] = v;
+    __syncthreads();
+    double t = 0.0;
+    for (int i = 0; i < BS / 32; ++i) t += red[i];  // every thread, same order
+    return t;
+}
+
+// q = A v for the rows of one system (thread per row, local columns)
+__device__ __forceinline__ void sys_spmv(int n, int bs, const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
+                                         const double* __restrict__ val, int32_t base, const double* v, double* q)
+{
+    for (int i = threadIdx.x; i < n; i += bs) {
+        double acc = 0.0;
+        const int32_t k1 = rp[i + 1] - base;
+        for (int32_t k = rp[i] - base; k < k1; ++k) acc = fma(val[k], v[col[k]], acc);
+        q[i] = acc;
+    }
+}
+
+template <int BS>
+__global__ void __launch_bounds__(BS)
+    batched_cg_kernel(int64_t count, const int64_t* __restrict__ row_off, const int32_t* __restrict__ row_ptr,
+                      const int32_t* __restrict__ col_all, const double* __restrict__ val_all,
+                      const int32_t* __restrict__ order, int32_t* queue, const double* __restrict__ b_all,
+                      double* __restrict__ x_all, double tol, int maxit, double* __restrict__ res_out,
+                      int32_t* __restrict__ it_out, int32_t* __restrict__ st_out, int max_rows)
+{
+    extern __shared__ __align__(16) double sm[];
+    double* xs = sm;
+    double* rs = xs + max_rows;
+    double* ps = rs + max_rows;
+    double* qs = ps + max_rows;
+    __shared__ double red[BS / 32];
+    __shared__ int s_next;
+
+    while (true) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_next = atomicAdd(queue, 1);
+        __syncthreads();
+        const int qi = s_next;
+        if (qi >= count) return;
+        const int sys = order[qi];
+        const int64_t r0 = row_off[sys];
+        const int n = static_cast<int>(row_off[sys + 1] - r0);
+        const int32_t* rp = row_ptr + r0;
+        const int32_t base = rp[0];
+        const int32_t* col = col_all + base;
+        const double* val = val_all + base;
+        const double* b = b_all + r0;
+        double* x = x_all + r0;
+
+        double bb = 0.0;
+        for (int i = threadIdx.x; i < n; i += BS) {
+            xs[i] = x[i];
+            bb = fma(b[i], b[i], bb);
+        }
+        const double bnorm = sqrt(block_dot_sum<BS>(bb, red));
+        __syncthreads();
+        if (bnorm == 0.0) {
+            for (int i = threadIdx.x; i < n; i += BS) x[i] = 0.0;
+            if (threadIdx.x == 0) {
+                res_out[sys] = 0.0;
+                it_out[sys] = 0;
+                st_out[sys] = GKO_OK;
+            }
+            continue;
+        }
+        // r = b - A x, p = r
+        sys_spmv(n, BS, rp, col, val, base, xs, qs);
+        __syncthreads();
+        double rr = 0.0;
+        for (int i = threadIdx.x; i < n; i += BS) {
+            const double ri = b[i] - qs[i];
+            rs[i] = ri;
+            ps[i] = ri;
+            rr = fma(ri, ri, rr);
+        }
+        double rho = block_dot_sum<BS>(rr, red);
+        int status = GKO_ERR_NOT_CONVERGED, iter = 0, checks = 0;
+        double true_res = -1.0;
+        bool stop = sqrt(rho) <= tol * bnorm;
+        if (stop) status = GKO_OK;
+        while (!stop && iter < maxit) {
+            __syncthreads();
+            sys_spmv(n, BS, rp, col, val, base, ps, qs);
+            __syncthreads();
+            double pq = 0.0;
+            for (int i = threadIdx.x; i < n; i += BS) pq = fma(ps[i], qs[i], pq);
+            pq = block_dot_sum<BS>(pq, red);
+            ++iter;
+            if (!(pq > 0.0)) {
+                status = GKO_ERR_BREAKDOWN;
+                break;
+            }
+            const double alpha = rho / pq;
+            double rn = 0.0;
+            for (int i = threadIdx.x; i < n; i += BS) {
+                xs[i] = fma(alpha, ps[i], xs[i]);
+                const double ri = fma(-alpha, qs[i], rs[i]);
+                rs[i] = ri;
+                rn = fma(ri, ri, rn);
+            }
+            const double rho_new = block_dot_sum<BS>(rn, red);
+            if (!(rho_new == rho_new)) {
+                status = GKO_ERR_BREAKDOWN;
+                break;
+            }
+            if (sqrt(rho_new) <= tol * bnorm) {
+                // confirm with the true residual b - A x
+                __syncthreads();
+                sys_spmv(n, BS, rp, col, val, base, xs, qs);
+                __syncthreads();
+                double tt = 0.0;
+                for (int i = threadIdx.x; i < n; i += BS) {
+                    const double ti = b[i] - qs[i];
+                    tt = fma(ti, ti, tt);
+                }
+                true_res = sqrt(block_dot_sum<BS>(tt, red)) / bnorm;
+                ++checks;
+                if (true_res <= tol) {
+                    status = GKO_OK;
+                    break;
+                }
+                if (checks >= 4) break;
+                true_res = -1.0;
+            }
+            const double beta = rho_new / rho;
+            rho = rho_new;
+            __syncthreads();
+            for (int i = threadIdx.x; i < n; i += BS) ps[i] = fma(beta, ps[i], rs[i]);
+        }
+        __syncthreads();
+        if (true_res < 0.0) {
+            sys_spmv(n, BS, rp, col, val, base, xs, qs);
+            __syncthreads();
+            double tt = 0.0;
+            for (int i = threadIdx.x; i < n; i += BS) {
+                const double ti = b[i] - qs[i];
+                tt = fma(ti, ti, tt);
+            }
+            true_res = sqrt(block_dot_sum<BS>(tt, red)) / bnorm;
+        }
+        for (int i = threadIdx.x; i < n; i += BS) x[i] = xs[i];
+        if (threadIdx.x == 0) {
+            res_out[sys] = true_res;
+            it_out[sys] = iter;
+            st_out[sys] = status;
+        }
+    }
+}
+
+struct BatchLaunch {
+    const void* fn;
+    int bs;
+};
+
+template <int BS>
+static int launch_batched(gko_batch* B, const double* b, double* x, double tol, int maxit, cudaStream_t st)
+{
+    const size_t smem = 4 * static_cast<size_t>(B->max_rows) * sizeof(double);
+    GKO_CUDA(cudaFuncSetAttribute(batched_cg_kernel<BS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  static_cast<int>(smem)));
+    int per_sm = 0, sms = 0, dev = 0;
+    GKO_CUDA(cudaGetDevice(&dev));
+    GKO_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    GKO_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_cg_kernel<BS>, BS, smem));
+    if (per_sm < 1) return fail(GKO_ERR_INVALID_ARG, "batched CG: block does not fit on an SM");
+    const int64_t grid = std::min<int64_t>(static_cast<int64_t>(per_sm) * sms, B->count);
+    GKO_CUDA(cudaMemsetAsync(B->queue, 0, sizeof(int32_t), st));
+    batched_cg_kernel<BS><<<static_cast<unsigned>(std::max<int64_t>(grid, 1)), BS, smem, st>>>(
+        B->count, B->row_off, B->row_ptr, B->col, B->val, B->order, B->queue, b, x, tol, maxit, B->res, B->iters,
+        B->status, B->max_rows);
+    GKO_CUDA(cudaGetLastError());
+    return GKO_OK;
+}
+
+static int launch_any(gko_batch* B, int bs, const double* b, double* x, double tol, int maxit, cudaStream_t st)
+{
+    switch (bs) {
+        case 64: return launch_batched<64>(B, b, x, tol, maxit, st);
+        case 128: return launch_batched<128>(B, b, x, tol, maxit, st);
+        case 256: return launch_batched<256>(B, b, x, tol, maxit, st);
+        case 512: return launch_batched<512>(B, b, x, tol, maxit, st);
+        case 1024: return launch_batched<1024>(B, b, x, tol, maxit, st);
+    }
+    return fail(GKO_ERR_INVALID_ARG, "block_size must be 0, 64, 128, 256, 512 or 1024");
+}
+
+// run [queue reset + kernel] as a captured CUDA graph
+static int run_graph(gko_batch* B, int bs, const double* b, double* x, double tol, int maxit, cudaStream_t st)
+{
+    cudaStream_t cap;
+    GKO_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ge = nullptr;
+    int s = GKO_OK;
+    cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        s = launch_any(B, bs, b, x, tol, maxit, cap);
+        e = cudaStreamEndCapture(cap, &g);
+    }
+    if (e == cudaSuccess && s == GKO_OK) e = cudaGraphInstantiate(&ge, g, 0);
+    if (e == cudaSuccess && s == GKO_OK) e = cudaGraphLaunch(ge, st);
+    if (ge) cudaGraphExecDestroy(ge);
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cap);
+    if (s != GKO_OK) return s;
+    if (e != cudaSuccess) return cuda_fail(e, "batched CG graph");
+    return GKO_OK;
+}
+
+}  // namespace gko
+
+using namespace gko;
+
+extern "C" {
+
+int gko_batch_create(int64_t count, const int64_t* row_off, const int32_t* row_ptr, const int32_t* col,
+                     const double* val, int on_device, void* stream, gko_batch** out)
+{
+    if (!out || !row_off || !row_ptr) return fail(GKO_ERR_INVALID_ARG, "NULL argument");
+    *out = nullptr;
+    if (count < 1 || count > INT32_MAX) return fail(GKO_ERR_INVALID_ARG, "count must be in [1, 2^31)");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost;
+    std::vector<int64_t> ro(count + 1);
+    GKO_CUDA(cudaMemcpy(ro.data(), row_off, (count + 1) * sizeof(int64_t), kind));
+    if (ro[0] != 0) return fail(GKO_ERR_INVALID_ARG, "row_off[0] must be 0");
+    int max_rows = 0;
+    for (int64_t s = 0; s < count; ++s) {
+        const int64_t n = ro[s + 1] - ro[s];
+        if (n < 1 || n > kBatchMaxRows) return fail(GKO_ERR_INVALID_ARG, "systems must have 1..4096 rows");
+        max_rows = std::max<int>(max_rows, static_cast<int>(n));
+    }
+    const int64_t n_rows = ro[count];
+    if (n_rows >= INT32_MAX) return fail(GKO_ERR_INVALID_ARG, "too many rows");
+    int32_t last = 0;
+    GKO_CUDA(cudaMemcpy(&last, row_ptr + n_rows, sizeof(int32_t), kind));
+    const int64_t nnz = last;
+    if (nnz > 0 && (!col || !val)) return fail(GKO_ERR_INVALID_ARG, "NULL array");
+    gko_batch* B = new gko_batch();
+    auto cleanup = [&](int s) {
+        gko_batch_destroy(B);
+        return s;
+    };
+    B->count = count;
+    B->n_rows = n_rows;
+    B->nnz = nnz;
+    B->max_rows = max_rows;
+    GKO_CUDA(cudaGetDevice(&B->device));
+    int s;
+    if ((s = dev_alloc(&B->row_off, count + 1)) || (s = dev_alloc(&B->row_ptr, n_rows + 1)) ||
+        (s = dev_alloc(&B->col, nnz)) || (s = dev_alloc(&B->val, nnz)) || (s = dev_alloc(&B->order, count)) ||
+        (s = dev_alloc(&B->queue, 1)) || (s = dev_alloc(&B->res, count)) || (s = dev_alloc(&B->iters, count)) ||
+        (s = dev_alloc(&B->status, count)) || (s = dev_alloc(&B->d_err, 1)))
+        return cleanup(s);
+    const cudaMemcpyKind k2 = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    // work-queue order: decreasing size, ties by index
+    std::vector<int32_t> ord(count);
+    std::iota(ord.begin(), ord.end(), 0);
+    std::stable_sort(ord.begin(), ord.end(),
+                     [&](int32_t a, int32_t c) { return ro[a + 1] - ro[a] > ro[c + 1] - ro[c]; });
+    cudaError_t e = cudaMemcpyAsync(B->row_off, ro.data(), (count + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(B->row_ptr, row_ptr, (n_rows + 1) * sizeof(int32_t), k2, st);
+    if (e == cudaSuccess && nnz) e = cudaMemcpyAsync(B->col, col, nnz * sizeof(int32_t), k2, st);
+    if (e == cudaSuccess && nnz) e = cudaMemcpyAsync(B->val, val, nnz * sizeof(double), k2, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(B->order, ord.data(), count * sizeof(int32_t), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cleanup(cuda_fail(e, "copying the batch"));
+    if ((s = validate_csr(n_rows, max_rows, nnz, B->row_ptr, B->col, st)) != GKO_OK) return cleanup(s);
+    *out = B;
+    return GKO_OK;
+}
+
+int gko_batch_destroy(gko_batch* B)
+{
+    if (!B) return GKO_OK;
+    dev_free(B->row_off);
+    dev_free(B->row_ptr);
+    dev_free(B->col);
+    dev_free(B->val);
+    dev_free(B->order);
+    dev_free(B->queue);
+    dev_free(B->res);
+    dev_free(B->iters);
+    dev_free(B->status);
+    dev_free(B->d_err);
+    delete B;
+    return GKO_OK;
+}
+
+int gko_cg_batched(gko_batch* B, const double* b, double* x, double tol, int maxit, int block_size, void* stream,
+                   gko_solve_info* infos)
+{
+    if (!B || !b || !x) return fail(GKO_ERR_INVALID_ARG, "NULL argument");
+    if (!(tol >= 0.0) || maxit < 0) return fail(GKO_ERR_INVALID_ARG, "tol must be >= 0 and maxit >= 0");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int bs = block_size ? block_size : (B->best_block ? B->best_block : 256);
+    GKO_TRY(run_graph(B, bs, b, x, tol, maxit, st));
+    std::vector<double> res(B->count);
+    std::vector<int32_t> it(B->count), stv(B->count);
+    GKO_CUDA(cudaMemcpyAsync(res.data(), B->res, B->count * sizeof(double), cudaMemcpyDeviceToHost, st));
+    GKO_CUDA(cudaMemcpyAsync(it.data(), B->iters, B->count * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    GKO_CUDA(cudaMemcpyAsync(stv.data(), B->status, B->count * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    GKO_CUDA(cudaStreamSynchronize(st));
+    int worst = GKO_OK;
+    for (int64_t s = 0; s < B->count; ++s) {
+        if (stv[s] != GKO_OK && (worst == GKO_OK || stv[s] == GKO_ERR_BREAKDOWN)) worst = stv[s];
+        if (infos) {
+            infos[s].iterations = it[s];
+            infos[s].outer_iterations = 0;
+            infos[s].rel_residual = res[s];
+            infos[s].status = stv[s];
+            infos[s].reserved = 0;
+        }
+    }
+    if (worst != GKO_OK) set_error("batched CG: some systems did not converge");
+    return worst;
+}
+
+int gko_batch_autotune(gko_batch* B, const double* b, double* x, double tol, int maxit, void* stream, int* best)
+{
+    if (!B || !b || !x || !best) return fail(GKO_ERR_INVALID_ARG, "NULL argument");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    double* x0 = nullptr;
+    GKO_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&x0), B->n_rows * sizeof(double), st));
+    GKO_CUDA(cudaMemcpyAsync(x0, x, B->n_rows * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    cudaEvent_t e0, e1;
+    GKO_CUDA(cudaEventCreate(&e0));
+    GKO_CUDA(cudaEventCreate(&e1));
+    float best_ms = 0.0f;
+    int best_bs = 0;
+    const int cands[] = {64, 128, 256, 512, 1024};
+    for (int bs : cands) {
+        float tot = 0.0f;
+        int s = GKO_OK;
+        for (int rep = 0; rep < 3 && s == GKO_OK; ++rep) {
+            GKO_CUDA(cudaMemcpyAsync(x, x0, B->n_rows * sizeof(double), cudaMemcpyDeviceToDevice, st));
+            GKO_CUDA(cudaEventRecord(e0, st));
+            s = run_graph(B, bs, b, x, tol, maxit, st);
+            GKO_CUDA(cudaEventRecord(e1, st));
+            GKO_CUDA(cudaEventSynchronize(e1));
+            float ms = 0.0f;
+            GKO_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+            if (rep > 0) tot += ms;  // first run warms up
+        }
+        if (s != GKO_OK) continue;
+        if (best_bs == 0 || tot < best_ms) {
+            best_ms = tot;
+            best_bs = bs;
+        }
+    }
+    GKO_CUDA(cudaMemcpyAsync(x, x0, B->n_rows * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    GKO_CUDA(cudaFreeAsync(x0, st));
+    GKO_CUDA(cudaStreamSynchronize(st));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (!best_bs) return fail(GKO_ERR_INVALID_ARG, "no block size could be launched");
+    B->best_block = best_bs;
+    *best = best_bs;
+    return GKO_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,624 @@
+// Conjugate gradients (Hestenes-Stiefel 1952), the Krylov solver the
+// paper's Sec. 6.2 runs on SpMV, plus mixed-precision CG with FP64
+// iterative refinement.
+//
+// One CG step is four launches:
+//   q = A p                                  (format kernel of choice)
+//   alpha = rho / (p.q)                      (dot with grid reduction)
+//   x += alpha p, r -= alpha q, rho' = r.r   (fused update + grid reduction)
+//   p = r + beta p                           (beta = rho'/rho)
+// Each dot is one grid-wide reduction: every block writes its partial, the
+// last block to finish (atomic ticket) sums the partials in index order, so
+// results do not depend on block scheduling.  Scalars stay on the device.
+// The loop body is captured once into a CUDA graph under a conditional
+// WHILE node; the reduction epilogue clears the condition when the solve
+// stops, so the host waits once per solve (plus once per true-residual
+// confirmation) instead of once per step.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+
+#include "common.cuh"
+#include "internal.h"
+#include "segmented.cuh"
+
+namespace gko {
+
+int launch_seg(int64_t n_rows, int64_t nnz, const int32_t* row_ptr, const int32_t* rows, const int32_t* col,
+               const double* val, const int32_t* thr_row, const SegArrays& sa, const double* x, double* y,
+               double alpha, double beta, uint32_t* err, bool coo, cudaStream_t st, bool accumulate);
+
+constexpr int kRedThreads = 256;
+constexpr int kRedBlocks = 152 * 4;
+
+// Device-resident solver scalars.
+struct SolverState {
+    double rho;       // r.r of the current residual
+    double rho0;      // r.r at the start (inner solves stop relative to it)
+    double pq;        // p.q
+    double alpha, beta;
+    double stop_ref;  // ||b|| (outer CG) or sqrt(rho0) (inner CG)
+    double tol;
+    double dot_out;   // result of a plain dot
+    int32_t iter, maxit, done, status, conv, rel_inner;
+    uint32_t ticket;
+};
+
+enum { kDotStore = 0, kDotRhoInit = 1, kDotPQ = 2 };
+
+__device__ __forceinline__ double block_sum(double v, double* sh)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int o = 16; o; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (w == 0) {
+        r = lane < static_cast<int>(blockDim.x >> 5) ? sh[lane] : 0.0;
+        for (int o = 16; o; o >>= 1) r += __shfl_down_sync(0xffffffffu, r, o);
+    }
+    __syncthreads();
+    return r;  // valid in thread 0
+}
+
+// Grid-wide sum: partials by block, last block reduces them in index order
+// and runs epi(total) on thread 0.  Returns true in that thread.
+template <typename Epi>
+__device__ __forceinline__ void grid_sum(double v, double* part, uint32_t* ticket, Epi epi)
+{
+    __shared__ double sh[32];
+    __shared__ bool last;
+    const double b = block_sum(v, sh);
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = b;
+        __threadfence();
+        last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < static_cast<int>(gridDim.x); i += blockDim.x) acc += __ldcg(part + i);
+    const double tot = block_sum(acc, sh);
+    if (threadIdx.x == 0) {
+        *ticket = 0;
+        epi(tot);
+    }
+}
+
+__device__ __forceinline__ void stop_loop(SolverState* s, cudaGraphConditionalHandle h)
+{
+    s->done = 1;
+    if (h) cudaGraphSetConditional(h, 0);
+}
+
+// dot(a, b) with per-thread accumulation in T, cross-thread in FP64
+template <typename T, int kMode>
+__global__ void __launch_bounds__(kRedThreads)
+    dot_kernel(int64_t n, const T* __restrict__ a, const T* __restrict__ b, SolverState* s, double* part,
+               cudaGraphConditionalHandle h)
+{
+    T acc = T(0);
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(kRedThreads) + threadIdx.x; i < n;
+         i += static_cast<int64_t>(gridDim.x) * kRedThreads)
+        acc = fma(a[i], b[i], acc);
+    grid_sum(static_cast<double>(acc), part, &s->ticket, [&](double tot) {
+        if (kMode == kDotStore) {
+            s->dot_out = tot;
+        } else if (kMode == kDotRhoInit) {
+            s->rho = tot;
+            s->rho0 = tot;
+            if (s->rel_inner) s->stop_ref = sqrt(tot);
+            if (sqrt(tot) <= s->tol * s->stop_ref) {
+                s->conv = 1;
+                s->status = GKO_OK;
+                s->done = 1;
+            }
+        } else {  // p.q -> alpha
+            if (s->done || s->iter >= s->maxit) {
+                // already stopped (e.g. converged before the first step):
+                // clear the loop condition so the WHILE node always ends
+                stop_loop(s, h);
+                return;
+            }
+            s->pq = tot;
+            s->iter += 1;
+            if (!(tot > 0.0)) {
+                s->status = GKO_ERR_BREAKDOWN;
+                stop_loop(s, h);
+            } else {
+                s->alpha = s->rho / tot;
+            }
+        }
+    });
+}
+
+// x += alpha p; r -= alpha q; rho' = r.r; beta = rho'/rho; stop tests
+template <typename T>
+__global__ void __launch_bounds__(kRedThreads)
+    update_kernel(int64_t n, T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p,
+                  const T* __restrict__ q, SolverState* s, double* part, cudaGraphConditionalHandle h)
+{
+    if (s->done) return;  // only the last block of the previous kernel can set it
+    const T alpha = static_cast<T>(s->alpha);
+    T acc = T(0);
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(kRedThreads) + threadIdx.x; i < n;
+         i += static_cast<int64_t>(gridDim.x) * kRedThreads) {
+        x[i] = fma(alpha, p[i], x[i]);
+        const T ri = fma(-alpha, q[i], r[i]);
+        r[i] = ri;
+        acc = fma(ri, ri, acc);
+    }
+    grid_sum(static_cast<double>(acc), part, &s->ticket, [&](double rho_new) {
+        if (!(rho_new == rho_new)) {
+            s->status = GKO_ERR_BREAKDOWN;
+            stop_loop(s, h);
+            return;
+        }
+        s->beta = rho_new / s->rho;
+        s->rho = rho_new;
+        if (sqrt(rho_new) <= s->tol * s->stop_ref) {
+            s->conv = 1;
+            s->status = GKO_OK;
+            stop_loop(s, h);
+        } else if (s->iter >= s->maxit) {
+            s->status = GKO_ERR_NOT_CONVERGED;
+            stop_loop(s, h);
+        }
+    });
+}
+
+// p = r + beta p
+template <typename T>
+__global__ void __launch_bounds__(kRedThreads)
+    pupdate_kernel(int64_t n, T* __restrict__ p, const T* __restrict__ r, const SolverState* s, int force)
+{
+    if (s->done && !force) return;
+    const T beta = static_cast<T>(s->beta);
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(kRedThreads) + threadIdx.x; i < n;
+         i += static_cast<int64_t>(gridDim.x) * kRedThreads)
+        p[i] = fma(beta, p[i], r[i]);
+}
+
+static int red_grid(int64_t n)
+{
+    return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(kRedBlocks, (n + kRedThreads - 1) / kRedThreads)));
+}
+
+// ----------------------------------------------------------- workspace
+
+struct Workspace {
+    cudaStream_t st;
+    void* ptrs[16] = {nullptr};
+    int n = 0;
+    explicit Workspace(cudaStream_t s) : st(s) {}
+    template <typename T>
+    int get(T** p, int64_t count)
+    {
+        *p = nullptr;
+        cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(p), std::max<int64_t>(count, 1) * sizeof(T), st);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync (solver workspace)");
+        ptrs[n++] = *p;
+        return GKO_OK;
+    }
+    ~Workspace()
+    {
+        for (int i = 0; i < n; ++i) cudaFreeAsync(ptrs[i], st);
+    }
+};
+
+struct GraphHolder {
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    ~GraphHolder()
+    {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (g) cudaGraphDestroy(g);
+    }
+};
+
+// Build a graph whose single node is WHILE(cond){ body(handle, cap) }.
+// The body is captured on a private non-blocking stream `cap` (capture is
+// not allowed on the legacy default stream the caller may be using); the
+// instantiated graph is then launched on the caller's stream.
+template <typename Body>
+static int build_while_graph(GraphHolder* gh, Body body)
+{
+    GKO_CUDA(cudaGraphCreate(&gh->g, 0));
+    cudaGraphConditionalHandle handle;
+    GKO_CUDA(cudaGraphConditionalHandleCreate(&handle, gh->g, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams params = {};
+    params.type = cudaGraphNodeTypeConditional;
+    params.conditional.handle = handle;
+    params.conditional.type = cudaGraphCondTypeWhile;
+    params.conditional.size = 1;
+    cudaGraphNode_t node;
+    GKO_CUDA(cudaGraphAddNode(&node, gh->g, nullptr, nullptr, 0, &params));
+    cudaGraph_t bodyg = params.conditional.phGraph_out[0];
+    cudaStream_t cap;
+    GKO_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    cudaError_t e = cudaStreamBeginCaptureToGraph(cap, bodyg, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    int s = GKO_OK;
+    if (e == cudaSuccess) {
+        s = body(handle, cap);
+        cudaGraph_t captured = nullptr;
+        e = cudaStreamEndCapture(cap, &captured);
+    }
+    cudaStreamDestroy(cap);
+    if (s != GKO_OK) return s;
+    if (e != cudaSuccess) return cuda_fail(e, "capturing the CG body");
+    GKO_CUDA(cudaGraphInstantiate(&gh->exec, gh->g, 0));
+    return GKO_OK;
+}
+
+static int read_state(SolverState* h, const SolverState* d, cudaStream_t st)
+{
+    GKO_CUDA(cudaMemcpyAsync(h, d, sizeof(SolverState), cudaMemcpyDeviceToHost, st));
+    GKO_CUDA(cudaStreamSynchronize(st));
+    return GKO_OK;
+}
+
+static int write_state(SolverState* d, const SolverState* h, cudaStream_t st)
+{
+    GKO_CUDA(cudaMemcpyAsync(d, h, sizeof(SolverState), cudaMemcpyHostToDevice, st));
+    return GKO_OK;
+}
+
+static int spmv_fmt(const gko_matrix* A, int fmt, const double* x, double* y, double alpha, double beta,
+                    cudaStream_t st)
+{
+    switch (fmt) {
+        case GKO_FMT_CSR: return spmv_csr(A, GKO_CFG_DEFAULT, x, y, alpha, beta, st);
+        case GKO_FMT_COO: return spmv_coo(A, A->coo, x, y, alpha, beta, st);
+        case GKO_FMT_ELL: return spmv_ell(A, A->ell, x, y, alpha, beta, st);
+        case GKO_FMT_SELLP: return spmv_sellp(A, x, y, alpha, beta, st);
+        case GKO_FMT_HYBRID: return spmv_hybrid(A, x, y, alpha, beta, st);
+    }
+    return fail(GKO_ERR_INVALID_ARG, "unknown format");
+}
+
+// ||b - A x|| / ||b|| with the residual in FP64 (t is scratch of n)
+static int true_residual(const gko_matrix* A, int fmt, const double* b, const double* x, double* t,
+                         SolverState* ds, double* part, double bnorm, cudaStream_t st, double* out)
+{
+    const int64_t n = A->n_rows;
+    GKO_CUDA(cudaMemcpyAsync(t, b, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    GKO_TRY(spmv_fmt(A, fmt, x, t, -1.0, 1.0, st));
+    dot_kernel<double, kDotStore><<<red_grid(n), kRedThreads, 0, st>>>(n, t, t, ds, part, 0);
+    GKO_CUDA(cudaGetLastError());
+    double d = 0.0;
+    GKO_CUDA(cudaMemcpyAsync(&d, &ds->dot_out, sizeof(double), cudaMemcpyDeviceToHost, st));
+    GKO_CUDA(cudaStreamSynchronize(st));
+    *out = bnorm > 0.0 ? std::sqrt(d) / bnorm : std::sqrt(d);
+    return GKO_OK;
+}
+
+static void fill_info(gko_solve_info* info, int iters, int outer, double res, int status)
+{
+    if (!info) return;
+    info->iterations = iters;
+    info->outer_iterations = outer;
+    info->rel_residual = res;
+    info->status = status;
+    info->reserved = 0;
+}
+
+// -------------------------------------------------------------- FP64 CG
+
+int cg_solve(const gko_matrix* A, int fmt, const double* b, double* x, double tol, int maxit, cudaStream_t st,
+             gko_solve_info* info)
+{
+    const int64_t n = A->n_rows;
+    if (n == 0) {
+        fill_info(info, 0, 0, 0.0, GKO_OK);
+        return GKO_OK;
+    }
+    Workspace ws(st);
+    double *r, *p, *q, *part;
+    SolverState* ds;
+    GKO_TRY(ws.get(&r, n));
+    GKO_TRY(ws.get(&p, n));
+    GKO_TRY(ws.get(&q, n));
+    GKO_TRY(ws.get(&part, kRedBlocks));
+    GKO_TRY(ws.get(&ds, 1));
+    const int grid = red_grid(n);
+
+    SolverState hs = {};
+    GKO_TRY(write_state(ds, &hs, st));
+    dot_kernel<double, kDotStore><<<grid, kRedThreads, 0, st>>>(n, b, b, ds, part, 0);
+    GKO_TRY(read_state(&hs, ds, st));
+    const double bnorm = std::sqrt(hs.dot_out);
+    if (bnorm == 0.0) {
+        GKO_CUDA(cudaMemsetAsync(x, 0, n * sizeof(double), st));
+        GKO_CUDA(cudaStreamSynchronize(st));
+        fill_info(info, 0, 0, 0.0, GKO_OK);
+        return GKO_OK;
+    }
+    // r = b - A x, p = r, rho = r.r
+    GKO_CUDA(cudaMemcpyAsync(r, b, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    GKO_TRY(spmv_fmt(A, fmt, x, r, -1.0, 1.0, st));
+    GKO_CUDA(cudaMemcpyAsync(p, r, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    hs = {};
+    hs.tol = tol;
+    hs.stop_ref = bnorm;
+    hs.maxit = maxit;
+    hs.status = GKO_ERR_NOT_CONVERGED;
+    GKO_TRY(write_state(ds, &hs, st));
+    dot_kernel<double, kDotRhoInit><<<grid, kRedThreads, 0, st>>>(n, r, r, ds, part, 0);
+    GKO_TRY(read_state(&hs, ds, st));
+    if (hs.conv) {  // r is the true residual here
+        double res;
+        GKO_TRY(true_residual(A, fmt, b, x, q, ds, part, bnorm, st, &res));
+        fill_info(info, 0, 0, res, GKO_OK);
+        return GKO_OK;
+    }
+    if (maxit == 0) {
+        double res;
+        GKO_TRY(true_residual(A, fmt, b, x, q, ds, part, bnorm, st, &res));
+        fill_info(info, 0, 0, res, GKO_ERR_NOT_CONVERGED);
+        return GKO_ERR_NOT_CONVERGED;
+    }
+
+    GraphHolder gh;
+    GKO_TRY(build_while_graph(&gh, [&](cudaGraphConditionalHandle h, cudaStream_t cs) -> int {
+        GKO_TRY(spmv_fmt(A, fmt, p, q, 1.0, 0.0, cs));
+        dot_kernel<double, kDotPQ><<<grid, kRedThreads, 0, cs>>>(n, p, q, ds, part, h);
+        update_kernel<double><<<grid, kRedThreads, 0, cs>>>(n, x, r, p, q, ds, part, h);
+        pupdate_kernel<double><<<grid, kRedThreads, 0, cs>>>(n, p, r, ds, 0);
+        GKO_CUDA(cudaGetLastError());
+        return GKO_OK;
+    }));
+
+    int status = GKO_ERR_NOT_CONVERGED, checks = 0;
+    double res = -1.0;
+    while (true) {
+        GKO_CUDA(cudaGraphLaunch(gh.exec, st));
+        GKO_TRY(read_state(&hs, ds, st));
+        if (hs.status == GKO_ERR_BREAKDOWN) {
+            status = GKO_ERR_BREAKDOWN;
+            break;
+        }
+        if (hs.conv) {
+            GKO_TRY(true_residual(A, fmt, b, x, q, ds, part, bnorm, st, &res));
+            ++checks;
+            if (res <= tol) {
+                status = GKO_OK;
+                break;
+            }
+            if (checks >= 4 || hs.iter >= maxit) {
+                status = GKO_ERR_NOT_CONVERGED;
+                break;
+            }
+            // not confirmed: finish this step (p = r + beta p) and go on
+            hs.conv = 0;
+            hs.done = 0;
+            hs.status = GKO_ERR_NOT_CONVERGED;
+            GKO_CUDA(cudaMemcpyAsync(ds, &hs, sizeof(SolverState), cudaMemcpyHostToDevice, st));
+            pupdate_kernel<double><<<grid, kRedThreads, 0, st>>>(n, p, r, ds, 1);
+            res = -1.0;
+            continue;
+        }
+        status = GKO_ERR_NOT_CONVERGED;  // maxit
+        break;
+    }
+    if (res < 0.0) GKO_TRY(true_residual(A, fmt, b, x, q, ds, part, bnorm, st, &res));
+    fill_info(info, hs.iter, 0, res, status);
+    if (status != GKO_OK)
+        set_error(status == GKO_ERR_BREAKDOWN ? "CG breakdown (p.q <= 0 or NaN)" : "CG reached maxit");
+    return status;
+}
+
+// ------------------------------------------- mixed precision refinement
+
+// IEEE binary64 -> bfloat16, round to nearest, ties to even, from the bit
+// pattern (values in the normal range of bfloat16).
+__device__ __forceinline__ uint16_t f64_to_bf16_rn(double v)
+{
+    const uint64_t b = static_cast<uint64_t>(__double_as_longlong(v));
+    const uint64_t sign = b >> 63;
+    int64_t exp = static_cast<int64_t>((b >> 52) & 0x7ff);
+    uint64_t mant = b & ((1ull << 52) - 1);
+    if (exp == 0 && mant == 0) return static_cast<uint16_t>(sign << 15);
+    uint64_t keep = mant >> 45;                    // top 7 stored bits
+    const uint64_t rem = mant & ((1ull << 45) - 1);
+    const uint64_t half = 1ull << 44;
+    if (rem > half || (rem == half && (keep & 1))) {
+        ++keep;
+        if (keep == 128) {
+            keep = 0;
+            ++exp;
+        }
+    }
+    const uint64_t e8 = static_cast<uint64_t>(exp - 1023 + 127);
+    return static_cast<uint16_t>((sign << 15) | (e8 << 7) | keep);
+}
+
+template <int kBf16>
+__device__ __forceinline__ double round_lo(double v)
+{
+    if (kBf16) {
+        const uint32_t bits = static_cast<uint32_t>(f64_to_bf16_rn(v)) << 16;
+        return static_cast<double>(__uint_as_float(bits));
+    }
+    return static_cast<double>(__double2float_rn(v));
+}
+
+// Low-precision copy, one row per thread: off-diagonals rounded to
+// nearest-even; the diagonal target a_ii + sum_j(|rn(a_ij)| - |a_ij|)
+// formed in FP64 (row sums preserved) and rounded to nearest-even.
+template <int kBf16>
+__global__ void lowprec_kernel(int64_t n, const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                               const double* __restrict__ val, float* __restrict__ out32,
+                               uint16_t* __restrict__ out16)
+{
+    const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+    if (i >= n) return;
+    double shift = 0.0;
+    int64_t kd = -1;
+    for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
+        if (col[k] == i) {
+            kd = k;
+            continue;
+        }
+        const double r = round_lo<kBf16>(val[k]);
+        const double d = fabs(r) - fabs(val[k]);
+        shift = shift + d;
+        if (kBf16)
+            out16[k] = f64_to_bf16_rn(val[k]);
+        else
+            out32[k] = __double2float_rn(val[k]);
+    }
+    if (kd >= 0) {
+        const double d = __dadd_rn(val[kd], shift);
+        if (kBf16)
+            out16[kd] = f64_to_bf16_rn(d);
+        else
+            out32[kd] = __double2float_rn(d);
+    }
+}
+
+// rl = float(r / nr); d = 0; p = rl
+__global__ void inner_init_kernel(int64_t n, const double* __restrict__ r, double nr, float* __restrict__ rl,
+                                  float* __restrict__ d, float* __restrict__ p)
+{
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const float v = __double2float_rn(r[i] / nr);
+        rl[i] = v;
+        d[i] = 0.0f;
+        p[i] = v;
+    }
+}
+
+// x += nr * d in FP64
+__global__ void correct_kernel(int64_t n, double* __restrict__ x, const float* __restrict__ d, double nr)
+{
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+        x[i] = fma(nr, static_cast<double>(d[i]), x[i]);
+}
+
+template <typename V>
+static cudaError_t inner_spmv(const gko_matrix* A, const V* val, SegScratchT<float> sc, const float* p, float* q,
+                              cudaStream_t st)
+{
+    if (A->nnz == 0) {
+        return cudaMemsetAsync(q, 0, A->n_rows * sizeof(float), st);
+    }
+    return seg_launch<kSegP, V, float, false, false, false, false>(A->n_rows, A->nnz, A->csr.row_ptr, nullptr,
+                                                                   A->csr.col, val, A->csr.thr_row, sc, p, q, 1.0f,
+                                                                   0.0f, A->d_err, st);
+}
+
+int cg_mixed_solve(gko_matrix* A, int inner, const double* b, double* x, double tol, int maxit_outer,
+                   double inner_tol, int inner_maxit, cudaStream_t st, gko_solve_info* info)
+{
+    const int64_t n = A->n_rows, nnz = A->nnz;
+    if (n == 0) {
+        fill_info(info, 0, 0, 0.0, GKO_OK);
+        return GKO_OK;
+    }
+    const bool bf16 = inner == GKO_BF16;
+    // cached low-precision copy of the values (CSR order)
+    if (bf16 && !A->val_bf16) {
+        GKO_TRY(dev_alloc(&A->val_bf16, padded_len(nnz)));
+        GKO_CUDA(cudaMemsetAsync(A->val_bf16, 0, padded_len(nnz) * sizeof(uint16_t), st));
+        lowprec_kernel<1><<<ceil_div(n, 256), 256, 0, st>>>(n, A->csr.row_ptr, A->csr.col, A->csr.val, nullptr,
+                                                             A->val_bf16);
+    }
+    if (!bf16 && !A->val_f32) {
+        GKO_TRY(dev_alloc(&A->val_f32, padded_len(nnz)));
+        GKO_CUDA(cudaMemsetAsync(A->val_f32, 0, padded_len(nnz) * sizeof(float), st));
+        lowprec_kernel<0><<<ceil_div(n, 256), 256, 0, st>>>(n, A->csr.row_ptr, A->csr.col, A->csr.val, A->val_f32,
+                                                             nullptr);
+    }
+    GKO_CUDA(cudaGetLastError());
+
+    Workspace ws(st);
+    double *r, *part;
+    float *rl, *d, *p, *q;
+    SolverState *ds, *di;
+    GKO_TRY(ws.get(&r, n));
+    GKO_TRY(ws.get(&part, kRedBlocks));
+    GKO_TRY(ws.get(&rl, n));
+    GKO_TRY(ws.get(&d, n));
+    GKO_TRY(ws.get(&p, n));
+    GKO_TRY(ws.get(&q, n));
+    GKO_TRY(ws.get(&ds, 1));
+    GKO_TRY(ws.get(&di, 1));
+    const int64_t tiles = std::max<int64_t>(1, (nnz + SegShape<kSegP>::kTile - 1) / SegShape<kSegP>::kTile);
+    SegScratchT<float> sc;
+    GKO_TRY(ws.get(&sc.tail_val, tiles));
+    GKO_TRY(ws.get(&sc.tail_row, tiles));
+    GKO_TRY(ws.get(&sc.tail_pass, tiles));
+    GKO_TRY(ws.get(&sc.head_val, tiles));
+    GKO_TRY(ws.get(&sc.head_row, tiles));
+    const int grid = red_grid(n);
+
+    SolverState hs = {};
+    GKO_TRY(write_state(ds, &hs, st));
+    dot_kernel<double, kDotStore><<<grid, kRedThreads, 0, st>>>(n, b, b, ds, part, 0);
+    GKO_TRY(read_state(&hs, ds, st));
+    const double bnorm = std::sqrt(hs.dot_out);
+    if (bnorm == 0.0) {
+        GKO_CUDA(cudaMemsetAsync(x, 0, n * sizeof(double), st));
+        GKO_CUDA(cudaStreamSynchronize(st));
+        fill_info(info, 0, 0, 0.0, GKO_OK);
+        return GKO_OK;
+    }
+
+    // inner CG graph: q = A_lo p; alpha; d += alpha p, rl -= alpha q; beta; p = rl + beta p
+    GraphHolder gh;
+    GKO_TRY(build_while_graph(&gh, [&](cudaGraphConditionalHandle h, cudaStream_t cs) -> int {
+        cudaError_t e = bf16 ? inner_spmv<__nv_bfloat16>(A, reinterpret_cast<const __nv_bfloat16*>(A->val_bf16), sc,
+                                                          p, q, cs)
+                             : inner_spmv<float>(A, A->val_f32, sc, p, q, cs);
+        if (e != cudaSuccess) return cuda_fail(e, "inner SpMV launch");
+        dot_kernel<float, kDotPQ><<<grid, kRedThreads, 0, cs>>>(n, p, q, di, part, h);
+        update_kernel<float><<<grid, kRedThreads, 0, cs>>>(n, d, rl, p, q, di, part, h);
+        pupdate_kernel<float><<<grid, kRedThreads, 0, cs>>>(n, p, rl, di, 0);
+        GKO_CUDA(cudaGetLastError());
+        return GKO_OK;
+    }));
+
+    int status = GKO_ERR_NOT_CONVERGED, outer = 0, inner_total = 0;
+    double res = -1.0;
+    for (int o = 0; o <= maxit_outer; ++o) {
+        // r = b - A x (FP64), ||r||
+        GKO_CUDA(cudaMemcpyAsync(r, b, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        GKO_TRY(spmv_csr(A, GKO_CFG_DEFAULT, x, r, -1.0, 1.0, st));
+        dot_kernel<double, kDotStore><<<grid, kRedThreads, 0, st>>>(n, r, r, ds, part, 0);
+        GKO_TRY(read_state(&hs, ds, st));
+        const double nr = std::sqrt(hs.dot_out);
+        res = nr / bnorm;
+        if (!(nr == nr)) {
+            status = GKO_ERR_BREAKDOWN;
+            break;
+        }
+        if (res <= tol) {
+            status = GKO_OK;
+            break;
+        }
+        if (o == maxit_outer) break;
+        outer = o + 1;
+        inner_init_kernel<<<grid, kRedThreads, 0, st>>>(n, r, nr, rl, d, p);
+        SolverState is = {};
+        is.tol = inner_tol;
+        is.rel_inner = 1;
+        is.maxit = inner_maxit;
+        is.status = GKO_ERR_NOT_CONVERGED;
+        GKO_TRY(write_state(di, &is, st));
+        dot_kernel<float, kDotRhoInit><<<grid, kRedThreads, 0, st>>>(n, rl, rl, di, part, 0);
+        GKO_CUDA(cudaGraphLaunch(gh.exec, st));
+        correct_kernel<<<grid, kRedThreads, 0, st>>>(n, x, d, nr);
+        GKO_TRY(read_state(&is, di, st));
+        inner_total += is.iter;
+    }
+    GKO_CUDA(cudaGetLastError());
+    fill_info(info, inner_total, outer, res, status);
+    if (status != GKO_OK) set_error("mixed-precision CG did not reach the tolerance");
+    return status;
+}
+
+}  // namespace gko

