@@ -207,6 +207,8 @@ def run_gpu(args):
         mats[name] = A
         M = gko.Matrix(A, stream=st)
         for f in FORMATS[1:]:
+            if args.only and "%s/%s" % (name, f) not in args.only.split(","):
+                continue
             try:
                 M.convert(f, stream=st)
             except gko.GkoError as e:

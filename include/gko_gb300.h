@@ -85,7 +85,10 @@ enum {
     GKO_CFG_CSR_SUBWARP_16 = 5,
     GKO_CFG_CSR_SUBWARP_32 = 6,
     GKO_CFG_CSR_NNZSPLIT = 7,   /* CSR, load-balanced equal-nnz split with segmented reduction */
-    GKO_CFG_CSR_BANDED = 8      /* CSR, x window staged in shared memory (banded matrices) */
+    GKO_CFG_CSR_BANDED = 8,     /* CSR row blocks with the x window staged in shared memory (banded
+                                   matrices: max |i - j| <= 1024 and max row length <= 128) */
+    GKO_CFG_CSR_ROWBLOCK = 9    /* CSR row blocks staged in shared memory, one thread per row (max row
+                                   length <= 128); the default when row lengths are close */
 };
 
 typedef struct gko_matrix gko_matrix;

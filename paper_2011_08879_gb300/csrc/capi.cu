@@ -71,8 +71,9 @@ int gko_matrix_create_csr(int64_t n_rows, int64_t n_cols, int64_t nnz, const int
     if (!out) return fail(GKO_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
     if (n_rows < 0 || n_cols < 0 || nnz < 0) return fail(GKO_ERR_INVALID_ARG, "negative size");
-    if (n_rows >= INT32_MAX || n_cols >= INT32_MAX || nnz >= INT32_MAX)
-        return fail(GKO_ERR_INVALID_ARG, "sizes must fit int32 indices");
+    // int32 indices; a margin of 2^16 keeps tile arithmetic in int32
+    if (n_rows >= INT32_MAX - 65536 || n_cols >= INT32_MAX - 65536 || nnz >= INT32_MAX - 65536)
+        return fail(GKO_ERR_INVALID_ARG, "sizes must be below 2^31 - 2^16 (int32 indices)");
     if (!row_ptr || (nnz > 0 && (!col || !val))) return fail(GKO_ERR_INVALID_ARG, "NULL array");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     gko_matrix* A = new gko_matrix();
@@ -314,7 +315,7 @@ int gko_spmv_config(int fmt, int config, const gko_matrix* A, const double* x, d
                     double beta, void* stream)
 {
     GKO_TRY(spmv_checks(fmt, A, x, y));
-    if (config < GKO_CFG_DEFAULT || config > GKO_CFG_CSR_BANDED)
+    if (config < GKO_CFG_DEFAULT || config > GKO_CFG_CSR_ROWBLOCK)
         return fail(GKO_ERR_INVALID_ARG, "unknown kernel configuration");
     if (fmt == GKO_FMT_AUTO) return fail(GKO_ERR_INVALID_ARG, "AUTO takes no explicit configuration");
     return spmv_dispatch(fmt, config, A, x, y, alpha, beta, static_cast<cudaStream_t>(stream));

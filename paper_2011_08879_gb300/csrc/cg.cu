@@ -506,6 +506,12 @@ static cudaError_t inner_spmv(const gko_matrix* A, const V* val, SegScratchT<flo
     if (A->nnz == 0) {
         return cudaMemsetAsync(q, 0, A->n_rows * sizeof(float), st);
     }
+    if (rowblock_preferred(A)) {  // rows of similar length: one thread per row
+        if constexpr (sizeof(V) == 2)
+            return rowblock_lowprec_bf16(A, val, p, q, st);
+        else
+            return rowblock_lowprec_f32(A, val, p, q, st);
+    }
     return seg_launch<kSegP, V, float, false, false, false, false>(A->n_rows, A->nnz, A->csr.row_ptr, nullptr,
                                                                    A->csr.col, val, A->csr.thr_row, sc, p, q, 1.0f,
                                                                    0.0f, A->d_err, st);

@@ -165,6 +165,14 @@ int spmv_sellp(const gko_matrix* A, const double* x, double* y, double alpha, do
 int spmv_hybrid(const gko_matrix* A, const double* x, double* y, double alpha, double beta,
                 cudaStream_t st);
 int scale_vector(int64_t n, double* y, double beta, cudaStream_t st);  // y = beta * y (beta 0: zero)
+int spmv_csr_rowblock(const gko_matrix* A, const double* x, double* y, double alpha, double beta,
+                      cudaStream_t st);
+int spmv_csr_banded(const gko_matrix* A, const double* x, double* y, double alpha, double beta,
+                    cudaStream_t st);
+int rowblock_rows(const gko_matrix* A);
+bool rowblock_preferred(const gko_matrix* A);
+cudaError_t rowblock_lowprec_f32(const gko_matrix* A, const float* val, const float* x, float* y, cudaStream_t st);
+cudaError_t rowblock_lowprec_bf16(const gko_matrix* A, const void* val, const float* x, float* y, cudaStream_t st);
 
 // conversions (convert.cu); all synchronise the stream where sizes are read
 int convert_csr_to_coo(gko_matrix* A, cudaStream_t st);

@@ -14,7 +14,8 @@
 //    mbarrier;
 //  * thread g owns entries [g*P, g*P+P) (P odd, so shared-memory reads of
 //    consecutive threads fall in distinct banks) and sums them row by row
-//    with one FMA per entry;
+//    with one FMA per entry; all per-entry index arithmetic is 32-bit and
+//    local to the tile;
 //  * a row is finalised by the thread holding its last entry (rows whose
 //    end index lies in the thread's range (s, e]); contributions of earlier
 //    threads are added from their outgoing partials (segmented reduction
@@ -123,12 +124,190 @@ __device__ __forceinline__ void fence_proxy_async_smem()
 
 // Metadata of a staged tile, written by the issuing thread.
 struct SegTileInfo {
-    int64_t t0;
+    int32_t t0;
     int32_t r_lo;     // CSR: row holding entry t0;  COO: row of entry t0
     int32_t a_lo;     // CSR: first staged row_ptr index (multiple of 4)
     int32_t staged;   // CSR: row_ptr segment staged in shared memory
     int32_t began;    // COO: the tile's first row began before the tile
+    int32_t next_r;   // COO: row of entry t1 (n_rows at the end)
 };
+
+// Per-thread state after phase 1 of a tile.
+template <typename T>
+struct SegThreadOut {
+    int fin_row;   // row finalised here that began before the thread (-1: none)
+    T fin_val;
+    int open_row;  // row still open at the thread's end (-1: none)
+    T open_val;
+};
+
+// Phase 1 of one tile for one thread: sum its entries row by row, store
+// rows that start and end in its range, report the deferred and open rows.
+// ls/le: the thread's entries, local to the tile; RP: CSR row pointers as
+// a pointer whose index is the global row (shared or global memory).
+template <int P, typename V, typename T, bool kAlpha, bool kBeta, bool kCoo, bool kSkipEmpty, typename RP>
+__device__ __forceinline__ SegThreadOut<T> seg_thread(int ls, int le, int t0, int cnt, int n_rows, const V* s_val,
+                                                      const int32_t* s_col, const int32_t* s_aux, RP rp,
+                                                      int first_row, bool first_carried, int next_r_tile,
+                                                      int my_row, const T* __restrict__ x, T* __restrict__ y,
+                                                      T alpha, T beta)
+{
+    SegThreadOut<T> o{-1, T(0), -1, T(0)};
+    const int rem = le - ls;  // entries of this thread (<= 0: none)
+    T vv[P], xv[P];
+#pragma unroll
+    for (int j = 0; j < P; ++j) {
+        const bool ok = j < rem;
+        const int c = ok ? s_col[ls + j] : 0;
+        vv[j] = ok ? to_t<V, T>(s_val[ls + j]) : T(0);
+        xv[j] = ldg(x + c);
+    }
+    // NOTE: lanes without entries must not return before the warp vote below
+    // (__all_sync over the full warp would wait for them forever).
+    const bool has = rem > 0;
+
+    int row = 0, endr = 0;  // current row; its end relative to ls (CSR)
+    bool ob = false;        // current row began before the thread's range
+    if (has) {
+        if (kCoo) {
+            row = s_aux[ls];
+            ob = (ls == 0) ? first_carried : (s_aux[ls - 1] == row);
+        } else {
+            row = my_row;
+            endr = rp[row + 1] - t0 - ls;
+            ob = rp[row] - t0 < ls;
+        }
+        // rows before the first stored entry are empty (end position 0)
+        if (!kSkipEmpty && t0 + ls == 0)
+            for (int r = 0; r < row; ++r) seg_store<kAlpha, kBeta>(y, r, T(0), alpha, beta);
+    }
+
+    // ---- fast path: at most three row ends in the range, no empty row among
+    // them.  Ends e0 < e1 < e2 (relative to ls, in (0, rem] when inside the
+    // range) are known up front, each entry costs one FMA plus selects, and
+    // the finished rows are stored after the loop: no divergent branches.
+    int e0 = INT32_MAX, e1 = INT32_MAX, e2 = INT32_MAX;
+    int ra = row + 1, rb = row + 2, rc = row + 3;  // rows after the 1st, 2nd, 3rd end
+    bool fast = true;
+    if (!has) {
+        // nothing to sum; still takes part in the vote
+    } else if (kCoo) {
+        int cur = row, n_chg = 0;
+        bool gap = false;
+        e0 = e1 = e2 = INT32_MAX;
+#pragma unroll
+        for (int j = 0; j < P; ++j) {
+            if (j < rem) {
+                const int nr = (ls + j + 1 < cnt) ? s_aux[ls + j + 1] : next_r_tile;
+                const bool c = nr != cur;
+                gap |= nr > cur + 1;  // rows without entries in between (or after the last row)
+                e0 = (c && n_chg == 0) ? j + 1 : e0;
+                e1 = (c && n_chg == 1) ? j + 1 : e1;
+                e2 = (c && n_chg == 2) ? j + 1 : e2;
+                ra = (c && n_chg == 0) ? nr : ra;
+                rb = (c && n_chg == 1) ? nr : rb;
+                rc = (c && n_chg == 2) ? nr : rc;
+                n_chg += c;
+                cur = nr;
+            }
+        }
+        // rows without entries need explicit zero stores unless skipped
+        fast = (kSkipEmpty || !gap) && n_chg <= 3;
+    } else {
+        // The end of row + k is read only when row + k - 1 ends inside the
+        // range: then row + k + 1 <= R(t1) + 1 lies in the staged segment.
+        auto end_at = [&](int k) { return row + k < n_rows ? rp[row + k + 1] - t0 - ls : INT32_MAX; };
+        e0 = endr;
+        e1 = e0 <= rem ? end_at(1) : INT32_MAX;
+        e2 = e1 <= rem ? end_at(2) : INT32_MAX;
+        const int e3 = e2 <= rem ? end_at(3) : INT32_MAX;
+        fast = (e0 > rem || e1 > e0) && (e1 > rem || e2 > e1) && (e2 > rem || e3 > e2) && e3 > rem;
+    }
+    const bool warp_fast = __all_sync(0xffffffffu, fast);  // every lane of the warp reaches this
+    if (!has) return o;
+    if (warp_fast) {
+        T v0 = T(0), v1 = T(0), v2 = T(0), acc = T(0);
+#pragma unroll
+        for (int j = 0; j < P; ++j) {
+            if (j < rem) {
+                acc = fma(vv[j], xv[j], acc);
+                const bool h0 = j + 1 == e0, h1 = j + 1 == e1, h2 = j + 1 == e2;
+                v0 = h0 ? acc : v0;
+                v1 = h1 ? acc : v1;
+                v2 = h2 ? acc : v2;
+                acc = (h0 || h1 || h2) ? T(0) : acc;
+            }
+        }
+        const int n_end = (e0 <= rem) + (e1 <= rem) + (e2 <= rem);
+        if (n_end > 0) {
+            if (ob) {
+                o.fin_row = row;
+                o.fin_val = v0;
+            } else {
+                seg_store<kAlpha, kBeta>(y, row, v0, alpha, beta);
+            }
+        }
+        if (n_end > 1) seg_store<kAlpha, kBeta>(y, ra, v1, alpha, beta);
+        if (n_end > 2) seg_store<kAlpha, kBeta>(y, rb, v2, alpha, beta);
+        const int last_end = n_end == 0 ? 0 : (n_end == 1 ? e0 : (n_end == 2 ? e1 : e2));
+        if (last_end < rem) {  // entries after the last end belong to an open row
+            o.open_row = n_end == 0 ? row : (n_end == 1 ? ra : (n_end == 2 ? rb : rc));
+            o.open_val = acc;
+        }
+        return o;
+    }
+
+    // ---- general path: any number of row ends, empty rows included
+    T acc = T(0);
+    bool pending = false;
+#pragma unroll
+    for (int j = 0; j < P; ++j) {
+        if (j < rem) {
+            acc = fma(vv[j], xv[j], acc);
+            pending = true;
+            int nr = 0;
+            bool ends;
+            if (kCoo) {
+                nr = (ls + j + 1 < cnt) ? s_aux[ls + j + 1] : next_r_tile;
+                ends = nr != row;
+            } else {
+                ends = (j + 1 == endr);
+            }
+            if (ends) {
+                if (ob) {
+                    o.fin_row = row;
+                    o.fin_val = acc;
+                } else {
+                    seg_store<kAlpha, kBeta>(y, row, acc, alpha, beta);
+                }
+                acc = T(0);
+                pending = false;
+                ob = false;
+                if (kCoo) {
+                    if (!kSkipEmpty)
+                        for (int r = row + 1; r < nr; ++r) seg_store<kAlpha, kBeta>(y, r, T(0), alpha, beta);
+                    row = nr;
+                } else {
+                    // skip the empty rows that end at the same position
+                    ++row;
+                    int e = row < n_rows ? rp[row + 1] - t0 - ls : INT32_MAX;
+                    while (e == j + 1) {
+                        if (!kSkipEmpty) seg_store<kAlpha, kBeta>(y, row, T(0), alpha, beta);
+                        ++row;
+                        e = row < n_rows ? rp[row + 1] - t0 - ls : INT32_MAX;
+                    }
+                    endr = e;
+                }
+            }
+        }
+    }
+    if (pending) {
+        o.open_row = row;
+        o.open_val = acc;
+    }
+    (void)first_row;
+    return o;
+}
 
 // kCoo = false: CSR with row_ptr and the per-thread start rows thr_row
 // (thr_row[g] = row holding entry g*P).  kCoo = true: COO with row[].
@@ -136,7 +315,7 @@ struct SegTileInfo {
 // part of the hybrid format onto the ELL part's result, with beta = 1).
 template <int P, typename V, typename T, bool kAlpha, bool kBeta, bool kCoo, bool kSkipEmpty>
 __global__ void __launch_bounds__(kSegThreads, kSegCtasPerSm)
-    seg_spmv_kernel(int64_t n_rows, int64_t nnz, const int32_t* __restrict__ row_ptr,
+    seg_spmv_kernel(int64_t n_rows64, int64_t nnz64, const int32_t* __restrict__ row_ptr,
                     const int32_t* __restrict__ rows, const int32_t* __restrict__ col,
                     const V* __restrict__ val, const int32_t* __restrict__ thr_row, const T* __restrict__ x,
                     T* __restrict__ y, T alpha, T beta, SegScratchT<T> sc, uint32_t* err)
@@ -153,37 +332,39 @@ __global__ void __launch_bounds__(kSegThreads, kSegCtasPerSm)
     __shared__ SegTileInfo info[2];
     __shared__ int s_head_done;
 
+    const int n_rows = static_cast<int>(n_rows64);  // sizes fit int32 (checked at creation)
+    const int nnz = static_cast<int>(nnz64);
     const int tid = threadIdx.x;
-    const int64_t n_tiles = (nnz + S::kTile - 1) / S::kTile;
-    const int64_t stride = gridDim.x;
+    const int n_tiles = (nnz + S::kTile - 1) / S::kTile;
+    const int stride = gridDim.x;
 
     auto stage_val = [&](int st) { return reinterpret_cast<V*>(smem + st * G::kBytes); };
     auto stage_col = [&](int st) { return reinterpret_cast<int32_t*>(smem + st * G::kBytes + G::kVal); };
     auto stage_aux = [&](int st) { return reinterpret_cast<int32_t*>(smem + st * G::kBytes + G::kVal + G::kCol); };
 
     // Issue the bulk copies of `tile` into stage `st` (thread 0 only).
-    // CSR: a = R(t0), b = R(t1) (or n_rows at the end).  COO: a = rows[t0-1]
-    // (or -1), b = rows[t0].
-    auto issue = [&](int64_t tile, int st, int32_t a, int32_t b) {
-        const int64_t t0 = tile * S::kTile;
-        const int64_t t1 = min(t0 + S::kTile, nnz);
-        const int cnt = static_cast<int>(t1 - t0);
-        const int cnt_al = (cnt + kAlign - 1) / kAlign * kAlign;
+    // CSR: a = R(t0), b = R(t1) (n_rows at the end).  COO: a = rows[t0-1]
+    // (or -1), b = rows[t0], c = rows[t1] (n_rows at the end).
+    auto issue = [&](int tile, int st, int32_t a, int32_t b, int32_t c) {
+        const int t0 = tile * S::kTile;
+        const int t1 = min(t0 + S::kTile, nnz);
+        const int cnt_al = (t1 - t0 + kAlign - 1) / kAlign * kAlign;
         uint32_t bytes = cnt_al * static_cast<uint32_t>(sizeof(V) + sizeof(int32_t) + (kCoo ? sizeof(int32_t) : 0));
         SegTileInfo ti;
         ti.t0 = t0;
         ti.staged = 0;
         ti.a_lo = 0;
+        ti.began = 0;
+        ti.next_r = c;
         int a_cnt = 0;
         if (kCoo) {
             ti.r_lo = b;
             ti.began = (t0 > 0) && (a == b);
         } else {
             ti.r_lo = a;
-            ti.began = 0;
-            const int64_t count = min(static_cast<int64_t>(b) + 2, n_rows + 1) - a;
+            const int count = min(b + 2, n_rows + 1) - a;
             ti.a_lo = a & ~3;
-            a_cnt = static_cast<int>((a + count - ti.a_lo + 3) & ~3);
+            a_cnt = (a + count - ti.a_lo + 3) & ~3;
             if (a_cnt <= S::kRowStage) {
                 ti.staged = 1;
                 bytes += a_cnt * sizeof(int32_t);
@@ -199,13 +380,23 @@ __global__ void __launch_bounds__(kSegThreads, kSegCtasPerSm)
             bulk_g2s(stage_aux(st), row_ptr + ti.a_lo, a_cnt * sizeof(int32_t), &bar[st]);
     };
     // metadata loads needed to issue `tile` (read early, used later)
-    auto meta_a = [&](int64_t tile) -> int32_t {
+    auto meta_a = [&](int tile) -> int32_t {
         if (kCoo) return tile > 0 ? rows[tile * S::kTile - 1] : -1;
         return thr_row[tile * kSegThreads];
     };
-    auto meta_b = [&](int64_t tile) -> int32_t {
+    auto meta_b = [&](int tile) -> int32_t {
         if (kCoo) return rows[tile * S::kTile];
-        return (tile + 1) * S::kTile < nnz ? thr_row[(tile + 1) * kSegThreads] : static_cast<int32_t>(n_rows);
+        return (tile + 1) * S::kTile < nnz ? thr_row[(tile + 1) * kSegThreads] : n_rows;
+    };
+    auto meta_c = [&](int tile) -> int32_t {
+        if (!kCoo) return 0;
+        return (tile + 1) * S::kTile < nnz ? rows[(tile + 1) * S::kTile] : n_rows;
+    };
+    // start row of this thread's entries in a tile (threads whose first
+    // entry exists only: thr_row has ceil(nnz / P) entries)
+    auto start_row = [&](int tile) -> int32_t {
+        const int g = tile * kSegThreads + tid;
+        return (!kCoo && tile < n_tiles && static_cast<int64_t>(g) * P < nnz) ? thr_row[g] : 0;
     };
 
     if (tid == 0) {
@@ -217,20 +408,14 @@ __global__ void __launch_bounds__(kSegThreads, kSegCtasPerSm)
     __syncthreads();
     if (tid == 0) {
         for (int k = 0; k < 2; ++k) {
-            const int64_t t = blockIdx.x + k * stride;
-            if (t < n_tiles) issue(t, k, meta_a(t), meta_b(t));
+            const int t = blockIdx.x + k * stride;
+            if (t < n_tiles) issue(t, k, meta_a(t), meta_b(t), meta_c(t));
         }
     }
-    // start row of this thread's entries in its next tile (only threads whose
-    // first entry exists: thr_row has ceil(nnz / P) entries)
-    auto start_row = [&](int64_t tile) -> int32_t {
-        const int64_t g = tile * kSegThreads + tid;
-        return (!kCoo && tile < n_tiles && g * P < nnz) ? thr_row[g] : 0;
-    };
     int32_t my_row = start_row(blockIdx.x);
 
     for (int it = 0;; ++it) {
-        const int64_t tile = blockIdx.x + it * stride;
+        const int tile = blockIdx.x + it * stride;
         if (tile >= n_tiles) break;
         const int st = it & 1;
         const uint32_t parity = (it >> 1) & 1;
@@ -238,111 +423,48 @@ __global__ void __launch_bounds__(kSegThreads, kSegCtasPerSm)
         if (!landed) landed = mbar_wait_bounded(&bar[st], parity, err);  // copies still in flight: once more
         if (!__syncthreads_and(landed)) return;                           // CTA-uniform exit
 
-        // prefetch what the next issues and the next tile need
-        const int64_t t_issue = tile + 2 * stride;
-        int32_t pa = 0, pb = 0;
+        // prefetch what the next issue and the next tile need
+        const int t_issue = tile + 2 * stride;
+        int32_t pa = 0, pb = 0, pc = 0;
         if (tid == 0 && t_issue < n_tiles) {
             pa = meta_a(t_issue);
             pb = meta_b(t_issue);
+            pc = meta_c(t_issue);
         }
-        const int64_t t_next = tile + stride;
-        const int32_t next_row = start_row(t_next);
+        const int32_t next_row = start_row(tile + stride);
 
         const SegTileInfo ti = info[st];
+        const int t0 = ti.t0;
+        const int cnt = min(t0 + S::kTile, nnz) - t0;
+        const int ls = tid * P;
+        const int le = min(ls + P, cnt);
         const V* s_val = stage_val(st);
         const int32_t* s_col = stage_col(st);
         const int32_t* s_aux = stage_aux(st);
-        const int64_t t0 = ti.t0;
-        const int64_t t1 = min(t0 + S::kTile, nnz);
-        const int cnt = static_cast<int>(t1 - t0);
-        const int32_t* rp = (!kCoo && ti.staged) ? (s_aux - ti.a_lo) : row_ptr;
         const int first_row = ti.r_lo;
-        const bool first_carried = kCoo ? (ti.began != 0) : (rp[first_row] < t0);
-
-        const int64_t s = t0 + static_cast<int64_t>(tid) * P;
-        const int64_t e = min(s + P, t1);
-        const bool active = s < t1;
-
-        // ------------------------------------------------------------ phase 1
-        T vv[P], xv[P];
-#pragma unroll
-        for (int j = 0; j < P; ++j) {
-            const int li = tid * P + j;
-            const bool ok = s + j < e;
-            const int c = ok ? s_col[li] : 0;
-            vv[j] = ok ? to_t<V, T>(s_val[li]) : T(0);
-            xv[j] = ldg(x + c);
+        bool first_carried;
+        SegThreadOut<T> o;
+        if (kCoo) {
+            first_carried = ti.began != 0;
+            o = seg_thread<P, V, T, kAlpha, kBeta, kCoo, kSkipEmpty>(ls, le, t0, cnt, n_rows, s_val, s_col, s_aux,
+                                                                     s_aux, first_row, first_carried, ti.next_r,
+                                                                     my_row, x, y, alpha, beta);
+        } else if (ti.staged) {
+            const int32_t* rps = s_aux - ti.a_lo;  // shared memory, indexed by global row
+            first_carried = rps[first_row] < t0;
+            o = seg_thread<P, V, T, kAlpha, kBeta, kCoo, kSkipEmpty>(ls, le, t0, cnt, n_rows, s_val, s_col, s_aux,
+                                                                     rps, first_row, first_carried, 0, my_row, x, y,
+                                                                     alpha, beta);
+        } else {
+            first_carried = row_ptr[first_row] < t0;
+            o = seg_thread<P, V, T, kAlpha, kBeta, kCoo, kSkipEmpty>(ls, le, t0, cnt, n_rows, s_val, s_col, s_aux,
+                                                                     row_ptr, first_row, first_carried, 0, my_row,
+                                                                     x, y, alpha, beta);
         }
 
-        int64_t row = 0, end = 0;
-        bool open_before = false;  // current row began before s
-        int fin_row = -1;          // deferred row (began before s, ends here)
-        T fin_val = T(0);
-        T acc = T(0);
-        bool pending = false;  // acc holds entries of a row not finalised yet
-        if (active) {
-            if (kCoo) {
-                row = s_aux[tid * P];
-                open_before = (s > 0) && ((s == t0) ? first_carried : (s_aux[tid * P - 1] == row));
-            } else {
-                row = my_row;
-                end = rp[row + 1];
-                open_before = rp[row] < s;
-            }
-            // rows before the first stored entry are empty (end position 0)
-            if (s == 0 && !kSkipEmpty)
-                for (int64_t r = 0; r < row; ++r) seg_store<kAlpha, kBeta>(y, r, T(0), alpha, beta);
-        }
-
-#pragma unroll
-        for (int j = 0; j < P; ++j) {
-            const int64_t k = s + j;
-            if (k < e) {
-                acc = fma(vv[j], xv[j], acc);
-                pending = true;
-                bool ends;
-                int64_t next_r = 0;
-                if (kCoo) {
-                    const int li = tid * P + j;
-                    if (k + 1 < t1)
-                        next_r = s_aux[li + 1];
-                    else
-                        next_r = (k + 1 < nnz) ? rows[k + 1] : n_rows;
-                    ends = next_r != row;
-                } else {
-                    ends = (k + 1 == end);
-                }
-                if (ends) {
-                    if (open_before) {
-                        fin_row = static_cast<int>(row);
-                        fin_val = acc;
-                    } else {
-                        seg_store<kAlpha, kBeta>(y, row, acc, alpha, beta);
-                    }
-                    acc = T(0);
-                    pending = false;
-                    open_before = false;
-                    // empty rows that end at k + 1
-                    if (kCoo) {
-                        if (!kSkipEmpty)
-                            for (int64_t r = row + 1; r < next_r; ++r)
-                                seg_store<kAlpha, kBeta>(y, r, T(0), alpha, beta);
-                        row = next_r;
-                    } else {
-                        ++row;
-                        while (row < n_rows && rp[row + 1] == k + 1) {
-                            if (!kSkipEmpty) seg_store<kAlpha, kBeta>(y, row, T(0), alpha, beta);
-                            ++row;
-                        }
-                        if (row < n_rows) end = rp[row + 1];
-                    }
-                }
-            }
-        }
-
-        // outgoing partial: the row still open at e (it continues past e)
-        s_prow[tid] = pending ? static_cast<int32_t>(row) : -1;
-        s_part[tid] = pending ? acc : T(0);
+        // outgoing partial: the row still open at the thread's end
+        s_prow[tid] = o.open_row;
+        s_part[tid] = o.open_val;
         __syncthreads();
 
         // ------------------------------------------------------------ phase 2
@@ -366,21 +488,20 @@ __global__ void __launch_bounds__(kSegThreads, kSegCtasPerSm)
         // A row is carried across tiles only if it is the tile's first row and
         // that row began before the tile; a row whose run of partials merely
         // reaches thread 0 may have started inside thread 0's range.
-        if (fin_row >= 0) {
+        if (o.fin_row >= 0) {
             bool reached;
-            const T carry = seg_walk<T>(tid - 1, fin_row, s_part, s_prow, s_wsum, s_wrow, &reached);
-            const T total = carry + fin_val;
-            if (reached && first_carried && fin_row == first_row) {
+            const T carry = seg_walk<T>(tid - 1, o.fin_row, s_part, s_prow, s_wsum, s_wrow, &reached);
+            const T total = carry + o.fin_val;
+            if (reached && first_carried && o.fin_row == first_row) {
                 sc.head_val[tile] = total;
-                sc.head_row[tile] = fin_row;
+                sc.head_row[tile] = o.fin_row;
                 s_head_done = 1;
             } else {
-                seg_store<kAlpha, kBeta>(y, fin_row, total, alpha, beta);
+                seg_store<kAlpha, kBeta>(y, o.fin_row, total, alpha, beta);
             }
         }
         // the tile's last active thread publishes the carry of a row open at t1
-        const int last = (cnt - 1) / P;
-        if (tid == last) {
+        if (tid == (cnt - 1) / P) {
             const int32_t r = s_prow[tid];
             if (r >= 0) {
                 bool reached;
@@ -399,7 +520,7 @@ __global__ void __launch_bounds__(kSegThreads, kSegCtasPerSm)
             s_head_done = 0;
             if (t_issue < n_tiles) {
                 fence_proxy_async_smem();  // generic-proxy reads of the stage before the async refill
-                issue(t_issue, st, pa, pb);
+                issue(t_issue, st, pa, pb, pc);
             }
         }
     }

@@ -233,7 +233,11 @@ int spmv_csr(const gko_matrix* A, int config, const double* x, double* y, double
         case GKO_CFG_CSR_SUBWARP_8: launch_subwarp<8>(A, x, y, alpha, beta, st); break;
         case GKO_CFG_CSR_SUBWARP_16: launch_subwarp<16>(A, x, y, alpha, beta, st); break;
         case GKO_CFG_CSR_SUBWARP_32: launch_subwarp<32>(A, x, y, alpha, beta, st); break;
+        case GKO_CFG_CSR_ROWBLOCK: return spmv_csr_rowblock(A, x, y, alpha, beta, st);
+        case GKO_CFG_CSR_BANDED: return spmv_csr_banded(A, x, y, alpha, beta, st);
         case GKO_CFG_DEFAULT:
+            if (rowblock_preferred(A)) return spmv_csr_rowblock(A, x, y, alpha, beta, st);
+            [[fallthrough]];
         case GKO_CFG_CSR_NNZSPLIT:
             return launch_seg(A->n_rows, A->nnz, A->csr.row_ptr, nullptr, A->csr.col, A->csr.val, A->csr.thr_row,
                               A->csr.seg, x, y, alpha, beta, A->d_err, false, st, false);

@@ -46,6 +46,7 @@ def test_conversions_bit_exact(gko, dev, orc, name):
         assert g["info"][4] == o["K"] and g["info"][5] == o["n_pad"]
         assert same(g["col"], o["col"]) and same(g["val"], o["val"])
 
+    M.set_params(ell_factor=1e6)  # conversions are checked whatever the padding
     for S, f in ((64, 1), (32, 1), (32, 4), (8, 2)):
         M.set_params(sellp_slice=S, sellp_stride=f)
         M.convert("sellp")
@@ -70,7 +71,7 @@ def test_round_trips(gko, dev, name):
         try:
             M.convert(f)
         except gko.GkoError as e:
-            assert f == "ell" and e.status == gko.binding.ERR_FORMAT_TOO_LARGE
+            assert f in ("ell", "sellp") and e.status == gko.binding.ERR_FORMAT_TOO_LARGE
             continue
         M.release("csr")
         assert not M.has("csr")
@@ -91,11 +92,20 @@ def test_full_size_conversions_bit_exact(gko, dev, orc):
     o = orc.to_hybrid(A)
     for k in ("ell_col", "ell_val", "coo_row", "coo_col", "coo_val"):
         assert same(g[k], o[k]), k
-    M.convert("sellp")
-    g = M.export("sellp")
-    o = orc.to_sellp(A, 64, 1)
-    for k in ("slice_len", "slice_set", "col", "val"):
-        assert same(g[k], o[k]), k
+    with pytest.raises(gko.GkoError) as e:  # 13.9x padding: over the limit
+        M.convert("sellp")
+    assert e.value.status == gko.binding.ERR_FORMAT_TOO_LARGE
     M.convert("coo")
     g = M.export("coo")
     assert same(g["row"], np.repeat(np.arange(A["n_rows"], dtype=np.int32), np.diff(A["row_ptr"])))
+    B = syn.workload("banded_4M")
+    MB = gko.Matrix(B)
+    MB.convert("sellp")
+    g = MB.export("sellp")
+    o = orc.to_sellp(B, 64, 1)
+    for k in ("slice_len", "slice_set", "col", "val"):
+        assert same(g[k], o[k]), k
+    MB.convert("ell")
+    g = MB.export("ell")
+    o = orc.to_ell(B)
+    assert same(g["col"], o["col"]) and same(g["val"], o["val"])

@@ -53,12 +53,13 @@ def handles(gko, dev):
     out = {}
     for name, A in mats().items():
         M = gko.Matrix(A)
-        for f in ("coo", "sellp", "hybrid"):
+        for f in ("coo", "hybrid"):
             M.convert(f)
-        try:
-            M.convert("ell")
-        except gko.GkoError as e:
-            assert e.status == gko.binding.ERR_FORMAT_TOO_LARGE
+        for f in ("ell", "sellp"):  # padded formats may be refused
+            try:
+                M.convert(f)
+            except gko.GkoError as e:
+                assert e.status == gko.binding.ERR_FORMAT_TOO_LARGE
         out[name] = (A, M)
     return out
 
@@ -88,14 +89,49 @@ def test_formats_match_oracle(gko, dev, handles, orc, alpha, beta):
         assert M.errors() == 0
 
 
-def test_csr_configs_match_oracle(gko, dev, handles, orc):
+def _applies(A, cfg):
+    """Row-block kernels need max row length <= 128; banded also max |i-j| <= 1024."""
+    L = np.diff(A["row_ptr"])
+    if L.sum() == 0:  # no stored entry: every configuration reduces to y = beta y
+        return True
+    if cfg in (8, 9) and not (1 <= L.max(initial=0) <= 128):
+        return False
+    if cfg == 8:
+        rows = np.repeat(np.arange(A["n_rows"]), L)
+        return np.abs(A["col_idx"].astype(np.int64) - rows).max(initial=0) <= 1024
+    return True
+
+
+@pytest.mark.parametrize("alpha,beta", [(1.0, 0.0), (-0.5, 2.0)])
+def test_csr_configs_match_oracle(gko, dev, handles, orc, alpha, beta):
     for name, (A, M) in handles.items():
         x = syn.vector(A["n_cols"], 13)
         y0 = syn.vector(A["n_rows"], 14)
-        ref, mag = orc.spmv_dot2(A, x, 1.0, 0.0, y0)
-        for cfg in CSR_CONFIGS:
-            y = _run(M, "csr", x, y0, 1.0, 0.0, dev, config=cfg)
+        ref, mag = orc.spmv_dot2(A, x, alpha, beta, y0)
+        for cfg in CSR_CONFIGS + (8, 9):
+            if not _applies(A, cfg):
+                with pytest.raises(gko.GkoError):
+                    _run(M, "csr", x, y0, alpha, beta, dev, config=cfg)
+                continue
+            y = _run(M, "csr", x, y0, alpha, beta, dev, config=cfg)
             assert np.all(np.abs(y - ref) <= 1e-12 * mag + 1e-300), (name, cfg)
+
+
+def test_banded_kernel_with_unaligned_x(gko, dev, orc):
+    """x at an 8-byte (not 16-byte) offset: the banded kernel must fall back
+    to gathers through L1/L2 and still be exact."""
+    import torch
+    A = syn.banded(5000, 64, 16, seed=77)
+    M = gko.Matrix(A)
+    x = syn.vector(A["n_cols"], 78)
+    xbuf = torch.zeros(A["n_cols"] + 1, dtype=torch.float64, device=dev)
+    xbuf[1:] = torch.from_numpy(x).to(dev)
+    xv = xbuf[1:]
+    assert xv.data_ptr() % 16 == 8
+    y = torch.zeros(A["n_rows"], dtype=torch.float64, device=dev)
+    M.spmv(xv, y, config=8)
+    ref, mag = orc.spmv_dot2(A, x)
+    assert np.all(np.abs(y.cpu().numpy() - ref) <= 1e-12 * mag)
 
 
 def test_beta_zero_overwrites_nan(gko, dev, handles):
@@ -114,10 +150,11 @@ def test_integer_inputs_bit_exact_across_kernels(gko, dev, orc):
     x = np.round(syn.vector(A["n_cols"], 22) * 64.0)
     exact = orc.spmv_csr(A, x)  # every partial sum is an integer below 2^53
     M = gko.Matrix(A)
-    for f in ("coo", "sellp", "hybrid"):
+    M.set_params(ell_factor=1000.0)  # allow the padded formats on this skewed matrix
+    for f in ("coo", "sellp", "hybrid", "ell"):
         M.convert(f)
     y0 = np.zeros(A["n_rows"])
-    for f in ("csr", "coo", "sellp", "hybrid"):
+    for f in ("csr", "coo", "sellp", "hybrid", "ell"):
         assert np.array_equal(_run(M, f, x, y0, 1.0, 0.0, dev), exact), f
     for cfg in CSR_CONFIGS:
         assert np.array_equal(_run(M, "csr", x, y0, 1.0, 0.0, dev, config=cfg), exact), cfg
@@ -175,7 +212,7 @@ def test_full_size_sampled_rows(gko, dev, orc, name):
         try:
             M.convert(f)
         except gko.GkoError as e:
-            assert f == "ell" and e.status == gko.binding.ERR_FORMAT_TOO_LARGE
+            assert f in ("ell", "sellp") and e.status == gko.binding.ERR_FORMAT_TOO_LARGE
     x = syn.vector(A["n_cols"], 99)
     rows = np.unique(np.concatenate([np.linspace(0, A["n_rows"] - 1, 1500).astype(np.int64),
                                      np.argsort(np.diff(A["row_ptr"]))[-500:]]))
