@@ -109,23 +109,6 @@ static int read_back(T* host, const T* dev, cudaStream_t st)
     return GKO_OK;
 }
 
-__global__ void fill_i32_kernel(int32_t* __restrict__ p, int64_t n, int32_t v)
-{
-    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
-         i += static_cast<int64_t>(gridDim.x) * blockDim.x)
-        p[i] = v;
-}
-
-static int pad_fill(int32_t* col, double* val, int64_t slots, int64_t alloc, cudaStream_t st)
-{
-    // padding: col = -1 (all bits set), val = +0.0 (all bits clear); the
-    // allocation tail past the slots is zero for bulk copies
-    GKO_CUDA(cudaMemsetAsync(col, 0xff, slots * sizeof(int32_t), st));
-    if (alloc > slots) GKO_CUDA(cudaMemsetAsync(col + slots, 0, (alloc - slots) * sizeof(int32_t), st));
-    GKO_CUDA(cudaMemsetAsync(val, 0, alloc * sizeof(double), st));
-    return GKO_OK;
-}
-
 // Walk the entries [g*P, g*P+P) of a CSR matrix with their row r and slot
 // j = k - row_ptr[r]; F(k, r, j) is called for each.
 template <typename F>
@@ -236,18 +219,31 @@ int convert_coo_to_csr(gko_matrix* A, cudaStream_t st)
 
 // ------------------------------------------------------------ CSR <-> ELL
 
-__global__ void csr_to_ell_kernel(int64_t nnz, int64_t n_rows, int64_t n_pad, int64_t K,
-                                  const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ thr_row,
-                                  const int32_t* __restrict__ col, const double* __restrict__ val,
-                                  int32_t* __restrict__ ecol, double* __restrict__ eval)
+
+// Row r of an ELL part of width K: slot k (column-major, k*n_pad + r) gets
+// the row's k-th entry, or padding (col -1, val +0.0) when k >= its length.
+// One thread per row: the writes of consecutive threads are contiguous, and
+// the padding is written in the same pass.
+__global__ void csr_to_ell_rows_kernel(int64_t n_rows, int64_t n_pad, int64_t K, const int32_t* __restrict__ row_ptr,
+                                       const int32_t* __restrict__ col, const double* __restrict__ val,
+                                       int32_t* __restrict__ ecol, double* __restrict__ eval)
 {
-    const int64_t g = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
-    for_entries(g, kSegP, nnz, n_rows, row_ptr, thr_row, [&](int64_t k, int64_t r, int64_t j) {
-        if (j < K) {
-            ecol[j * n_pad + r] = col[k];
-            eval[j * n_pad + r] = val[k];
+    const int64_t r = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+    if (r >= n_pad) return;
+    int64_t a = 0, L = 0;
+    if (r < n_rows) {
+        a = row_ptr[r];
+        L = row_ptr[r + 1] - a;
+    }
+    for (int64_t k = 0; k < K; ++k) {
+        if (k < L) {
+            ecol[k * n_pad + r] = col[a + k];
+            eval[k * n_pad + r] = val[a + k];
+        } else {
+            ecol[k * n_pad + r] = -1;
+            eval[k * n_pad + r] = 0.0;
         }
-    });
+    }
 }
 
 int ell_fill(gko_matrix* A, EllPart* e, int64_t K, cudaStream_t st)
@@ -258,12 +254,12 @@ int ell_fill(gko_matrix* A, EllPart* e, int64_t K, cudaStream_t st)
     const int64_t alloc = padded_len(slots);
     GKO_TRY(dev_alloc(&e->col, alloc));
     GKO_TRY(dev_alloc(&e->val, alloc));
-    GKO_TRY(pad_fill(e->col, e->val, slots, alloc, st));
-    const int64_t n_thr = (A->nnz + kSegP - 1) / kSegP;
-    if (n_thr > 0 && K > 0)
-        csr_to_ell_kernel<<<ceil_div(n_thr, 256), 256, 0, st>>>(A->nnz, A->n_rows, e->n_pad, K, A->csr.row_ptr,
-                                                                 A->csr.thr_row, A->csr.col, A->csr.val, e->col,
-                                                                 e->val);
+    // the allocation tail past the slots is zero (bulk copies may read it)
+    GKO_CUDA(cudaMemsetAsync(e->col + slots, 0, (alloc - slots) * sizeof(int32_t), st));
+    GKO_CUDA(cudaMemsetAsync(e->val + slots, 0, (alloc - slots) * sizeof(double), st));
+    if (K > 0 && e->n_pad > 0)
+        csr_to_ell_rows_kernel<<<ceil_div(e->n_pad, 256), 256, 0, st>>>(A->n_rows, e->n_pad, K, A->csr.row_ptr,
+                                                                         A->csr.col, A->csr.val, e->col, e->val);
     GKO_CUDA(cudaGetLastError());
     return GKO_OK;
 }
@@ -378,17 +374,33 @@ __global__ void i64_to_i32_kernel(int64_t n, const int64_t* __restrict__ in, int
     out[i] = static_cast<int32_t>(in[i]);
 }
 
-__global__ void csr_to_sellp_kernel(int64_t nnz, int64_t n_rows, int64_t S, const int32_t* __restrict__ row_ptr,
-                                    const int32_t* __restrict__ thr_row, const int32_t* __restrict__ col,
-                                    const double* __restrict__ val, const int32_t* __restrict__ sset,
-                                    int32_t* __restrict__ scol, double* __restrict__ sval)
+// One thread per row slot of a slice (rows past n are all padding): slot k
+// of row s*S + l at (slice_set[s] + k)*S + l gets the row's k-th entry or
+// padding.  Consecutive threads write consecutive slots.
+__global__ void csr_to_sellp_rows_kernel(int64_t n_rows, int64_t S, int64_t n_slices,
+                                         const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                                         const double* __restrict__ val, const int32_t* __restrict__ slen,
+                                         const int32_t* __restrict__ sset, int32_t* __restrict__ scol,
+                                         double* __restrict__ sval)
 {
-    const int64_t g = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
-    for_entries(g, kSegP, nnz, n_rows, row_ptr, thr_row, [&](int64_t k, int64_t r, int64_t j) {
-        const int64_t slot = (static_cast<int64_t>(sset[r / S]) + j) * S + r % S;
-        scol[slot] = col[k];
-        sval[slot] = val[k];
-    });
+    const int64_t r = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+    if (r >= n_slices * S) return;
+    const int64_t s = r / S, l = r % S;
+    const int64_t w = slen[s], base = static_cast<int64_t>(sset[s]) * S + l;
+    int64_t a = 0, L = 0;
+    if (r < n_rows) {
+        a = row_ptr[r];
+        L = row_ptr[r + 1] - a;
+    }
+    for (int64_t k = 0; k < w; ++k) {
+        if (k < L) {
+            scol[base + k * S] = col[a + k];
+            sval[base + k * S] = val[a + k];
+        } else {
+            scol[base + k * S] = -1;
+            sval[base + k * S] = 0.0;
+        }
+    }
 }
 
 int convert_csr_to_sellp(gko_matrix* A, cudaStream_t st)
@@ -427,12 +439,12 @@ int convert_csr_to_sellp(gko_matrix* A, cudaStream_t st)
     const int64_t alloc = padded_len(s.slots);
     GKO_TRY(dev_alloc(&s.col, alloc));
     GKO_TRY(dev_alloc(&s.val, alloc));
-    GKO_TRY(pad_fill(s.col, s.val, s.slots, alloc, st));
-    const int64_t n_thr = (A->nnz + kSegP - 1) / kSegP;
-    if (n_thr > 0)
-        csr_to_sellp_kernel<<<ceil_div(n_thr, 256), 256, 0, st>>>(A->nnz, A->n_rows, s.S, A->csr.row_ptr,
-                                                                   A->csr.thr_row, A->csr.col, A->csr.val,
-                                                                   s.slice_set, s.col, s.val);
+    GKO_CUDA(cudaMemsetAsync(s.col + s.slots, 0, (alloc - s.slots) * sizeof(int32_t), st));
+    GKO_CUDA(cudaMemsetAsync(s.val + s.slots, 0, (alloc - s.slots) * sizeof(double), st));
+    if (s.n_slices > 0)
+        csr_to_sellp_rows_kernel<<<ceil_div(s.n_slices * s.S, 256), 256, 0, st>>>(
+            A->n_rows, s.S, s.n_slices, A->csr.row_ptr, A->csr.col, A->csr.val, s.slice_len, s.slice_set, s.col,
+            s.val);
     GKO_CUDA(cudaFreeAsync(w, st));
     GKO_CUDA(cudaFreeAsync(off, st));
     GKO_CUDA(cudaGetLastError());
@@ -491,25 +503,73 @@ int convert_sellp_to_csr(gko_matrix* A, cudaStream_t st)
 
 // --------------------------------------------------------- CSR <-> hybrid
 
-__global__ void len_hist_kernel(int64_t n_rows, const int32_t* __restrict__ row_ptr, int64_t* __restrict__ hist)
+// Row-length histogram: shared-memory bins for lengths < 4096 (flushed
+// once per block), global atomics for longer rows.  Integer counts: the
+// result does not depend on the order of the additions.
+constexpr int kHistShared = 4096;
+__global__ void len_hist_kernel(int64_t n_rows, int64_t kmax, const int32_t* __restrict__ row_ptr,
+                                int64_t* __restrict__ hist)
 {
-    const int64_t r = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
-    if (r >= n_rows) return;
-    atomicAdd(reinterpret_cast<unsigned long long*>(hist + (row_ptr[r + 1] - row_ptr[r])), 1ull);
+    __shared__ unsigned int sh[kHistShared];
+    const int nb = static_cast<int>(min(kmax + 1, static_cast<int64_t>(kHistShared)));
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) sh[i] = 0;
+    __syncthreads();
+    for (int64_t r = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; r < n_rows;
+         r += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int L = row_ptr[r + 1] - row_ptr[r];
+        if (L < nb)
+            atomicAdd(&sh[L], 1u);
+        else
+            atomicAdd(reinterpret_cast<unsigned long long*>(hist + L), 1ull);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nb; i += blockDim.x)
+        if (sh[i]) atomicAdd(reinterpret_cast<unsigned long long*>(hist + i), static_cast<unsigned long long>(sh[i]));
 }
 
-// K_h = argmin_K n_pad*K*(s_v+4) + overflow(K)*(s_v+8), ties to smaller K.
-// One thread walks K downwards keeping the counts of longer rows; the
-// byte counts are integers below 2^53, so the double sums are exact.
-__global__ void hybrid_width_kernel(int64_t kmax, int64_t n_pad, int64_t s_v, const int64_t* __restrict__ hist,
-                                    int64_t* __restrict__ out)
+// K_h = argmin_K n_pad*K*(s_v+4) + overflow(K)*(s_v+8), ties to smaller K,
+// with overflow(K) = sum_{L > K} (L - K) hist[L].  One block of 1024
+// threads: thread t owns the lengths of a contiguous chunk, the counts of
+// longer rows come from a suffix scan of the chunk totals, each thread
+// walks its chunk downwards, and a block argmin picks the best K.  Byte
+// counts are integers below 2^53, so the double arithmetic is exact and
+// the choice is the same as any sequential evaluation.
+constexpr int kWidthThreads = 1024;
+__global__ void __launch_bounds__(kWidthThreads)
+    hybrid_width_kernel(int64_t kmax, int64_t n_pad, int64_t s_v, const int64_t* __restrict__ hist,
+                        int64_t* __restrict__ out)
 {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    int64_t cnt_gt = 0, sum_gt = 0;  // rows with length > K, and their total length
+    __shared__ int64_t s_cnt[kWidthThreads], s_sum[kWidthThreads];
+    __shared__ double s_best[kWidthThreads];
+    __shared__ int64_t s_bk[kWidthThreads];
+    const int t = threadIdx.x;
+    const int64_t nbins = kmax + 1;
+    const int64_t ch = (nbins + kWidthThreads - 1) / kWidthThreads;
+    const int64_t c0 = t * ch, c1 = min(c0 + ch, nbins);
+    int64_t cnt = 0, sum = 0;
+    for (int64_t L = c0; L < c1; ++L) {
+        cnt += hist[L];
+        sum += L * hist[L];
+    }
+    s_cnt[t] = cnt;
+    s_sum[t] = sum;
+    __syncthreads();
+    // inclusive suffix scan over threads (Hillis-Steele on integers)
+    for (int o = 1; o < kWidthThreads; o <<= 1) {
+        const int64_t a = t + o < kWidthThreads ? s_cnt[t + o] : 0;
+        const int64_t b = t + o < kWidthThreads ? s_sum[t + o] : 0;
+        __syncthreads();
+        s_cnt[t] += a;
+        s_sum[t] += b;
+        __syncthreads();
+    }
+    // rows with length >= c1 (chunks after this one)
+    int64_t cnt_gt = t + 1 < kWidthThreads ? s_cnt[t + 1] : 0;
+    int64_t sum_gt = t + 1 < kWidthThreads ? s_sum[t + 1] : 0;
     double best = -1.0;
-    int64_t best_k = 0;
-    for (int64_t K = kmax; K >= 0; --K) {
-        if (K + 1 <= kmax) {
+    int64_t best_k = -1;
+    for (int64_t K = c1 - 1; K >= c0; --K) {
+        if (K + 1 < c1) {  // hist[K + 1] of this chunk joins the "longer than K" rows
             cnt_gt += hist[K + 1];
             sum_gt += (K + 1) * hist[K + 1];
         }
@@ -521,7 +581,22 @@ __global__ void hybrid_width_kernel(int64_t kmax, int64_t n_pad, int64_t s_v, co
             best_k = K;
         }
     }
-    out[0] = best_k;
+    s_best[t] = best;
+    s_bk[t] = best_k;
+    __syncthreads();
+    for (int o = kWidthThreads / 2; o; o >>= 1) {
+        if (t < o) {
+            const double b2 = s_best[t + o];
+            const int64_t k2 = s_bk[t + o];
+            const bool take = k2 >= 0 && (s_bk[t] < 0 || b2 < s_best[t] || (b2 == s_best[t] && k2 < s_bk[t]));
+            if (take) {
+                s_best[t] = b2;
+                s_bk[t] = k2;
+            }
+        }
+        __syncthreads();
+    }
+    if (t == 0) out[0] = s_bk[0] < 0 ? 0 : s_bk[0];
 }
 
 __global__ void overflow_count_kernel(int64_t n_rows, int64_t K, const int32_t* __restrict__ row_ptr,
@@ -558,9 +633,10 @@ int convert_csr_to_hybrid(gko_matrix* A, cudaStream_t st)
     GKO_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&hist), (kmax + 2) * sizeof(int64_t), st));
     GKO_CUDA(cudaMemsetAsync(hist, 0, (kmax + 2) * sizeof(int64_t), st));
     const int grid = ceil_div(std::max<int64_t>(A->n_rows, 1), 256);
-    if (A->n_rows > 0) len_hist_kernel<<<grid, 256, 0, st>>>(A->n_rows, A->csr.row_ptr, hist);
+    if (A->n_rows > 0)
+        len_hist_kernel<<<std::min(grid, 152 * 2), 256, 0, st>>>(A->n_rows, kmax, A->csr.row_ptr, hist);
     const int64_t n_pad = (A->n_rows + 31) / 32 * 32;
-    hybrid_width_kernel<<<1, 32, 0, st>>>(kmax, n_pad, 8, hist, hist + kmax + 1);
+    hybrid_width_kernel<<<1, kWidthThreads, 0, st>>>(kmax, n_pad, 8, hist, hist + kmax + 1);
     int64_t K = 0;
     GKO_TRY(read_back(&K, hist + kmax + 1, st));
     GKO_CUDA(cudaFreeAsync(hist, st));
@@ -666,23 +742,33 @@ int convert_hybrid_to_csr(gko_matrix* A, cudaStream_t st)
 
 // Flags: bit 0 row_ptr[0] != 0 or row_ptr[n] != nnz; bit 1 row_ptr not
 // monotone; bit 2 column out of range; bit 3 columns not strictly ascending.
-__global__ void validate_kernel(int64_t n_rows, int64_t n_cols, int64_t nnz, const int32_t* __restrict__ row_ptr,
-                                const int32_t* __restrict__ col, uint32_t* __restrict__ flags)
+__global__ void validate_rows_kernel(int64_t n_rows, int64_t nnz, const int32_t* __restrict__ row_ptr,
+                                     uint32_t* __restrict__ flags)
 {
     const int64_t r = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
     if (r == 0 && (row_ptr[0] != 0 || row_ptr[n_rows] != nnz)) atomicOr(flags, 1u);
     if (r >= n_rows) return;
     const int32_t a = row_ptr[r], b = row_ptr[r + 1];
-    if (b < a || a < 0 || b > nnz) {
-        atomicOr(flags, 2u);
-        return;
-    }
-    for (int32_t k = a; k < b; ++k) {
-        const int32_t c = col[k];
-        if (c < 0 || c >= n_cols) atomicOr(flags, 4u);
-        if (k > a && c <= col[k - 1]) atomicOr(flags, 8u);
-    }
+    if (b < a || a < 0 || b > nnz) atomicOr(flags, 2u);
 }
+
+// entry-parallel (equal chunks of entries, any row lengths): columns in
+// range and strictly ascending within each row
+__global__ void validate_entries_kernel(int64_t n_rows, int64_t n_cols, int64_t nnz,
+                                        const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ thr_row,
+                                        const int32_t* __restrict__ col, uint32_t* __restrict__ flags)
+{
+    const int64_t g = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+    uint32_t f = 0;
+    for_entries(g, kSegP, nnz, n_rows, row_ptr, thr_row, [&](int64_t k, int64_t, int64_t j) {
+        const int32_t c = col[k];
+        if (c < 0 || c >= n_cols) f |= 4u;
+        if (j > 0 && c <= col[k - 1]) f |= 8u;
+    });
+    if (f) atomicOr(flags, f);
+}
+
+int compute_thr_row(int64_t n_rows, int64_t nnz, const int32_t* row_ptr, int32_t* thr_row, cudaStream_t st);
 
 int validate_csr(int64_t n_rows, int64_t n_cols, int64_t nnz, const int32_t* row_ptr, const int32_t* col,
                  cudaStream_t st)
@@ -690,10 +776,18 @@ int validate_csr(int64_t n_rows, int64_t n_cols, int64_t nnz, const int32_t* row
     uint32_t* d = nullptr;
     GKO_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&d), sizeof(uint32_t), st));
     GKO_CUDA(cudaMemsetAsync(d, 0, sizeof(uint32_t), st));
-    validate_kernel<<<ceil_div(std::max<int64_t>(n_rows, 1), 256), 256, 0, st>>>(n_rows, n_cols, nnz, row_ptr, col,
-                                                                                 d);
+    validate_rows_kernel<<<ceil_div(std::max<int64_t>(n_rows, 1), 256), 256, 0, st>>>(n_rows, nnz, row_ptr, d);
     uint32_t h = 0;
     GKO_TRY(read_back(&h, d, st));
+    if (h == 0 && nnz > 0) {  // row pointers are valid: split the entries evenly
+        const int64_t n_thr = (nnz + kSegP - 1) / kSegP;
+        int32_t* tr = nullptr;
+        GKO_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&tr), n_thr * sizeof(int32_t), st));
+        GKO_TRY(compute_thr_row(n_rows, nnz, row_ptr, tr, st));
+        validate_entries_kernel<<<ceil_div(n_thr, 256), 256, 0, st>>>(n_rows, n_cols, nnz, row_ptr, tr, col, d);
+        GKO_TRY(read_back(&h, d, st));
+        GKO_CUDA(cudaFreeAsync(tr, st));
+    }
     GKO_CUDA(cudaFreeAsync(d, st));
     GKO_CUDA(cudaGetLastError());
     if (h) {

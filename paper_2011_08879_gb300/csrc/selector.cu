@@ -368,11 +368,20 @@ int gko_select_format(gko_matrix* A, int* fmt, int* config, void* stream)
     GKO_CUDA(cudaMemcpyAsync(out, d + 12, g_sel.n_out * sizeof(float), cudaMemcpyDeviceToHost, st));
     GKO_CUDA(cudaFreeAsync(d, st));
     GKO_CUDA(cudaStreamSynchronize(st));
-    int best = 0;
-    for (int i = 1; i < g_sel.n_out; ++i)
-        if (out[i] < out[best]) best = i;
-    *fmt = g_sel.fmts[best];
-    *config = g_sel.cfgs[best];
+    // argmin over the candidates this handle can run: its format is
+    // materialised and the kernel configuration applies to the matrix
+    int best = -1;
+    for (int i = 0; i < g_sel.n_out; ++i) {
+        const int f = g_sel.fmts[i], c = g_sel.cfgs[i];
+        if (f < 0 || f > GKO_FMT_HYBRID || !A->has[f]) continue;
+        if ((c == GKO_CFG_CSR_ROWBLOCK || c == GKO_CFG_CSR_BANDED) && rowblock_rows(A) == 0) continue;
+        if (c == GKO_CFG_CSR_BANDED && (A->csr.band < 0 || A->csr.band > 1024)) continue;
+        if (best < 0 || out[i] < out[best]) best = i;
+    }
+    if (best >= 0) {
+        *fmt = g_sel.fmts[best];
+        *config = g_sel.cfgs[best];
+    }
     return GKO_OK;
 }
 

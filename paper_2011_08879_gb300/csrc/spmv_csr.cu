@@ -81,6 +81,14 @@ void seg_free(SegArrays* s)
     s->n_tiles = 0;
 }
 
+int compute_thr_row(int64_t n_rows, int64_t nnz, const int32_t* row_ptr, int32_t* thr_row, cudaStream_t st)
+{
+    const int64_t n_thr = (nnz + kSegP - 1) / kSegP;
+    if (n_thr > 0) thr_row_kernel<<<ceil_div(n_thr, 256), 256, 0, st>>>(n_rows, n_thr, kSegP, row_ptr, thr_row);
+    GKO_CUDA(cudaGetLastError());
+    return GKO_OK;
+}
+
 int csr_analyse(gko_matrix* A, cudaStream_t st)
 {
     CsrPart& c = A->csr;

@@ -386,6 +386,52 @@ def batched_spd(count: int = 4096, seed: int = 7, n_min: int = 32, n_max: int = 
     return d
 
 
+SWEEP_STRUCTURES = ("stencil", "banded", "powerlaw", "random")
+
+
+def sweep_params(seed: int, n_min: float = 1e4, n_max: float = 2e6, m_min: float = 4.0, m_max: float = 200.0,
+                 nnz_cap: float = 1.5e7) -> dict:
+    """Shape of one selector-sweep matrix: structure equiprobable over
+    SWEEP_STRUCTURES, rows log-uniform in [n_min, n_max], mean entries per
+    row log-uniform in [m_min, m_max]; rows are reduced so that rows * mean
+    stays below nnz_cap."""
+    u = uniform01(seed, S_STRUCT, np.arange(4, dtype=np.uint64))
+    structure = SWEEP_STRUCTURES[min(3, int(u[0] * 4))]
+    n = 10 ** (math.log10(n_min) + u[1] * (math.log10(n_max) - math.log10(n_min)))
+    m = 10 ** (math.log10(m_min) + u[2] * (math.log10(m_max) - math.log10(m_min)))
+    n = int(max(n_min / 4, min(n, nnz_cap / m)))
+    return dict(structure=structure, n=n, mean=m, u3=float(u[3]))
+
+
+def sweep_matrix(seed: int, **kw) -> dict:
+    """One matrix of the selector sweep (see sweep_params); values uniform
+    in [-1, 1)."""
+    p = sweep_params(seed, **kw)
+    n, m, s = p["n"], p["mean"], p["structure"]
+    if s == "stencil":  # 2D 5-point, 3D 7-point or 3D 27-point pattern by u3
+        kind = int(p["u3"] * 3)
+        if kind == 0:
+            side = max(2, int(round(n ** 0.5)))
+            A = laplace2d(side)
+            A["val"] = uniform_pm1(seed, S_VAL, np.arange(len(A["col_idx"]), dtype=np.uint64))
+        elif kind == 1:
+            side = max(2, int(round(n ** (1 / 3))))
+            A = diffusion7(side, 1.0, seed=seed)
+            A["val"] = uniform_pm1(seed, S_VAL, np.arange(len(A["col_idx"]), dtype=np.uint64))
+        else:
+            A = stencil27(max(2, int(round(n ** (1 / 3)))), seed=seed)
+    elif s == "banded":
+        per_row = max(2, int(round(m)))
+        half_bw = max(per_row, int(round(per_row * (1 + 7 * p["u3"]))))
+        A = banded(n, half_bw, per_row, seed=seed)
+    elif s == "powerlaw":
+        A = powerlaw(n, m, 1.5, min(20000, n), seed=seed)
+    else:
+        A = uniform_random(n, m, seed)
+    A["structure"] = s
+    return A
+
+
 # Workloads of the benchmark configurations, with their seeds.
 def workload(name: str) -> dict:
     """The named synthetic workload at full size."""
