@@ -95,17 +95,33 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
+def kernel_source_hash():
+    """Hash of the CUDA sources (the counters of a capture are valid only for
+    the kernels they were taken on)."""
+    import glob
+    import hashlib
+    h = hashlib.sha256()
+    for p in sorted(glob.glob(os.path.join(ROOT, "paper_2011_08879_gb300", "csrc", "*"))):
+        if p.endswith((".cu", ".cuh", ".h")):
+            with open(p, "rb") as f:
+                h.update(f.read())
+    return h.hexdigest()[:16]
+
+
 def profile_traffic():
-    """DRAM bytes per launch from the committed ncu summary, if present:
-    lines 'traffic <matrix>/<format> <bytes>'."""
-    out = {}
+    """DRAM bytes per launch from the committed ncu summary, if present and
+    taken on the current kernel sources: lines 'source <hash>' and
+    'traffic <matrix>/<format> <bytes>'."""
+    out, src = {}, None
     path = os.path.join(ROOT, "profiles", "spmv_dram_traffic.txt")
     if os.path.exists(path):
         for line in open(path):
             parts = line.split()
+            if len(parts) == 2 and parts[0] == "source":
+                src = parts[1]
             if len(parts) == 3 and parts[0] == "traffic":
                 out[parts[1]] = float(parts[2])
-    return out
+    return out if src == kernel_source_hash() else {}
 
 
 # ----------------------------------------------------------------- clocks
