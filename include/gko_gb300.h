@@ -190,6 +190,41 @@ int gko_spmv_config(int fmt, int config, const gko_matrix* A, const double* x, d
 int gko_spmv_host(int fmt, const gko_matrix* A, const double* x_host, double* y_host, double alpha,
                   double beta, void* stream);
 
+/* COO SpMV that allocates no memory at all.  The paper has no counterpart:
+ * this entry point exists for callers that cannot call cudaMalloc (or any
+ * allocator) while they run -- code captured into CUDA graphs or replayed
+ * with a fixed memory footprint, real-time loops that cannot take an
+ * allocation's latency or failure, and applications whose device memory
+ * belongs to another allocator (a framework's caching pool) that a
+ * library-side cudaMalloc would bypass.
+ *
+ * y = alpha * A * x + beta * y with A given directly by caller-owned device
+ * arrays row[nnz], col[nnz], val[nnz] (COO sorted by (row, col), indices in
+ * range; not validated), x[n_cols], y[n_rows].  row, col and val must be
+ * 16-byte aligned; they are not read past nnz.  beta == 0: y is not read.
+ * Same kernel and accuracy as gko_spmv(GKO_FMT_COO, ...).
+ *
+ * Scratch: the carries of rows that cross tiles live in a fixed device
+ * array inside the library (GKO_NOALLOC_MAX_TILES tiles of 2816 entries,
+ * 896 KiB, held by every GPU that loads the library until exit), so nnz
+ * may not exceed GKO_NOALLOC_MAX_TILES * 2816 (GKO_ERR_INVALID_ARG beyond).
+ * All calls share that array: calls that can overlap on the GPU (different
+ * streams, or different host threads on one device) race and must be
+ * serialised by the caller.  Nothing needs clearing between calls (each
+ * call writes every carry it reads).
+ *
+ * The first call on a device looks up the device address of the array
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before capturing a stream.  Later calls only launch kernels.
+ *
+ * err_flags: optional caller-owned device word; bit 0 is ORed in if a
+ * bounded wait for a bulk copy gave up (y is then incomplete).  NULL: not
+ * reported.  Asynchronous on stream. */
+#define GKO_NOALLOC_MAX_TILES 32768
+int gko_spmv_coo_noalloc(int64_t n_rows, int64_t n_cols, int64_t nnz, const int32_t* row, const int32_t* col,
+                         const double* val, const double* x, double* y, double alpha, double beta,
+                         uint32_t* err_flags, void* stream);
+
 /* ----------------------------------------------------------- solvers */
 
 /* Conjugate gradients (Hestenes-Stiefel; the Krylov solvers of Sec. 6.2)

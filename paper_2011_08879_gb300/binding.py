@@ -57,6 +57,7 @@ _SIGS = {
     "gko_spmv": (_INT, [_INT, _P, _P, _P, _D, _D, _P]),
     "gko_spmv_config": (_INT, [_INT, _INT, _P, _P, _P, _D, _D, _P]),
     "gko_spmv_host": (_INT, [_INT, _P, _P, _P, _D, _D, _P]),
+    "gko_spmv_coo_noalloc": (_INT, [_I64, _I64, _I64, _P, _P, _P, _P, _P, _D, _D, _P, _P]),
     "gko_cg": (_INT, [_P, _INT, _P, _P, _D, _INT, _P, C.POINTER(SolveInfo)]),
     "gko_cg_mixed": (_INT, [_P, _INT, _P, _P, _D, _INT, _D, _INT, _P, C.POINTER(SolveInfo)]),
     "gko_batch_create": (_INT, [_I64, _P, _P, _P, _P, _INT, _P, C.POINTER(_P)]),
@@ -154,6 +155,13 @@ def gko_spmv_config(fmt, config, A, x, y, alpha=1.0, beta=0.0, stream=0) -> None
 
 def gko_spmv_host(fmt, A, x_host, y_host, alpha=1.0, beta=0.0, stream=0) -> None:
     _check(lib.gko_spmv_host(fmt, A, x_host, y_host, alpha, beta, stream), "gko_spmv_host")
+
+
+def gko_spmv_coo_noalloc(n_rows, n_cols, nnz, row, col, val, x, y, alpha=1.0, beta=0.0, err_flags=None,
+                         stream=0) -> None:
+    """COO SpMV without any allocation (see the header); device pointers."""
+    _check(lib.gko_spmv_coo_noalloc(n_rows, n_cols, nnz, row, col, val, x, y, alpha, beta, err_flags, stream),
+           "gko_spmv_coo_noalloc")
 
 
 def gko_cg(A, fmt, b, x, tol, maxit, stream=0, raise_on=()) -> SolveInfo:

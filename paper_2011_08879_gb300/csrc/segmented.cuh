@@ -313,7 +313,10 @@ __device__ __forceinline__ SegThreadOut<T> seg_thread(int ls, int le, int t0, in
 // (thr_row[g] = row holding entry g*P).  kCoo = true: COO with row[].
 // kSkipEmpty: rows without entries are left untouched (used to add the COO
 // part of the hybrid format onto the ELL part's result, with beta = 1).
-template <int P, typename V, typename T, bool kAlpha, bool kBeta, bool kCoo, bool kSkipEmpty>
+// kExactTail (COO only): the arrays end exactly at nnz (caller-owned, not
+// padded), so the last tile bulk-copies only whole 16-byte groups and the
+// threads load the remaining few entries themselves.
+template <int P, typename V, typename T, bool kAlpha, bool kBeta, bool kCoo, bool kSkipEmpty, bool kExactTail = false>
 __global__ void __launch_bounds__(kSegThreads, kSegCtasPerSm)
     seg_spmv_kernel(int64_t n_rows64, int64_t nnz64, const int32_t* __restrict__ row_ptr,
                     const int32_t* __restrict__ rows, const int32_t* __restrict__ col,
@@ -322,6 +325,7 @@ __global__ void __launch_bounds__(kSegThreads, kSegCtasPerSm)
 {
     using S = SegShape<P>;
     using G = SegStage<P, V, kCoo>;
+    static_assert(!kExactTail || kCoo, "exact tails are implemented for COO");
     constexpr int kAlign = 16 / sizeof(V) > 4 ? 16 / sizeof(V) : 4;  // entries per 16-byte group
     extern __shared__ __align__(16) unsigned char smem[];
     T* s_part = reinterpret_cast<T*>(smem + 2 * G::kBytes);
@@ -348,7 +352,9 @@ __global__ void __launch_bounds__(kSegThreads, kSegCtasPerSm)
     auto issue = [&](int tile, int st, int32_t a, int32_t b, int32_t c) {
         const int t0 = tile * S::kTile;
         const int t1 = min(t0 + S::kTile, nnz);
-        const int cnt_al = (t1 - t0 + kAlign - 1) / kAlign * kAlign;
+        // padded arrays: round up to whole 16-byte groups; exact arrays:
+        // round down (the ragged rest is loaded by the threads)
+        const int cnt_al = kExactTail ? (t1 - t0) / kAlign * kAlign : (t1 - t0 + kAlign - 1) / kAlign * kAlign;
         uint32_t bytes = cnt_al * static_cast<uint32_t>(sizeof(V) + sizeof(int32_t) + (kCoo ? sizeof(int32_t) : 0));
         SegTileInfo ti;
         ti.t0 = t0;
@@ -372,12 +378,12 @@ __global__ void __launch_bounds__(kSegThreads, kSegCtasPerSm)
         }
         info[st] = ti;
         mbar_arrive_expect_tx(&bar[st], bytes);
-        bulk_g2s(stage_val(st), val + t0, cnt_al * sizeof(V), &bar[st]);
-        bulk_g2s(stage_col(st), col + t0, cnt_al * sizeof(int32_t), &bar[st]);
-        if (kCoo)
-            bulk_g2s(stage_aux(st), rows + t0, cnt_al * sizeof(int32_t), &bar[st]);
-        else if (ti.staged)
-            bulk_g2s(stage_aux(st), row_ptr + ti.a_lo, a_cnt * sizeof(int32_t), &bar[st]);
+        if (cnt_al > 0) {  // (an exact tail of fewer than 4 entries has no whole group)
+            bulk_g2s(stage_val(st), val + t0, cnt_al * sizeof(V), &bar[st]);
+            bulk_g2s(stage_col(st), col + t0, cnt_al * sizeof(int32_t), &bar[st]);
+            if (kCoo) bulk_g2s(stage_aux(st), rows + t0, cnt_al * sizeof(int32_t), &bar[st]);
+        }
+        if (!kCoo && ti.staged) bulk_g2s(stage_aux(st), row_ptr + ti.a_lo, a_cnt * sizeof(int32_t), &bar[st]);
     };
     // metadata loads needed to issue `tile` (read early, used later)
     auto meta_a = [&](int tile) -> int32_t {
@@ -422,6 +428,16 @@ __global__ void __launch_bounds__(kSegThreads, kSegCtasPerSm)
         bool landed = mbar_wait_bounded(&bar[st], parity, err);
         if (!landed) landed = mbar_wait_bounded(&bar[st], parity, err);  // copies still in flight: once more
         if (!__syncthreads_and(landed)) return;                           // CTA-uniform exit
+        if (kExactTail) {  // entries past the last whole 16-byte group (last tile only)
+            const int tx0 = info[st].t0;
+            const int cx = min(tx0 + S::kTile, nnz) - tx0;
+            for (int i = cx / kAlign * kAlign + tid; i < cx; i += kSegThreads) {
+                stage_val(st)[i] = val[tx0 + i];
+                stage_col(st)[i] = col[tx0 + i];
+                stage_aux(st)[i] = rows[tx0 + i];
+            }
+            __syncthreads();
+        }
 
         // prefetch what the next issue and the next tile need
         const int t_issue = tile + 2 * stride;
@@ -559,7 +575,7 @@ inline int seg_grid_ctas()
 // Host-side launcher of the load-balanced kernel + fix-up for one
 // (V, T) pair.  sc must hold ceil(nnz / TILE) tiles.  Sets the dynamic
 // shared-memory attribute on first use (per instantiation).
-template <int P, typename V, typename T, bool kAlpha, bool kBeta, bool kCoo, bool kSkip>
+template <int P, typename V, typename T, bool kAlpha, bool kBeta, bool kCoo, bool kSkip, bool kExact = false>
 inline cudaError_t seg_launch(int64_t n_rows, int64_t nnz, const int32_t* row_ptr, const int32_t* rows,
                               const int32_t* col, const V* val, const int32_t* thr_row, SegScratchT<T> sc,
                               const T* x, T* y, T alpha, T beta, uint32_t* err, cudaStream_t st)
@@ -567,15 +583,16 @@ inline cudaError_t seg_launch(int64_t n_rows, int64_t nnz, const int32_t* row_pt
     constexpr size_t smem = seg_smem_bytes<P, V, T, kCoo>();
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(seg_spmv_kernel<P, V, T, kAlpha, kBeta, kCoo, kSkip>,
+        cudaError_t e = cudaFuncSetAttribute(seg_spmv_kernel<P, V, T, kAlpha, kBeta, kCoo, kSkip, kExact>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
     const int64_t tiles = (nnz + SegShape<P>::kTile - 1) / SegShape<P>::kTile;
     const int64_t grid = tiles < seg_grid_ctas() ? tiles : seg_grid_ctas();
-    seg_spmv_kernel<P, V, T, kAlpha, kBeta, kCoo, kSkip><<<static_cast<unsigned>(grid), kSegThreads, smem, st>>>(
-        n_rows, nnz, row_ptr, rows, col, val, thr_row, x, y, alpha, beta, sc, err);
+    seg_spmv_kernel<P, V, T, kAlpha, kBeta, kCoo, kSkip, kExact>
+        <<<static_cast<unsigned>(grid), kSegThreads, smem, st>>>(n_rows, nnz, row_ptr, rows, col, val, thr_row, x, y,
+                                                                 alpha, beta, sc, err);
     if (tiles > 1)
         seg_fixup_kernel<kAlpha, kBeta, T>
             <<<static_cast<unsigned>((tiles + 255) / 256), 256, 0, st>>>(tiles, sc, y, alpha, beta);
