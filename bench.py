@@ -140,7 +140,7 @@ class ClockSampler:
              "clocks_event_reasons.sw_power_cap")
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -152,7 +152,12 @@ class ClockSampler:
         for line in self.proc.stdout:
             p = [s.strip() for s in line.split(",")]
             if len(p) == 7:
-                self.samples.append(p)
+                self.samples.append((time.perf_counter(), p))
+
+    def window(self, t0, t1, slack=0.06):
+        """Keep the samples taken within [t0 - slack, t1 + slack]."""
+        inside = [s for s in self.samples if t0 - slack <= s[0] <= t1 + slack]
+        self.samples = inside or self.samples[-2:]
 
     def __exit__(self, *a):
         if self.proc:
@@ -165,12 +170,13 @@ class ClockSampler:
     def summary(self):
         if not self.samples:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
-        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
-        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        rows = [s[1] for s in self.samples]
+        sm = [float(s[0]) for s in rows if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in rows if s[1].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for s in self.samples for i in range(4) if s[3 + i].lower().startswith("active")})
+        reasons = sorted({names[i] for s in rows for i in range(4) if s[3 + i].lower().startswith("active")})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(self.samples)}
+                "reasons": reasons, "samples": len(rows)}
 
 
 # ------------------------------------------------------------ CPU baseline
@@ -258,19 +264,24 @@ def run_gpu(args):
             e1.record(stream)
             times.append((c, e0, e1))
 
-    for _ in range(args.warmup):
-        one_step([])
-    torch.cuda.synchronize()
-    if world > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
     times = []
+    # the sampler starts before the warm-up (nvidia-smi needs a moment to
+    # produce its first line); only samples inside the timed window are kept
     with ClockSampler(local) as clk:
+        for _ in range(args.warmup):
+            one_step([])
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
         w0 = time.perf_counter()
         for _ in range(args.steps):
             one_step(times)
         torch.cuda.synchronize()
-        wall = time.perf_counter() - w0
+        w1 = time.perf_counter()
+        wall = w1 - w0
+        time.sleep(0.06)
+    clk.window(w0, w1)
     if world > 1:
         torch.distributed.barrier()
     per_case = {}
