@@ -238,13 +238,32 @@ int gko_spmv_coo_noalloc(int64_t n_rows, int64_t n_cols, int64_t nnz, const int3
 int gko_cg(const gko_matrix* A, int fmt, const double* b, double* x, double tol, int maxit,
            void* stream, gko_solve_info* info);
 
+/* CG in the single-reduction form of Chronopoulos and Gear (J. Comput.
+ * Appl. Math. 25, 1989), the same Krylov method as gko_cg (Sec. 6.2) with
+ * its two dot products merged: each step computes w = A r, gamma = r.r and
+ * delta = w.r in one pass and one grid reduction, then
+ *   beta = gamma / gamma_old, alpha = gamma / (delta - beta gamma / alpha_old),
+ *   p = r + beta p, s = w + beta s (s = A p), x += alpha p, r -= alpha s
+ * in one vector pass: two kernel launches per step (for CSR matrices with
+ * rows of similar length the dots run inside the SpMV kernel; other formats
+ * add one dot launch).  Arguments, stopping (recursive residual, then the
+ * FP64 true residual, up to four confirmations), breakdown (non-positive
+ * delta - beta gamma / alpha_old, or NaN), errors and synchronisation are
+ * those of gko_cg; info->iterations counts steps taken (updates of x).
+ * Iterates equal gko_cg's up to rounding. */
+int gko_cg_single_reduction(const gko_matrix* A, int fmt, const double* b, double* x, double tol, int maxit,
+                            void* stream, gko_solve_info* info);
+
 /* Mixed-precision CG with FP64 iterative refinement.  The inner CG runs on
  * a copy of A stored in inner_dtype (GKO_F32 or GKO_BF16; off-diagonals
  * rounded to nearest-even, the diagonal a_ii + sum_j(|rn(a_ij)| - |a_ij|)
- * rounded up, which keeps diagonal dominance) with FP32 vectors and FP32
- * accumulation, to relative residual inner_tol.  The outer loop forms
+ * formed in FP64 and rounded to nearest-even, which keeps the row sums of
+ * matrices with non-positive off-diagonals) with FP32 vectors and FP32
+ * accumulation, in the single-reduction form above, from d = 0 to relative
+ * recursive residual inner_tol or inner_maxit steps.  The outer loop forms
  * r = b - A x, x += correction and the norms in FP64 and stops at
  * ||r|| <= tol ||b||.  The low-precision copy is cached in the handle.
+ * info->iterations = inner steps in total, outer_iterations = corrections.
  * Synchronises the stream. */
 int gko_cg_mixed(gko_matrix* A, int inner_dtype, const double* b, double* x, double tol,
                  int maxit_outer, double inner_tol, int inner_maxit, void* stream,

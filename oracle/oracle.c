@@ -19,7 +19,8 @@
  * Sec. 6.2 for Krylov solvers built on SpMV); the formats it refers to but
  * does not define follow their standard definitions: ELL and hybrid ELL+COO
  * (Bell and Garland, SC'09), SELL-P (Anzt, Tomov and Dongarra, 2014);
- * CG is the method of Hestenes and Stiefel (1952); Dot2 is Algorithm 5.3 of
+ * CG is the method of Hestenes and Stiefel (1952), also in the
+ * single-reduction form of Chronopoulos and Gear (1989); Dot2 is Algorithm 5.3 of
  * Ogita, Rump and Oishi, "Accurate sum and dot product" (SISC 2005).
  */
 #include <math.h>
@@ -593,6 +594,97 @@ int orc_cg(int64_t n, const int32_t *row_ptr, const int32_t *col, const double *
     free(r);
     free(p);
     free(q);
+    return status;
+}
+
+/* CG in the single-reduction form of Chronopoulos and Gear ("s-step
+ * iterative methods for symmetric linear systems", J. Comput. Appl. Math.
+ * 25, 1989, with s = 1): the residual's product w = A r and the two inner
+ * products gamma = r.r and delta = w.r are formed together, and the search
+ * direction's product s = A p is carried by a recurrence:
+ *   r = b - A x0, p = 0, s = 0
+ *   repeat: w = A r; gamma = r.r; delta = w.r
+ *           beta = gamma / gamma_old              (0 at the first step)
+ *           alpha = gamma / (delta - beta gamma / alpha_old)
+ *                                                 (gamma / delta at the first step)
+ *           p = r + beta p; s = w + beta s; x += alpha p; r -= alpha s
+ * In exact arithmetic the iterates equal orc_cg's.  Stopping is tested on
+ * gamma of the current residual, with the same true-residual confirmation
+ * as orc_cg (an unconfirmed test lets the step proceed); a non-positive or
+ * NaN denominator is a breakdown.  *iters counts the updates of x. */
+int orc_cg_single_reduction(int64_t n, const int32_t *row_ptr, const int32_t *col,
+                            const double *val, const double *b, double *x, double tol,
+                            int maxit, int *iters, double *rel_res)
+{
+    double nb = nrm2(n, b);
+    *iters = 0;
+    if (nb == 0.0) {
+        for (int64_t i = 0; i < n; ++i)
+            x[i] = 0.0;
+        *rel_res = 0.0;
+        return ORC_OK;
+    }
+    size_t bytes = (size_t)(n > 0 ? n : 1) * sizeof(double);
+    double *r = (double *)malloc(bytes), *p = (double *)malloc(bytes),
+           *s = (double *)malloc(bytes), *w = (double *)malloc(bytes);
+    for (int64_t i = 0; i < n; ++i) {
+        r[i] = b[i];
+        p[i] = 0.0;
+        s[i] = 0.0;
+    }
+    orc_spmv_csr(n, row_ptr, col, val, x, -1.0, 1.0, r);
+    int status = ORC_NOT_CONVERGED, checks = 0, k = 0;
+    double gamma_old = 0.0, alpha_old = 0.0;
+    while (1) {
+        orc_spmv_csr(n, row_ptr, col, val, r, 1.0, 0.0, w);
+        double gamma = orc_dot(n, r, r);
+        double delta = orc_dot(n, w, r);
+        if (!(gamma == gamma) || !(delta == delta)) {
+            status = ORC_BREAKDOWN;
+            break;
+        }
+        if (sqrt(gamma) <= tol * nb) {
+            double t = orc_true_rel_residual(n, row_ptr, col, val, b, x);
+            ++checks;
+            if (t <= tol) {
+                status = ORC_OK;
+                break;
+            }
+            if (checks >= 4)
+                break;
+        }
+        if (k >= maxit)
+            break;
+        double beta = 0.0, denom = delta;
+        if (k > 0) {
+            beta = gamma / gamma_old;
+            denom = delta - beta * gamma / alpha_old;
+        }
+        if (!(denom > 0.0)) {
+            status = ORC_BREAKDOWN;
+            break;
+        }
+        double alpha = gamma / denom;
+        for (int64_t i = 0; i < n; ++i) {
+            double t = beta * p[i];
+            p[i] = r[i] + t;
+            t = beta * s[i];
+            s[i] = w[i] + t;
+            t = alpha * p[i];
+            x[i] = x[i] + t;
+            t = alpha * s[i];
+            r[i] = r[i] - t;
+        }
+        gamma_old = gamma;
+        alpha_old = alpha;
+        k += 1;
+        *iters = k;
+    }
+    *rel_res = orc_true_rel_residual(n, row_ptr, col, val, b, x);
+    free(r);
+    free(p);
+    free(s);
+    free(w);
     return status;
 }
 

@@ -59,6 +59,7 @@ _SIGS = {
     "gko_spmv_host": (_INT, [_INT, _P, _P, _P, _D, _D, _P]),
     "gko_spmv_coo_noalloc": (_INT, [_I64, _I64, _I64, _P, _P, _P, _P, _P, _D, _D, _P, _P]),
     "gko_cg": (_INT, [_P, _INT, _P, _P, _D, _INT, _P, C.POINTER(SolveInfo)]),
+    "gko_cg_single_reduction": (_INT, [_P, _INT, _P, _P, _D, _INT, _P, C.POINTER(SolveInfo)]),
     "gko_cg_mixed": (_INT, [_P, _INT, _P, _P, _D, _INT, _D, _INT, _P, C.POINTER(SolveInfo)]),
     "gko_batch_create": (_INT, [_I64, _P, _P, _P, _P, _INT, _P, C.POINTER(_P)]),
     "gko_batch_destroy": (_INT, [_P]),
@@ -171,6 +172,16 @@ def gko_cg(A, fmt, b, x, tol, maxit, stream=0, raise_on=()) -> SolveInfo:
     s = lib.gko_cg(A, fmt, b, x, tol, maxit, stream, C.byref(info))
     allow = tuple(c for c in (ERR_NOT_CONVERGED, ERR_BREAKDOWN) if c not in raise_on)
     _check(s, "gko_cg", allow)
+    info.status = s
+    return info
+
+
+def gko_cg_single_reduction(A, fmt, b, x, tol, maxit, stream=0, raise_on=()) -> SolveInfo:
+    """As gko_cg, for the single-reduction (Chronopoulos-Gear) CG."""
+    info = SolveInfo()
+    s = lib.gko_cg_single_reduction(A, fmt, b, x, tol, maxit, stream, C.byref(info))
+    allow = tuple(c for c in (ERR_NOT_CONVERGED, ERR_BREAKDOWN) if c not in raise_on)
+    _check(s, "gko_cg_single_reduction", allow)
     info.status = s
     return info
 

@@ -22,6 +22,7 @@
 #include "common.cuh"
 #include "internal.h"
 #include "segmented.cuh"
+#include "solver.cuh"
 
 namespace gko {
 
@@ -29,69 +30,7 @@ int launch_seg(int64_t n_rows, int64_t nnz, const int32_t* row_ptr, const int32_
                const double* val, const int32_t* thr_row, const SegArrays& sa, const double* x, double* y,
                double alpha, double beta, uint32_t* err, bool coo, cudaStream_t st, bool accumulate);
 
-constexpr int kRedThreads = 256;
-constexpr int kRedBlocks = 152 * 4;
-
-// Device-resident solver scalars.
-struct SolverState {
-    double rho;       // r.r of the current residual
-    double rho0;      // r.r at the start (inner solves stop relative to it)
-    double pq;        // p.q
-    double alpha, beta;
-    double stop_ref;  // ||b|| (outer CG) or sqrt(rho0) (inner CG)
-    double tol;
-    double dot_out;   // result of a plain dot
-    int32_t iter, maxit, done, status, conv, rel_inner;
-    uint32_t ticket;
-};
-
 enum { kDotStore = 0, kDotRhoInit = 1, kDotPQ = 2 };
-
-__device__ __forceinline__ double block_sum(double v, double* sh)
-{
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    for (int o = 16; o; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if (lane == 0) sh[w] = v;
-    __syncthreads();
-    double r = 0.0;
-    if (w == 0) {
-        r = lane < static_cast<int>(blockDim.x >> 5) ? sh[lane] : 0.0;
-        for (int o = 16; o; o >>= 1) r += __shfl_down_sync(0xffffffffu, r, o);
-    }
-    __syncthreads();
-    return r;  // valid in thread 0
-}
-
-// Grid-wide sum: partials by block, last block reduces them in index order
-// and runs epi(total) on thread 0.  Returns true in that thread.
-template <typename Epi>
-__device__ __forceinline__ void grid_sum(double v, double* part, uint32_t* ticket, Epi epi)
-{
-    __shared__ double sh[32];
-    __shared__ bool last;
-    const double b = block_sum(v, sh);
-    if (threadIdx.x == 0) {
-        part[blockIdx.x] = b;
-        __threadfence();
-        last = atomicAdd(ticket, 1u) == gridDim.x - 1;
-    }
-    __syncthreads();
-    if (!last) return;
-    __threadfence();
-    double acc = 0.0;
-    for (int i = threadIdx.x; i < static_cast<int>(gridDim.x); i += blockDim.x) acc += __ldcg(part + i);
-    const double tot = block_sum(acc, sh);
-    if (threadIdx.x == 0) {
-        *ticket = 0;
-        epi(tot);
-    }
-}
-
-__device__ __forceinline__ void stop_loop(SolverState* s, cudaGraphConditionalHandle h)
-{
-    s->done = 1;
-    if (h) cudaGraphSetConditional(h, 0);
-}
 
 // dot(a, b) with per-thread accumulation in T, cross-thread in FP64
 template <typename T, int kMode>
@@ -184,6 +123,110 @@ __global__ void __launch_bounds__(kRedThreads)
 static int red_grid(int64_t n)
 {
     return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(kRedBlocks, (n + kRedThreads - 1) / kRedThreads)));
+}
+
+// ------------------------------------------- single-reduction CG kernels
+
+template <typename T>
+struct Vec16;
+template <>
+struct Vec16<float> {
+    using type = float4;
+};
+template <>
+struct Vec16<double> {
+    using type = double2;
+};
+
+// One vector step of the single-reduction CG (Chronopoulos and Gear 1989):
+//   p = r + beta p;  s = w + beta s;  x += alpha p;  r -= alpha s
+// with alpha, beta from the product kernel's scalar step (s = A p is carried
+// by recurrence, so no second product or reduction is needed).  kVec: all
+// vectors 16-byte aligned, moved as 128-bit words.
+template <typename T, bool kVec>
+__global__ void __launch_bounds__(kRedThreads)
+    cg1_update_kernel(int64_t n, T* __restrict__ x, T* __restrict__ r, T* __restrict__ p, T* __restrict__ s,
+                      const T* __restrict__ w, const SolverState* st)
+{
+    if (st->done) return;
+    const T alpha = static_cast<T>(st->alpha), beta = static_cast<T>(st->beta);
+    const int64_t tid = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+    const int64_t nth = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    int64_t i0 = 0;
+    if (kVec) {
+        using V = typename Vec16<T>::type;
+        constexpr int W = 16 / sizeof(T);
+        union U {
+            V v;
+            T a[W];
+        };
+        const int64_t nv = n / W;
+        for (int64_t i = tid; i < nv; i += nth) {
+            U rv, wv, pv, sv, xv;
+            rv.v = reinterpret_cast<const V*>(r)[i];
+            wv.v = reinterpret_cast<const V*>(w)[i];
+            pv.v = reinterpret_cast<const V*>(p)[i];
+            sv.v = reinterpret_cast<const V*>(s)[i];
+            xv.v = reinterpret_cast<const V*>(x)[i];
+#pragma unroll
+            for (int k = 0; k < W; ++k) {
+                pv.a[k] = fma(beta, pv.a[k], rv.a[k]);
+                sv.a[k] = fma(beta, sv.a[k], wv.a[k]);
+                xv.a[k] = fma(alpha, pv.a[k], xv.a[k]);
+                rv.a[k] = fma(-alpha, sv.a[k], rv.a[k]);
+            }
+            reinterpret_cast<V*>(p)[i] = pv.v;
+            reinterpret_cast<V*>(s)[i] = sv.v;
+            reinterpret_cast<V*>(x)[i] = xv.v;
+            reinterpret_cast<V*>(r)[i] = rv.v;
+        }
+        i0 = nv * W;
+    }
+    for (int64_t i = i0 + tid; i < n; i += nth) {
+        const T pi = fma(beta, p[i], r[i]);
+        const T si = fma(beta, s[i], w[i]);
+        p[i] = pi;
+        s[i] = si;
+        x[i] = fma(alpha, pi, x[i]);
+        r[i] = fma(-alpha, si, r[i]);
+    }
+}
+
+// gamma = r.r and delta = w.r with one grid reduction ending in the scalar
+// step (for products by kernels that do not fuse the dots themselves)
+template <typename T>
+__global__ void __launch_bounds__(kRedThreads)
+    cg1_dots_kernel(int64_t n, const T* __restrict__ r, const T* __restrict__ w, Cg1Reduce red)
+{
+    T g = T(0), d = T(0);
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(kRedThreads) + threadIdx.x; i < n;
+         i += static_cast<int64_t>(gridDim.x) * kRedThreads) {
+        const T ri = r[i];
+        g = fma(ri, ri, g);
+        d = fma(w[i], ri, d);
+    }
+    SolverState* s = red.s;
+    grid_sum2(static_cast<double>(g), static_cast<double>(d), red.part, &s->ticket,
+              [&](double gamma, double delta) { cg1_scalars(s, gamma, delta, red.err, red.h); });
+}
+
+static int upd_grid(int64_t n)
+{
+    const int64_t v = (n + 3) / 4;
+    return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(152 * 8, (v + kRedThreads - 1) / kRedThreads)));
+}
+
+template <typename T>
+static void launch_cg1_update(int64_t n, T* x, T* r, T* p, T* s, const T* w, const SolverState* st,
+                              cudaStream_t cs)
+{
+    const bool vec = ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(r) |
+                       reinterpret_cast<uintptr_t>(p) | reinterpret_cast<uintptr_t>(s) |
+                       reinterpret_cast<uintptr_t>(w)) & 15) == 0;
+    if (vec)
+        cg1_update_kernel<T, true><<<upd_grid(n), kRedThreads, 0, cs>>>(n, x, r, p, s, w, st);
+    else
+        cg1_update_kernel<T, false><<<upd_grid(n), kRedThreads, 0, cs>>>(n, x, r, p, s, w, st);
 }
 
 // ----------------------------------------------------------- workspace
@@ -409,6 +452,122 @@ int cg_solve(const gko_matrix* A, int fmt, const double* b, double* x, double to
     return status;
 }
 
+// ------------------------------------------------ single-reduction CG
+
+// The step's product w = A r with the dots and scalar step fused where the
+// kernel allows it (row-block CSR), else the format's SpMV + one dot kernel.
+static int cg1_product_f64(const gko_matrix* A, int fmt, const double* r, double* w, Cg1Reduce red, int grid,
+                           cudaStream_t cs)
+{
+    const int64_t n = A->n_rows;
+    if (fmt == GKO_FMT_CSR && A->nnz > 0 && rowblock_preferred(A)) {
+        const cudaError_t e = rowblock_cg1_f64(A, r, w, red, cs);
+        return e == cudaSuccess ? GKO_OK : cuda_fail(e, "single-reduction CG product");
+    }
+    GKO_TRY(spmv_fmt(A, fmt, r, w, 1.0, 0.0, cs));
+    cg1_dots_kernel<double><<<grid, kRedThreads, 0, cs>>>(n, r, w, red);
+    GKO_CUDA(cudaGetLastError());
+    return GKO_OK;
+}
+
+// CG in the single-reduction form of Chronopoulos and Gear (1989): per step
+// one product w = A r fused with gamma = r.r, delta = w.r and the scalar
+// step, then one vector update of p, s = A p, x and r.  Two launches and one
+// grid reduction per step instead of four launches and two reductions.
+// Stopping, confirmation by the true residual and breakdown as in cg_solve.
+int cg1_solve(const gko_matrix* A, int fmt, const double* b, double* x, double tol, int maxit, cudaStream_t st,
+              gko_solve_info* info)
+{
+    const int64_t n = A->n_rows;
+    if (n == 0) {
+        fill_info(info, 0, 0, 0.0, GKO_OK);
+        return GKO_OK;
+    }
+    Workspace ws(st);
+    double *r, *w, *p, *sv, *part;
+    SolverState* ds;
+    GKO_TRY(ws.get(&r, n));
+    GKO_TRY(ws.get(&w, n));
+    GKO_TRY(ws.get(&p, n));
+    GKO_TRY(ws.get(&sv, n));
+    GKO_TRY(ws.get(&part, 2 * kRedBlocks));
+    GKO_TRY(ws.get(&ds, 1));
+    const int grid = red_grid(n);
+
+    SolverState hs = {};
+    GKO_TRY(write_state(ds, &hs, st));
+    dot_kernel<double, kDotStore><<<grid, kRedThreads, 0, st>>>(n, b, b, ds, part, 0);
+    GKO_TRY(read_state(&hs, ds, st));
+    const double bnorm = std::sqrt(hs.dot_out);
+    if (bnorm == 0.0) {
+        GKO_CUDA(cudaMemsetAsync(x, 0, n * sizeof(double), st));
+        GKO_CUDA(cudaStreamSynchronize(st));
+        fill_info(info, 0, 0, 0.0, GKO_OK);
+        return GKO_OK;
+    }
+    // r = b - A x; p = s = 0 (beta = 0 at the first step)
+    GKO_CUDA(cudaMemcpyAsync(r, b, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    GKO_TRY(spmv_fmt(A, fmt, x, r, -1.0, 1.0, st));
+    GKO_CUDA(cudaMemsetAsync(p, 0, n * sizeof(double), st));
+    GKO_CUDA(cudaMemsetAsync(sv, 0, n * sizeof(double), st));
+    hs = {};
+    hs.tol = tol;
+    hs.stop_ref = bnorm;
+    hs.maxit = maxit;
+    hs.status = GKO_ERR_NOT_CONVERGED;
+    GKO_TRY(write_state(ds, &hs, st));
+
+    GraphHolder gh;
+    GKO_TRY(build_while_graph(&gh, [&](cudaGraphConditionalHandle h, cudaStream_t cs) -> int {
+        const Cg1Reduce red{ds, part, A->d_err, h};
+        GKO_TRY(cg1_product_f64(A, fmt, r, w, red, grid, cs));
+        launch_cg1_update<double>(n, x, r, p, sv, w, ds, cs);
+        GKO_CUDA(cudaGetLastError());
+        return GKO_OK;
+    }));
+
+    int status = GKO_ERR_NOT_CONVERGED, checks = 0;
+    double res = -1.0;
+    while (true) {
+        GKO_CUDA(cudaGraphLaunch(gh.exec, st));
+        GKO_TRY(read_state(&hs, ds, st));
+        if (hs.status == GKO_ERR_BREAKDOWN || hs.status == GKO_ERR_TIMEOUT) {
+            status = hs.status;
+            break;
+        }
+        if (hs.conv) {
+            GKO_TRY(true_residual(A, fmt, b, x, w, ds, part, bnorm, st, &res));
+            ++checks;
+            if (res <= tol) {
+                status = GKO_OK;
+                break;
+            }
+            if (checks >= 4 || hs.iter >= maxit) {
+                status = GKO_ERR_NOT_CONVERGED;
+                break;
+            }
+            // not confirmed: take the step the test stopped and go on
+            GKO_TRY(read_state(&hs, ds, st));  // true_residual used dot_out only
+            hs.conv = 0;
+            hs.done = 0;
+            hs.skip_test = 1;
+            hs.status = GKO_ERR_NOT_CONVERGED;
+            GKO_TRY(write_state(ds, &hs, st));
+            res = -1.0;
+            continue;
+        }
+        status = GKO_ERR_NOT_CONVERGED;  // maxit
+        break;
+    }
+    if (res < 0.0) GKO_TRY(true_residual(A, fmt, b, x, w, ds, part, bnorm, st, &res));
+    fill_info(info, hs.iter, 0, res, status);
+    if (status != GKO_OK)
+        set_error(status == GKO_ERR_BREAKDOWN ? "CG breakdown (non-positive curvature or NaN)"
+                  : status == GKO_ERR_TIMEOUT  ? "CG product: a bounded wait for a bulk copy gave up"
+                                               : "CG reached maxit");
+    return status;
+}
+
 // ------------------------------------------- mixed precision refinement
 
 // IEEE binary64 -> bfloat16, round to nearest, ties to even, from the bit
@@ -478,16 +637,16 @@ __global__ void lowprec_kernel(int64_t n, const int32_t* __restrict__ row_ptr, c
     }
 }
 
-// rl = float(r / nr); d = 0; p = rl
+// rl = float(r / nr); d = p = s = 0
 __global__ void inner_init_kernel(int64_t n, const double* __restrict__ r, double nr, float* __restrict__ rl,
-                                  float* __restrict__ d, float* __restrict__ p)
+                                  float* __restrict__ d, float* __restrict__ p, float* __restrict__ s)
 {
     for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
          i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-        const float v = __double2float_rn(r[i] / nr);
-        rl[i] = v;
+        rl[i] = __double2float_rn(r[i] / nr);
         d[i] = 0.0f;
-        p[i] = v;
+        p[i] = 0.0f;
+        s[i] = 0.0f;
     }
 }
 
@@ -540,17 +699,20 @@ int cg_mixed_solve(gko_matrix* A, int inner, const double* b, double* x, double 
                                                              nullptr);
     }
     GKO_CUDA(cudaGetLastError());
+    bool use_ell = false;
+    GKO_TRY(lp_ell_prepare(A, bf16, st, &use_ell));
 
     Workspace ws(st);
     double *r, *part;
-    float *rl, *d, *p, *q;
+    float *rl, *d, *p, *sv, *w;
     SolverState *ds, *di;
     GKO_TRY(ws.get(&r, n));
-    GKO_TRY(ws.get(&part, kRedBlocks));
+    GKO_TRY(ws.get(&part, 2 * std::max(kRedBlocks, use_ell ? lp_ell_grid(A) : 0)));
     GKO_TRY(ws.get(&rl, n));
     GKO_TRY(ws.get(&d, n));
     GKO_TRY(ws.get(&p, n));
-    GKO_TRY(ws.get(&q, n));
+    GKO_TRY(ws.get(&sv, n));
+    GKO_TRY(ws.get(&w, n));
     GKO_TRY(ws.get(&ds, 1));
     GKO_TRY(ws.get(&di, 1));
     const int64_t tiles = std::max<int64_t>(1, (nnz + SegShape<kSegP>::kTile - 1) / SegShape<kSegP>::kTile);
@@ -574,16 +736,30 @@ int cg_mixed_solve(gko_matrix* A, int inner, const double* b, double* x, double 
         return GKO_OK;
     }
 
-    // inner CG graph: q = A_lo p; alpha; d += alpha p, rl -= alpha q; beta; p = rl + beta p
+    // inner CG on A_lo d = rl in the single-reduction form (Chronopoulos and
+    // Gear): w = A_lo rl fused with the dots and the scalar step (ELL copy of
+    // A_lo when its padding is small, else row-block CSR; otherwise the
+    // load-balanced product + one dot kernel), then
+    // p = rl + beta p, s = w + beta s, d += alpha p, rl -= alpha s
+    const bool fused = nnz > 0 && rowblock_preferred(A);
     GraphHolder gh;
     GKO_TRY(build_while_graph(&gh, [&](cudaGraphConditionalHandle h, cudaStream_t cs) -> int {
-        cudaError_t e = bf16 ? inner_spmv<__nv_bfloat16>(A, reinterpret_cast<const __nv_bfloat16*>(A->val_bf16), sc,
-                                                          p, q, cs)
-                             : inner_spmv<float>(A, A->val_f32, sc, p, q, cs);
-        if (e != cudaSuccess) return cuda_fail(e, "inner SpMV launch");
-        dot_kernel<float, kDotPQ><<<grid, kRedThreads, 0, cs>>>(n, p, q, di, part, h);
-        update_kernel<float><<<grid, kRedThreads, 0, cs>>>(n, d, rl, p, q, di, part, h);
-        pupdate_kernel<float><<<grid, kRedThreads, 0, cs>>>(n, p, rl, di, 0);
+        const Cg1Reduce red{di, part, A->d_err, h};
+        cudaError_t e;
+        if (use_ell) {
+            e = lp_ell_cg1(A, bf16, rl, w, red, cs);
+        } else if (fused) {
+            e = bf16 ? rowblock_cg1_bf16(A, A->val_bf16, rl, w, red, cs) : rowblock_cg1_f32(A, A->val_f32, rl, w, red, cs);
+        } else {
+            e = bf16 ? inner_spmv<__nv_bfloat16>(A, reinterpret_cast<const __nv_bfloat16*>(A->val_bf16), sc, rl, w, cs)
+                     : inner_spmv<float>(A, A->val_f32, sc, rl, w, cs);
+            if (e == cudaSuccess) {
+                cg1_dots_kernel<float><<<grid, kRedThreads, 0, cs>>>(n, rl, w, red);
+                e = cudaGetLastError();
+            }
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "inner CG product launch");
+        launch_cg1_update<float>(n, d, rl, p, sv, w, di, cs);
         GKO_CUDA(cudaGetLastError());
         return GKO_OK;
     }));
@@ -608,18 +784,21 @@ int cg_mixed_solve(gko_matrix* A, int inner, const double* b, double* x, double 
         }
         if (o == maxit_outer) break;
         outer = o + 1;
-        inner_init_kernel<<<grid, kRedThreads, 0, st>>>(n, r, nr, rl, d, p);
+        inner_init_kernel<<<grid, kRedThreads, 0, st>>>(n, r, nr, rl, d, p, sv);
         SolverState is = {};
         is.tol = inner_tol;
         is.rel_inner = 1;
         is.maxit = inner_maxit;
         is.status = GKO_ERR_NOT_CONVERGED;
         GKO_TRY(write_state(di, &is, st));
-        dot_kernel<float, kDotRhoInit><<<grid, kRedThreads, 0, st>>>(n, rl, rl, di, part, 0);
         GKO_CUDA(cudaGraphLaunch(gh.exec, st));
         correct_kernel<<<grid, kRedThreads, 0, st>>>(n, x, d, nr);
         GKO_TRY(read_state(&is, di, st));
         inner_total += is.iter;
+        if (is.status == GKO_ERR_TIMEOUT) {
+            status = GKO_ERR_TIMEOUT;
+            break;
+        }
     }
     GKO_CUDA(cudaGetLastError());
     fill_info(info, inner_total, outer, res, status);

@@ -108,6 +108,18 @@ struct HybridPart {
     CooPart coo;
 };
 
+// ELL copy of the rounded matrix for the mixed-precision inner solve
+// (lowprec_ell.cu): col holds int16 offsets c - i when idx16, else int32
+// columns; K * n_pad slots.
+struct LowPrecEll {
+    bool tried = false, ok = false;
+    int idx16 = 0;
+    int64_t K = 0, n_pad = 0;
+    void* col = nullptr;
+    float* val_f32 = nullptr;
+    uint16_t* val_bf16 = nullptr;
+};
+
 }  // namespace gko
 
 struct gko_matrix {
@@ -126,6 +138,7 @@ struct gko_matrix {
     double* stage_y = nullptr;
     float* val_f32 = nullptr;        // mixed-precision copies (CSR order)
     uint16_t* val_bf16 = nullptr;
+    gko::LowPrecEll lp_ell;          // ELL layout of those copies (when padding is small)
     bool feats_valid = false;
     double feats[12] = {0};
 };
@@ -173,6 +186,12 @@ int rowblock_rows(const gko_matrix* A);
 bool rowblock_preferred(const gko_matrix* A);
 cudaError_t rowblock_lowprec_f32(const gko_matrix* A, const float* val, const float* x, float* y, cudaStream_t st);
 cudaError_t rowblock_lowprec_bf16(const gko_matrix* A, const void* val, const float* x, float* y, cudaStream_t st);
+struct Cg1Reduce;  // solver.cuh
+cudaError_t rowblock_cg1_f64(const gko_matrix* A, const double* r, double* w, Cg1Reduce red, cudaStream_t st);
+cudaError_t rowblock_cg1_f32(const gko_matrix* A, const float* val, const float* r, float* w, Cg1Reduce red,
+                             cudaStream_t st);
+cudaError_t rowblock_cg1_bf16(const gko_matrix* A, const void* val, const float* r, float* w, Cg1Reduce red,
+                              cudaStream_t st);
 
 // conversions (convert.cu); all synchronise the stream where sizes are read
 int convert_csr_to_coo(gko_matrix* A, cudaStream_t st);
@@ -193,6 +212,12 @@ int exclusive_scan_i64(const int32_t* in, int64_t* out, int64_t n, cudaStream_t 
 // BLAS-1 and solvers (blas1.cu, cg.cu)
 int cg_solve(const gko_matrix* A, int fmt, const double* b, double* x, double tol, int maxit,
              cudaStream_t st, gko_solve_info* info);
+int lp_ell_prepare(gko_matrix* A, bool bf16, cudaStream_t st, bool* usable);
+void lp_ell_free(gko_matrix* A);
+cudaError_t lp_ell_cg1(const gko_matrix* A, bool bf16, const float* r, float* w, Cg1Reduce red, cudaStream_t st);
+int lp_ell_grid(const gko_matrix* A);
+int cg1_solve(const gko_matrix* A, int fmt, const double* b, double* x, double tol, int maxit,
+              cudaStream_t st, gko_solve_info* info);
 int cg_mixed_solve(gko_matrix* A, int inner, const double* b, double* x, double tol, int maxit_outer,
                    double inner_tol, int inner_maxit, cudaStream_t st, gko_solve_info* info);
 

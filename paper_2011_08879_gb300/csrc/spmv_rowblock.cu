@@ -28,6 +28,7 @@
 #include "common.cuh"
 #include "internal.h"
 #include "segmented.cuh"
+#include "solver.cuh"
 
 namespace gko {
 
@@ -80,11 +81,15 @@ bool rowblock_preferred(const gko_matrix* A)
     return rowblock_rows(A) > 0 && A->csr.max_len <= 2.0 * A->csr.mean_len + 16.0;
 }
 
-template <typename V, typename T, bool kAlpha, bool kBeta, bool kX, int CH>
+// kDots: the product of a single-reduction CG step (x = r, y = w = A r);
+// every thread also sums r_i^2 and w_i r_i over its rows and the grid
+// reduction ends in the solver's scalar step (alpha = 1, beta = 0).
+// kHint: the matrix streams carry an L2 evict-first policy.
+template <typename V, typename T, bool kAlpha, bool kBeta, bool kX, int CH, bool kDots = false, bool kHint = false>
 __global__ void __launch_bounds__(kRbThreads, 2)
     csr_rowblock_kernel(int64_t n_rows, int64_t n_cols, int R, int band, int xbuf, const int32_t* __restrict__ row_ptr,
                         const int32_t* __restrict__ col, const V* __restrict__ val, const T* __restrict__ x,
-                        T* __restrict__ y, T alpha, T beta, uint32_t* err)
+                        T* __restrict__ y, T alpha, T beta, uint32_t* err, Cg1Reduce red)
 {
     using G = RbStage<V>;
     constexpr int kXAl = 16 / static_cast<int>(sizeof(T));
@@ -120,9 +125,16 @@ __global__ void __launch_bounds__(kRbThreads, 2)
         }
         info[st] = ti;
         mbar_arrive_expect_tx(&bar[st], bytes);
-        bulk_g2s(s_val(st), val + ti.a0, cnt * sizeof(V), &bar[st]);
-        bulk_g2s(s_col(st), col + ti.a0, cnt * sizeof(int32_t), &bar[st]);
-        bulk_g2s(s_rp(st), row_ptr + ti.ra0, rcnt * sizeof(int32_t), &bar[st]);
+        if (kHint) {
+            const uint64_t pol = l2_evict_first_policy();
+            bulk_g2s_hint(s_val(st), val + ti.a0, cnt * sizeof(V), &bar[st], pol);
+            bulk_g2s_hint(s_col(st), col + ti.a0, cnt * sizeof(int32_t), &bar[st], pol);
+            bulk_g2s_hint(s_rp(st), row_ptr + ti.ra0, rcnt * sizeof(int32_t), &bar[st], pol);
+        } else {
+            bulk_g2s(s_val(st), val + ti.a0, cnt * sizeof(V), &bar[st]);
+            bulk_g2s(s_col(st), col + ti.a0, cnt * sizeof(int32_t), &bar[st]);
+            bulk_g2s(s_rp(st), row_ptr + ti.ra0, rcnt * sizeof(int32_t), &bar[st]);
+        }
         if (kX && ti.wl > 0) bulk_g2s(s_x(st), x + ti.w0, ti.wl * sizeof(T), &bar[st]);
     };
     auto meta0 = [&](int64_t b) { return row_ptr[b * R]; };
@@ -140,6 +152,8 @@ __global__ void __launch_bounds__(kRbThreads, 2)
             if (b < n_blocks) issue(b, k, meta0(b), meta1(b));
         }
 
+    T dot_rr = T(0), dot_wr = T(0);
+    bool failed = false;
     for (int it = 0;; ++it) {
         const int64_t b = blockIdx.x + it * stride;
         if (b >= n_blocks) break;
@@ -147,7 +161,10 @@ __global__ void __launch_bounds__(kRbThreads, 2)
         const uint32_t parity = (it >> 1) & 1;
         bool landed = mbar_wait_bounded(&bar[st], parity, err);
         if (!landed) landed = mbar_wait_bounded(&bar[st], parity, err);
-        if (!__syncthreads_and(landed)) return;
+        if (!__syncthreads_and(landed)) {  // CTA-uniform: give up on the rest
+            failed = true;
+            break;
+        }
         const int64_t b_issue = b + 2 * stride;
         int32_t pe0 = 0, pe1 = 0;
         if (tid == 0 && b_issue < n_blocks) {
@@ -193,7 +210,13 @@ __global__ void __launch_bounds__(kRbThreads, 2)
                     if (j0 + u + 1 < len) acc1 = fma(to_t<V, T>(sv[kk[u + 1]]), xv[u + 1], acc1);
                 }
             }
-            seg_store<kAlpha, kBeta>(y, r, acc0 + acc1, alpha, beta);
+            const T w = acc0 + acc1;
+            seg_store<kAlpha, kBeta>(y, r, w, alpha, beta);
+            if (kDots) {
+                const T xr = ldg(x + r);
+                dot_rr = fma(xr, xr, dot_rr);
+                dot_wr = fma(w, xr, dot_wr);
+            }
         }
         __syncthreads();  // the stage is free again
         if (tid == 0 && b_issue < n_blocks) {
@@ -201,11 +224,21 @@ __global__ void __launch_bounds__(kRbThreads, 2)
             issue(b_issue, st, pe0, pe1);
         }
     }
+    if (kDots) {
+        // every block takes part in the reduction (a failed one with NaN),
+        // so the scalar step always runs and the solver loop always ends
+        const double nan = __longlong_as_double(0x7ff8000000000000ll);
+        const double g = failed ? nan : static_cast<double>(dot_rr);
+        const double d = failed ? nan : static_cast<double>(dot_wr);
+        SolverState* s = red.s;
+        grid_sum2(g, d, red.part, &s->ticket,
+                  [&](double gamma, double delta) { cg1_scalars(s, gamma, delta, red.err, red.h); });
+    }
 }
 
-template <typename V, typename T, bool kX, int CH>
+template <typename V, typename T, bool kX, int CH, bool kDots = false, bool kHint = false>
 static cudaError_t launch_rowblock_ch(const gko_matrix* A, const V* val, const T* x, T* y, T alpha, T beta,
-                                      cudaStream_t st)
+                                      cudaStream_t st, Cg1Reduce red = Cg1Reduce{})
 {
     const int R = rowblock_rows(A);
     const int band = kX ? A->csr.band : -1;
@@ -217,14 +250,17 @@ static cudaError_t launch_rowblock_ch(const gko_matrix* A, const V* val, const T
     cudaError_t e = cudaSuccess;
 #define GKO_RB(KA, KB)                                                                                    \
     do {                                                                                                  \
-        e = cudaFuncSetAttribute(csr_rowblock_kernel<V, T, KA, KB, kX, CH>,                               \
+        e = cudaFuncSetAttribute(csr_rowblock_kernel<V, T, KA, KB, kX, CH, kDots, kHint>,                 \
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));    \
         if (e != cudaSuccess) return e;                                                                   \
-        csr_rowblock_kernel<V, T, KA, KB, kX, CH><<<static_cast<unsigned>(grid), kRbThreads, smem, st>>>( \
-            A->n_rows, A->n_cols, R, band, xbuf, A->csr.row_ptr, A->csr.col, val, x, y, alpha, beta,      \
-            A->d_err);                                                                                    \
+        csr_rowblock_kernel<V, T, KA, KB, kX, CH, kDots, kHint>                                           \
+            <<<static_cast<unsigned>(grid), kRbThreads, smem, st>>>(A->n_rows, A->n_cols, R, band, xbuf,  \
+                                                                    A->csr.row_ptr, A->csr.col, val, x, y, \
+                                                                    alpha, beta, A->d_err, red);          \
     } while (0)
-    if (a && b)
+    if (kDots)
+        GKO_RB(false, false);
+    else if (a && b)
         GKO_RB(true, true);
     else if (a)
         GKO_RB(true, false);
@@ -237,12 +273,12 @@ static cudaError_t launch_rowblock_ch(const gko_matrix* A, const V* val, const T
 }
 
 // chunk of 8 gathers for short rows, 16 otherwise
-template <typename V, typename T, bool kX>
+template <typename V, typename T, bool kX, bool kDots = false, bool kHint = false>
 static cudaError_t launch_rowblock_t(const gko_matrix* A, const V* val, const T* x, T* y, T alpha, T beta,
-                                     cudaStream_t st)
+                                     cudaStream_t st, Cg1Reduce red = Cg1Reduce{})
 {
-    if (A->csr.max_len <= 8) return launch_rowblock_ch<V, T, kX, 8>(A, val, x, y, alpha, beta, st);
-    return launch_rowblock_ch<V, T, kX, 16>(A, val, x, y, alpha, beta, st);
+    if (A->csr.max_len <= 8) return launch_rowblock_ch<V, T, kX, 8, kDots, kHint>(A, val, x, y, alpha, beta, st, red);
+    return launch_rowblock_ch<V, T, kX, 16, kDots, kHint>(A, val, x, y, alpha, beta, st, red);
 }
 
 int spmv_csr_rowblock(const gko_matrix* A, const double* x, double* y, double alpha, double beta, cudaStream_t st)
@@ -273,6 +309,26 @@ cudaError_t rowblock_lowprec_bf16(const gko_matrix* A, const void* val, const fl
 {
     return launch_rowblock_t<__nv_bfloat16, float, false>(A, static_cast<const __nv_bfloat16*>(val), x, y, 1.0f,
                                                           0.0f, st);
+}
+
+// Product of a single-reduction CG step: w = A r with the step's dots and
+// scalars fused (double, float or bf16 values; FP64 or FP32 vectors).  The
+// matrix streams are marked evict-first in L2 so the solver's vectors stay
+// cached between the steps.
+cudaError_t rowblock_cg1_f64(const gko_matrix* A, const double* r, double* w, Cg1Reduce red, cudaStream_t st)
+{
+    return launch_rowblock_t<double, double, false, true, true>(A, A->csr.val, r, w, 1.0, 0.0, st, red);
+}
+cudaError_t rowblock_cg1_f32(const gko_matrix* A, const float* val, const float* r, float* w, Cg1Reduce red,
+                             cudaStream_t st)
+{
+    return launch_rowblock_t<float, float, false, true, true>(A, val, r, w, 1.0f, 0.0f, st, red);
+}
+cudaError_t rowblock_cg1_bf16(const gko_matrix* A, const void* val, const float* r, float* w, Cg1Reduce red,
+                              cudaStream_t st)
+{
+    return launch_rowblock_t<__nv_bfloat16, float, false, true, true>(A, static_cast<const __nv_bfloat16*>(val), r,
+                                                                      w, 1.0f, 0.0f, st, red);
 }
 
 }  // namespace gko

@@ -38,6 +38,95 @@ def test_cg_laplace_128(gko, dev, orc, fmt):
     assert e_g <= 10 * e_o + 1e-15
 
 
+def _skewed_spd(n, seed):
+    """SPD matrix with power-law row lengths: the symmetrised pattern of a
+    power-law matrix, off-diagonals -|a|, diagonal 1 + sum of |off-diagonals|
+    (strictly diagonally dominant)."""
+    sp = pytest.importorskip("scipy.sparse")
+    P = syn.powerlaw(n, 6.0, 1.5, n // 4, seed=seed)
+    M = sp.csr_matrix((np.abs(P["val"]), P["col_idx"], P["row_ptr"]), shape=(n, n))
+    M = (M + M.T).tolil()
+    M.setdiag(0.0)
+    M = -M.tocsr()
+    M.eliminate_zeros()
+    d = 1.0 + np.asarray(abs(M).sum(axis=1)).ravel()
+    M = (M + sp.diags(d)).tocsr()
+    M.sort_indices()
+    return dict(n_rows=n, n_cols=n, row_ptr=M.indptr.astype(np.int32), col_idx=M.indices.astype(np.int32),
+                val=M.data.astype(np.float64))
+
+
+@pytest.mark.parametrize("fmt", ["csr", "coo", "ell", "sellp", "hybrid"])
+def test_cg_single_reduction_laplace_128(gko, dev, orc, fmt):
+    A = syn.laplace2d(128)
+    n = A["n_rows"]
+    xt = syn.vector(n, 1)
+    b = orc.spmv_csr(A, xt)
+    x_o, st_o, it_o, res_o = orc.cg_single_reduction(A, b, tol=1e-10)
+    _, _, it_hs, _ = orc.cg(A, b, tol=1e-10)
+    M = gko.Matrix(A)
+    if fmt != "csr":
+        M.convert(fmt)
+    x = _t(np.zeros(n), dev)
+    info = M.cg_single_reduction(_t(b, dev), x, tol=1e-10, maxit=10000, fmt=fmt)
+    assert info.status == 0 and info.rel_residual <= 1e-10
+    for it in (it_o, it_hs):
+        assert abs(info.iterations - it) <= max(5, 0.02 * it), (info.iterations, it)
+    xg = x.cpu().numpy()
+    assert orc.true_rel_residual(A, b, xg) <= 1e-10
+    e_o = np.linalg.norm(x_o - xt) / np.linalg.norm(xt)
+    e_g = np.linalg.norm(xg - xt) / np.linalg.norm(xt)
+    assert e_g <= 10 * e_o + 1e-15
+
+
+def test_cg_single_reduction_skewed_rows(gko, dev, orc):
+    """Rows of very different lengths: the product is the load-balanced
+    kernel plus a separate dot launch (not the fused row-block kernel)."""
+    A = _skewed_spd(20000, 31)
+    n = A["n_rows"]
+    lens = np.diff(A["row_ptr"])
+    assert lens.max() > 2 * lens.mean() + 16  # the row-block kernel does not apply
+    xt = syn.vector(n, 5)
+    b = orc.spmv_csr(A, xt)
+    x_o, st_o, it_o, res_o = orc.cg_single_reduction(A, b, tol=1e-10)
+    assert st_o == 0
+    M = gko.Matrix(A)
+    for solve in (M.cg, M.cg_single_reduction):
+        x = _t(np.zeros(n), dev)
+        info = solve(_t(b, dev), x, tol=1e-10, maxit=5000)
+        assert info.status == 0 and info.rel_residual <= 1e-10
+        assert abs(info.iterations - it_o) <= max(5, 0.02 * it_o), (info.iterations, it_o)
+        assert orc.true_rel_residual(A, b, x.cpu().numpy()) <= 1e-10
+
+
+def test_cg_single_reduction_special_cases(gko, dev, orc):
+    A = syn.laplace2d(16)
+    n = A["n_rows"]
+    M = gko.Matrix(A)
+    x = _t(np.ones(n), dev)
+    info = M.cg_single_reduction(_t(np.zeros(n), dev), x)
+    assert info.status == 0 and info.iterations == 0 and float(x.abs().max()) == 0.0
+    b = orc.spmv_csr(A, syn.vector(n, 2))
+    x = _t(np.zeros(n), dev)
+    info = M.cg_single_reduction(_t(b, dev), x, maxit=3)
+    assert info.status == gko.binding.ERR_NOT_CONVERGED and info.iterations == 3
+    xo, _, _, _ = orc.cg_single_reduction(A, b, maxit=3)
+    assert np.linalg.norm(x.cpu().numpy() - xo) <= 1e-12 * np.linalg.norm(xo)
+    x = _t(syn.vector(n, 2), dev)
+    info = M.cg_single_reduction(_t(b, dev), x)
+    assert info.status == 0 and info.iterations == 0
+    N = dict(A)
+    N["val"] = -A["val"]
+    x = _t(np.zeros(n), dev)
+    info = gko.Matrix(N).cg_single_reduction(_t(b, dev), x)
+    assert info.status == gko.binding.ERR_BREAKDOWN
+    bn = b.copy()
+    bn[5] = np.nan
+    x = _t(np.zeros(n), dev)
+    info = M.cg_single_reduction(_t(bn, dev), x)
+    assert info.status == gko.binding.ERR_BREAKDOWN
+
+
 def test_cg_special_cases(gko, dev, orc):
     A = syn.laplace2d(16)
     n = A["n_rows"]
@@ -105,6 +194,49 @@ def test_mixed_cg_matches_oracle(gko, dev, orc, prec):
     assert abs(info.outer_iterations - outer_o) <= 2, (info.outer_iterations, outer_o)
     e_ref = np.linalg.norm(x64 - xt)
     assert np.linalg.norm(xg - xt) <= 10 * e_ref + 1e-14 * np.linalg.norm(xt)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_mixed_cg_skewed_rows(gko, dev, orc, prec):
+    """Inner product by the load-balanced kernel + separate dots."""
+    A = _skewed_spd(20000, 32)
+    n = A["n_rows"]
+    xt = syn.vector(n, 7)
+    b = orc.spmv_csr(A, xt)
+    xo, st_o, outer_o, inner_o, res_o = orc.cg_mixed(A, b, prec, tol=1e-10, inner_tol=1e-3)
+    assert st_o == 0
+    M = gko.Matrix(A)
+    x = _t(np.zeros(n), dev)
+    info = M.cg_mixed(_t(b, dev), x, inner=prec, tol=1e-10, inner_tol=1e-3)
+    assert info.status == 0 and info.rel_residual <= 1e-10
+    assert orc.true_rel_residual(A, b, x.cpu().numpy()) <= 1e-10
+    assert abs(info.outer_iterations - outer_o) <= 2, (info.outer_iterations, outer_o)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_mixed_cg_wide_band(gko, dev, orc, prec):
+    """Symmetrically permuted diffusion operator: short uniform rows but
+    |i - j| up to n > 32767, so the inner ELL copy keeps int32 columns."""
+    sp = pytest.importorskip("scipy.sparse")
+    A0 = syn.diffusion7(34, 1.0, seed=9)
+    n = A0["n_rows"]
+    perm = np.random.default_rng(5).permutation(n)
+    M0 = sp.csr_matrix((A0["val"], A0["col_idx"], A0["row_ptr"]), shape=(n, n))
+    Mp = M0[perm][:, perm].tocsr()
+    Mp.sort_indices()
+    A = dict(n_rows=n, n_cols=n, row_ptr=Mp.indptr.astype(np.int32), col_idx=Mp.indices.astype(np.int32),
+             val=Mp.data.astype(np.float64))
+    assert np.max(np.abs(A["col_idx"] - np.repeat(np.arange(n), np.diff(A["row_ptr"])))) > 32767
+    xt = syn.vector(n, 8)
+    b = orc.spmv_csr(A, xt)
+    xo, st_o, outer_o, inner_o, res_o = orc.cg_mixed(A, b, prec, tol=1e-10, inner_tol=1e-3)
+    assert st_o == 0
+    M = gko.Matrix(A)
+    x = _t(np.zeros(n), dev)
+    info = M.cg_mixed(_t(b, dev), x, inner=prec, tol=1e-10, inner_tol=1e-3)
+    assert info.status == 0 and info.rel_residual <= 1e-10
+    assert orc.true_rel_residual(A, b, x.cpu().numpy()) <= 1e-10
+    assert abs(info.outer_iterations - outer_o) <= 2, (info.outer_iterations, outer_o)
 
 
 def test_lowprec_copy_matches_oracle_rounding(gko, dev, orc):

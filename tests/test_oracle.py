@@ -293,6 +293,75 @@ def test_cg_matches_scipy_solution(orc):
     assert np.linalg.norm(x - xs) <= 1e-9 * np.linalg.norm(xs)
 
 
+def _diag_spd(eigs):
+    n = len(eigs)
+    return dict(n_rows=n, n_cols=n, row_ptr=np.arange(n + 1, dtype=np.int32),
+                col_idx=np.arange(n, dtype=np.int32), val=np.asarray(eigs, dtype=np.float64))
+
+
+@pytest.mark.parametrize("solver", ["cg", "cg_single_reduction"])
+def test_cg_first_step_is_steepest_descent(orc, solver):
+    """From x0 = 0 the first CG iterate is the exact line minimum along b:
+    x1 = (b.b / b.Ab) b (closed form of one step of either form)."""
+    A = syn.diffusion7(6, 1.0, seed=3)
+    n = A["n_rows"]
+    b = syn.vector(n, 11)
+    D = dense(A)
+    x1 = (b @ b) / (b @ (D @ b)) * b
+    x, st, it, res = getattr(orc, solver)(A, b, maxit=1)
+    assert it == 1
+    assert np.linalg.norm(x - x1) <= 1e-14 * np.linalg.norm(x1)
+
+
+@pytest.mark.parametrize("solver", ["cg", "cg_single_reduction"])
+def test_cg_finite_termination(orc, solver):
+    """CG on an SPD matrix with m distinct eigenvalues reaches the solution
+    in at most m steps (exact arithmetic; a well-conditioned case in FP64)."""
+    eigs = np.repeat([1.0, 1.5, 2.25, 3.0, 4.0], 7)
+    A = _diag_spd(eigs)
+    b = syn.vector(len(eigs), 12)
+    x, st, it, res = getattr(orc, solver)(A, b, tol=1e-13)
+    assert st == orc.OK and it <= 5
+    assert np.allclose(x, b / eigs, rtol=1e-12, atol=0)
+    # one step short of m leaves a residual far above the tolerance
+    x, st, it, res = getattr(orc, solver)(A, b, tol=1e-13, maxit=4)
+    assert st == orc.NOT_CONVERGED and res > 1e-6
+
+
+def test_cg_single_reduction_matches_hestenes_stiefel(orc):
+    """The two forms produce the same iterates up to rounding: same step
+    counts on the 5-point Laplacian and solutions within the CG error bound
+    of the manufactured solution."""
+    A = syn.laplace2d(64)
+    n = A["n_rows"]
+    xt = syn.vector(n, 1)
+    b = orc.spmv_csr(A, xt)
+    x0, st0, it0, res0 = orc.cg(A, b, tol=1e-10)
+    x1, st1, it1, res1 = orc.cg_single_reduction(A, b, tol=1e-10)
+    assert st0 == st1 == orc.OK and res1 <= 1e-10
+    assert abs(it0 - it1) <= 2
+    for k in (3, 17, 40):  # the same iterate after k steps
+        xa, _, _, _ = orc.cg(A, b, maxit=k)
+        xb, _, _, _ = orc.cg_single_reduction(A, b, maxit=k)
+        assert np.linalg.norm(xa - xb) <= 1e-10 * np.linalg.norm(xa)
+
+
+def test_cg_single_reduction_special_cases(orc):
+    A = syn.laplace2d(8)
+    n = A["n_rows"]
+    x, st, it, res = orc.cg_single_reduction(A, np.zeros(n), x0=np.ones(n))
+    assert st == orc.OK and it == 0 and np.all(x == 0)
+    b = orc.spmv_csr(A, syn.vector(n, 2))
+    x, st, it, res = orc.cg_single_reduction(A, b, maxit=1)
+    assert st == orc.NOT_CONVERGED and it == 1
+    Aneg = dict(A)
+    Aneg["val"] = -A["val"]
+    x, st, it, res = orc.cg_single_reduction(Aneg, b)
+    assert st == orc.BREAKDOWN
+    x, st, it, res = orc.cg_single_reduction(A, b, x0=syn.vector(n, 2))
+    assert st == orc.OK and it == 0
+
+
 def test_batched_cg(orc):
     B = syn.batched_spd(12, seed=8)
     x, st, it, res = orc.cg_batched(B, B["rhs"], tol=1e-10)
