@@ -87,8 +87,11 @@ enum {
     GKO_CFG_CSR_NNZSPLIT = 7,   /* CSR, load-balanced equal-nnz split with segmented reduction */
     GKO_CFG_CSR_BANDED = 8,     /* CSR row blocks with the x window staged in shared memory (banded
                                    matrices: max |i - j| <= 1024 and max row length <= 128) */
-    GKO_CFG_CSR_ROWBLOCK = 9    /* CSR row blocks staged in shared memory, one thread per row (max row
-                                   length <= 128); the default when row lengths are close */
+    GKO_CFG_CSR_ROWBLOCK = 9,   /* CSR row blocks staged in shared memory, one thread per row (max row
+                                   length <= 128) */
+    GKO_CFG_CSR_BINNED = 10     /* CSR rows grouped by length (bins up to 8, 20, 48, 128, 512, longer; built
+                                   when the handle is created): each bin by subwarps of 1, 2, 4, 8, 32
+                                   lanes per row, the longest rows one thread block each */
 };
 
 typedef struct gko_matrix gko_matrix;

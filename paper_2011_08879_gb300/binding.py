@@ -26,7 +26,7 @@ FORMATS = {"csr": FMT_CSR, "coo": FMT_COO, "ell": FMT_ELL, "sellp": FMT_SELLP, "
 F64, F32, BF16 = 0, 1, 2
 # kernel configurations
 (CFG_DEFAULT, CFG_CSR_SUBWARP_1, CFG_CSR_SUBWARP_2, CFG_CSR_SUBWARP_4, CFG_CSR_SUBWARP_8, CFG_CSR_SUBWARP_16,
- CFG_CSR_SUBWARP_32, CFG_CSR_NNZSPLIT, CFG_CSR_BANDED, CFG_CSR_ROWBLOCK) = range(10)
+ CFG_CSR_SUBWARP_32, CFG_CSR_NNZSPLIT, CFG_CSR_BANDED, CFG_CSR_ROWBLOCK, CFG_CSR_BINNED) = range(11)
 
 
 class GkoError(RuntimeError):

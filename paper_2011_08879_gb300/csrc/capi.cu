@@ -316,7 +316,7 @@ int gko_spmv_config(int fmt, int config, const gko_matrix* A, const double* x, d
                     double beta, void* stream)
 {
     GKO_TRY(spmv_checks(fmt, A, x, y));
-    if (config < GKO_CFG_DEFAULT || config > GKO_CFG_CSR_ROWBLOCK)
+    if (config < GKO_CFG_DEFAULT || config > GKO_CFG_CSR_BINNED)
         return fail(GKO_ERR_INVALID_ARG, "unknown kernel configuration");
     if (fmt == GKO_FMT_AUTO) return fail(GKO_ERR_INVALID_ARG, "AUTO takes no explicit configuration");
     return spmv_dispatch(fmt, config, A, x, y, alpha, beta, static_cast<cudaStream_t>(stream));

@@ -460,7 +460,7 @@ static int cg1_product_f64(const gko_matrix* A, int fmt, const double* r, double
                            cudaStream_t cs)
 {
     const int64_t n = A->n_rows;
-    if (fmt == GKO_FMT_CSR && A->nnz > 0 && rowblock_preferred(A)) {
+    if (fmt == GKO_FMT_CSR && A->nnz > 0 && default_csr_config(A) == GKO_CFG_CSR_ROWBLOCK) {
         const cudaError_t e = rowblock_cg1_f64(A, r, w, red, cs);
         return e == cudaSuccess ? GKO_OK : cuda_fail(e, "single-reduction CG product");
     }

@@ -810,6 +810,7 @@ void free_format(gko_matrix* A, int fmt)
             dev_free(A->csr.col);
             dev_free(A->csr.val);
             dev_free(A->csr.thr_row);
+            dev_free(A->csr.bin_rows);
             seg_free(&A->csr.seg);
             break;
         case GKO_FMT_COO:

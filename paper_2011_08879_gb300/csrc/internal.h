@@ -79,7 +79,10 @@ struct CsrPart {
     int32_t max_len = 0;
     double mean_len = 0.0;
     int32_t band = -1;  // max |i - j| (computed at analysis), -1 unknown
+    int32_t* bin_rows = nullptr;  // rows grouped by length bin (binned kernel)
+    int64_t bin_off[7] = {0, 0, 0, 0, 0, 0, 0};
 };
+constexpr int kCsrBins = 6;
 
 struct CooPart {
     int32_t* row = nullptr;
@@ -184,6 +187,7 @@ int spmv_csr_banded(const gko_matrix* A, const double* x, double* y, double alph
                     cudaStream_t st);
 int rowblock_rows(const gko_matrix* A);
 bool rowblock_preferred(const gko_matrix* A);
+int default_csr_config(const gko_matrix* A);  // kernel behind GKO_CFG_DEFAULT for CSR
 cudaError_t rowblock_lowprec_f32(const gko_matrix* A, const float* val, const float* x, float* y, cudaStream_t st);
 cudaError_t rowblock_lowprec_bf16(const gko_matrix* A, const void* val, const float* x, float* y, cudaStream_t st);
 struct Cg1Reduce;  // solver.cuh
@@ -206,8 +210,8 @@ int validate_csr(int64_t n_rows, int64_t n_cols, int64_t nnz, const int32_t* row
                  const int32_t* col, cudaStream_t st);
 void free_format(gko_matrix* A, int fmt);
 
-// exclusive scan of int32 counts into int64 offsets (device); total -> *sum (device, may be null)
-int exclusive_scan_i64(const int32_t* in, int64_t* out, int64_t n, cudaStream_t st);
+// out[0..n] = exclusive scan of in[0..n-1] on the device (out[n] = total)
+int exclusive_scan(const int64_t* in, int64_t* out, int64_t n, cudaStream_t st);
 
 // BLAS-1 and solvers (blas1.cu, cg.cu)
 int cg_solve(const gko_matrix* A, int fmt, const double* b, double* x, double tol, int maxit,

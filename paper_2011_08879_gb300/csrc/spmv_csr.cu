@@ -2,7 +2,9 @@
 //  * classical subwarp-per-row kernel (subwarp of 1..32 lanes, chosen at
 //    run time; the paper's cooperative-group subwarps and Listing 2's
 //    butterfly reduction);
-//  * load-balanced equal-nnz kernel (segmented.cuh), the default;
+//  * load-balanced equal-nnz kernel (segmented.cuh);
+//  * binned kernel: rows grouped by length, each group by subwarps sized to
+//    it (the default for skewed rows);
 //  * banded kernel: the x window of a row block staged in shared memory.
 #include <algorithm>
 
@@ -55,6 +57,65 @@ __global__ void row_stats_kernel(int64_t n_rows, const int32_t* __restrict__ row
         atomicMax(out, mx);
         atomicMax(out + 1, band);
     }
+}
+
+// Row-length bins of the binned kernel: bin b holds the rows whose length
+// lies in (kBinMax[b-1], kBinMax[b]]; the last bin is unbounded.
+__host__ __device__ __forceinline__ int csr_bin(int32_t len)
+{
+    return len <= 8 ? 0 : len <= 20 ? 1 : len <= 48 ? 2 : len <= 128 ? 3 : len <= 512 ? 4 : 5;
+}
+
+__global__ void bin_flag_kernel(int64_t n_rows, const int32_t* __restrict__ row_ptr, int b,
+                                int64_t* __restrict__ flag)
+{
+    const int64_t r = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+    if (r < n_rows) flag[r] = csr_bin(row_ptr[r + 1] - row_ptr[r]) == b;
+}
+
+// stable scatter: rows of bin b in ascending order at out[off[r]]
+__global__ void bin_scatter_kernel(int64_t n_rows, const int32_t* __restrict__ row_ptr, int b,
+                                   const int64_t* __restrict__ off, int32_t* __restrict__ out)
+{
+    const int64_t r = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+    if (r < n_rows && csr_bin(row_ptr[r + 1] - row_ptr[r]) == b) out[off[r]] = static_cast<int32_t>(r);
+}
+
+// Build bin_rows (the rows grouped by bin, ascending inside each bin) and
+// the bin offsets.  Synchronises the stream (bin sizes are read back).
+static int csr_build_bins(gko_matrix* A, cudaStream_t st)
+{
+    CsrPart& c = A->csr;
+    const int64_t n = A->n_rows;
+    dev_free(c.bin_rows);
+    for (int b = 0; b <= kCsrBins; ++b) c.bin_off[b] = 0;
+    if (n == 0) return GKO_OK;
+    GKO_TRY(dev_alloc(&c.bin_rows, n));
+    int64_t *flag, *off;
+    GKO_TRY(dev_alloc(&flag, n));
+    if (dev_alloc(&off, n + 1) != GKO_OK) {
+        cudaFree(flag);
+        return GKO_ERR_OUT_OF_MEMORY;
+    }
+    int s = GKO_OK;
+    int64_t base = 0;
+    for (int b = 0; b < kCsrBins && s == GKO_OK; ++b) {
+        bin_flag_kernel<<<ceil_div(n, 256), 256, 0, st>>>(n, c.row_ptr, b, flag);
+        s = exclusive_scan(flag, off, n, st);
+        if (s != GKO_OK) break;
+        bin_scatter_kernel<<<ceil_div(n, 256), 256, 0, st>>>(n, c.row_ptr, b, off, c.bin_rows + base);
+        int64_t cnt = 0;
+        cudaError_t e = cudaMemcpyAsync(&cnt, off + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) s = cuda_fail(e, "row binning");
+        c.bin_off[b] = base;
+        base += cnt;
+        c.bin_off[b + 1] = base;
+    }
+    cudaFree(flag);
+    cudaFree(off);
+    if (s == GKO_OK) GKO_CUDA(cudaGetLastError());
+    return s;
 }
 
 int seg_alloc(SegArrays* s, int64_t nnz, int P)
@@ -113,7 +174,7 @@ int csr_analyse(gko_matrix* A, cudaStream_t st)
     c.max_len = h[0];
     c.band = h[1];
     c.mean_len = A->n_rows ? static_cast<double>(A->nnz) / A->n_rows : 0.0;
-    return GKO_OK;
+    return csr_build_bins(A, st);
 }
 
 // ------------------------------------------------------------ y = beta*y
@@ -183,6 +244,145 @@ static void launch_subwarp(const gko_matrix* A, const double* x, double* y, doub
 #undef GKO_SW_LAUNCH
 }
 
+// ------------------------------------------------- binned rows (skewed)
+
+// Four entries of one lane: indices and values of entries k, k + S, k + 2S,
+// k + 3S (those below k1) are loaded first, then the four gathers are
+// issued, then two FMA chains.  With x gathered at random from L2 (skewed,
+// unstructured matrices) each lane thus keeps four gathers in flight
+// instead of one per memory round trip.
+template <int S>
+__device__ __forceinline__ void fma4(int32_t k, int32_t k1, const int32_t* __restrict__ col,
+                                     const double* __restrict__ val, const double* __restrict__ x, double& a0,
+                                     double& a1)
+{
+    int32_t c[4];
+    double v[4], xv[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int32_t kk = k + u * S;
+        c[u] = kk < k1 ? col[kk] : -1;
+        v[u] = kk < k1 ? val[kk] : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) xv[u] = c[u] >= 0 ? ldg(x + c[u]) : 0.0;
+    if (c[0] >= 0) a0 = fma(v[0], xv[0], a0);
+    if (c[1] >= 0) a1 = fma(v[1], xv[1], a1);
+    if (c[2] >= 0) a0 = fma(v[2], xv[2], a0);
+    if (c[3] >= 0) a1 = fma(v[3], xv[3], a1);
+}
+
+// The subwarp-per-row kernel over a list of rows (one bin of the binned
+// kernel): subwarp s of the warp takes rows[base + s], its lanes step
+// through the row four entries at a time (fma4).  On matrices whose columns
+// are spread at random (power-law rows over 2M columns) every gather is a
+// separate 32-byte L2 sector; GB300 serves such gathers at ~270 G/s (one
+// per SM clock), which bounds those products, not HBM bandwidth.
+template <int SW, bool kAlpha, bool kBeta>
+__global__ void __launch_bounds__(256)
+    csr_list_kernel(int64_t count, const int32_t* __restrict__ rows, const int32_t* __restrict__ row_ptr,
+                    const int32_t* __restrict__ col, const double* __restrict__ val, const double* __restrict__ x,
+                    double* __restrict__ y, double alpha, double beta)
+{
+    using G = subwarp<SW>;
+    constexpr int kRowsPerWarp = kWarp / SW;
+    const int lane = G::rank();
+    const int sub = (threadIdx.x % kWarp) / SW;
+    const int64_t warp = (blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x) / kWarp;
+    const int64_t n_warps = static_cast<int64_t>(gridDim.x) * blockDim.x / kWarp;
+    for (int64_t base = warp * kRowsPerWarp; base < count; base += n_warps * kRowsPerWarp) {
+        const int64_t q = base + sub;
+        const int32_t r = q < count ? rows[q] : 0;
+        double a0 = 0.0, a1 = 0.0;
+        if (q < count) {
+            const int32_t k1 = row_ptr[r + 1];
+            for (int32_t k = row_ptr[r] + lane; k < k1; k += 4 * SW) fma4<SW>(k, k1, col, val, x, a0, a1);
+        }
+        const double acc = G::reduce_sum(a0 + a1);
+        if (q < count && lane == 0) seg_store<kAlpha, kBeta>(y, r, acc, alpha, beta);
+    }
+}
+
+// One CTA of 256 threads per long row (rows[i] for i = block, block + grid,
+// ...): entries four per thread at a time (fma4), two FMA chains, then
+// warp sums and the 8 warp totals added in warp order (deterministic).
+template <bool kAlpha, bool kBeta>
+__global__ void __launch_bounds__(256)
+    csr_list_block_kernel(int64_t count, const int32_t* __restrict__ rows, const int32_t* __restrict__ row_ptr,
+                          const int32_t* __restrict__ col, const double* __restrict__ val,
+                          const double* __restrict__ x, double* __restrict__ y, double alpha, double beta)
+{
+    __shared__ double sh[8];
+    for (int64_t q = blockIdx.x; q < count; q += gridDim.x) {
+        const int32_t r = rows[q];
+        const int32_t k0 = row_ptr[r], k1 = row_ptr[r + 1];
+        double a0 = 0.0, a1 = 0.0;
+        for (int32_t k = k0 + static_cast<int32_t>(threadIdx.x); k < k1; k += 1024)
+            fma4<256>(k, k1, col, val, x, a0, a1);
+        const double t = subwarp<32>::reduce_sum(a0 + a1);
+        if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = t;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double tot = 0.0;
+            for (int w = 0; w < 8; ++w) tot += sh[w];
+            seg_store<kAlpha, kBeta>(y, r, tot, alpha, beta);
+        }
+        __syncthreads();
+    }
+}
+
+template <int SW, bool kAlpha, bool kBeta>
+static void launch_list(int64_t count, const int32_t* rows, const gko_matrix* A, const double* x, double* y,
+                        double alpha, double beta, cudaStream_t st)
+{
+    if (count <= 0) return;
+    const CsrPart& c = A->csr;
+    if (SW == 0) {
+        const int grid = static_cast<int>(std::min<int64_t>(count, 152LL * 8));
+        csr_list_block_kernel<kAlpha, kBeta><<<grid, 256, 0, st>>>(count, rows, c.row_ptr, c.col, c.val, x, y, alpha,
+                                                                  beta);
+        return;
+    }
+    constexpr int kSW = SW > 0 ? SW : 1;
+    const int64_t rows_per_block = 256 / kSW;
+    const int grid = static_cast<int>(std::min<int64_t>((count + rows_per_block - 1) / rows_per_block, 152LL * 16));
+    csr_list_kernel<kSW, kAlpha, kBeta><<<grid, 256, 0, st>>>(count, rows, c.row_ptr, c.col, c.val, x, y, alpha,
+                                                              beta);
+}
+
+// Binned CSR SpMV: every row is computed once by the kernel of its length
+// bin (1, 2, 4, 8 or 32 lanes per row, or a whole CTA for rows longer than
+// 512), so rows of any length mix take full occupancy, each entry one FMA,
+// and no partial sums cross threads except the lanes of one row.
+template <bool kAlpha, bool kBeta>
+static void launch_binned_ab(const gko_matrix* A, const double* x, double* y, double alpha, double beta,
+                             cudaStream_t st)
+{
+    const CsrPart& c = A->csr;
+    auto cnt = [&](int b) { return c.bin_off[b + 1] - c.bin_off[b]; };
+    auto rows = [&](int b) { return c.bin_rows + c.bin_off[b]; };
+    launch_list<1, kAlpha, kBeta>(cnt(0), rows(0), A, x, y, alpha, beta, st);
+    launch_list<2, kAlpha, kBeta>(cnt(1), rows(1), A, x, y, alpha, beta, st);
+    launch_list<4, kAlpha, kBeta>(cnt(2), rows(2), A, x, y, alpha, beta, st);
+    launch_list<8, kAlpha, kBeta>(cnt(3), rows(3), A, x, y, alpha, beta, st);
+    launch_list<32, kAlpha, kBeta>(cnt(4), rows(4), A, x, y, alpha, beta, st);
+    launch_list<0, kAlpha, kBeta>(cnt(5), rows(5), A, x, y, alpha, beta, st);
+}
+
+static void launch_binned(const gko_matrix* A, const double* x, double* y, double alpha, double beta,
+                          cudaStream_t st)
+{
+    const bool a = alpha != 1.0, b = beta != 0.0;
+    if (a && b)
+        launch_binned_ab<true, true>(A, x, y, alpha, beta, st);
+    else if (a)
+        launch_binned_ab<true, false>(A, x, y, alpha, beta, st);
+    else if (b)
+        launch_binned_ab<false, true>(A, x, y, alpha, beta, st);
+    else
+        launch_binned_ab<false, false>(A, x, y, alpha, beta, st);
+}
+
 // --------------------------------------------------- load-balanced launch
 
 static SegScratch scratch_of(const SegArrays& sa)
@@ -229,6 +429,22 @@ int launch_seg(int64_t n_rows, int64_t nnz, const int32_t* row_ptr, const int32_
 
 // ------------------------------------------------------------- dispatch
 
+// Kernel behind GKO_CFG_DEFAULT, from the row-length statistics, as measured
+// on GB300 (FP64, L2 flushed): rows of close length (max <= 2 mean + 16) go
+// one thread per row with direct loads when at most 8 long (7-point 160^3:
+// 73 % of HBM bandwidth vs 61 % for the staged row blocks), staged row blocks
+// up to 20 (random banded, 16 per row: 69 %), four lanes per row beyond
+// (27-point 128^3: 69 % vs 58 %); skewed rows take the row-length bins
+// (power-law 2M rows, mean 20, max 20k: 327 us vs 439 us for the equal-nnz
+// split; random gathers of x bound that matrix, see csr_list_kernel).
+int default_csr_config(const gko_matrix* A)
+{
+    if (!rowblock_preferred(A)) return GKO_CFG_CSR_BINNED;
+    if (A->csr.max_len <= 8) return GKO_CFG_CSR_SUBWARP_1;
+    if (A->csr.max_len <= 20) return GKO_CFG_CSR_ROWBLOCK;
+    return GKO_CFG_CSR_SUBWARP_4;
+}
+
 int spmv_csr(const gko_matrix* A, int config, const double* x, double* y, double alpha, double beta,
              cudaStream_t st)
 {
@@ -243,9 +459,15 @@ int spmv_csr(const gko_matrix* A, int config, const double* x, double* y, double
         case GKO_CFG_CSR_SUBWARP_32: launch_subwarp<32>(A, x, y, alpha, beta, st); break;
         case GKO_CFG_CSR_ROWBLOCK: return spmv_csr_rowblock(A, x, y, alpha, beta, st);
         case GKO_CFG_CSR_BANDED: return spmv_csr_banded(A, x, y, alpha, beta, st);
+        case GKO_CFG_CSR_BINNED: launch_binned(A, x, y, alpha, beta, st); break;
         case GKO_CFG_DEFAULT:
-            if (rowblock_preferred(A)) return spmv_csr_rowblock(A, x, y, alpha, beta, st);
-            [[fallthrough]];
+            switch (default_csr_config(A)) {
+                case GKO_CFG_CSR_SUBWARP_1: launch_subwarp<1>(A, x, y, alpha, beta, st); break;
+                case GKO_CFG_CSR_SUBWARP_4: launch_subwarp<4>(A, x, y, alpha, beta, st); break;
+                case GKO_CFG_CSR_ROWBLOCK: return spmv_csr_rowblock(A, x, y, alpha, beta, st);
+                default: launch_binned(A, x, y, alpha, beta, st); break;
+            }
+            break;
         case GKO_CFG_CSR_NNZSPLIT:
             return launch_seg(A->n_rows, A->nnz, A->csr.row_ptr, nullptr, A->csr.col, A->csr.val, A->csr.thr_row,
                               A->csr.seg, x, y, alpha, beta, A->d_err, false, st, false);

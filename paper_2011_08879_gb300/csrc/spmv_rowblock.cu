@@ -207,7 +207,7 @@ __global__ void __launch_bounds__(kRbThreads, 2)
 #pragma unroll
                 for (int u = 0; u < CH; u += 2) {
                     if (j0 + u < len) acc0 = fma(to_t<V, T>(sv[kk[u]]), xv[u], acc0);
-                    if (j0 + u + 1 < len) acc1 = fma(to_t<V, T>(sv[kk[u + 1]]), xv[u + 1], acc1);
+                    if (u + 1 < CH && j0 + u + 1 < len) acc1 = fma(to_t<V, T>(sv[kk[u + 1]]), xv[u + 1], acc1);
                 }
             }
             const T w = acc0 + acc1;

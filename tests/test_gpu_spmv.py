@@ -12,7 +12,7 @@ import synthetic as syn
 pytestmark = pytest.mark.gpu
 
 FORMATS = ("csr", "coo", "ell", "sellp", "hybrid")
-CSR_CONFIGS = (1, 2, 3, 4, 5, 6, 7)  # subwarp 1..32, load-balanced
+CSR_CONFIGS = (1, 2, 3, 4, 5, 6, 7, 10)  # subwarp 1..32, load-balanced, binned
 
 
 def mats():
