@@ -7,10 +7,12 @@ characteristics").  This module learns the choice:
 * sweep: for each synthetic matrix, time every (format, kernel) candidate
   with CUDA events (L2 flushed between repetitions, median of the reps) and
   record the 12 matrix statistics computed by gko_features;
-* train: a 12 -> 64 -> 64 -> C MLP regresses each candidate's log time per
-  stored entry; the forward pass, the gradients and the Adam updates all
-  run in the library's kernels (gko_mlp_forward / gko_mlp_grad /
-  gko_mlp_adam), on the GPU;
+* train: a 12 -> 64 -> 64 -> C MLP regresses each candidate's log10
+  slowdown against the matrix's fastest candidate (capped); the forward
+  pass, the gradients and the Adam updates all run in the library's
+  kernels (gko_mlp_forward / gko_mlp_grad / gko_mlp_adam), on the GPU; the
+  initialisation seed is chosen on a validation split of the training
+  matrices;
 * evaluate: the chosen candidate is the argmin of the predictions; the
   regret is t(chosen) / t(best) - 1 against the exhaustive best.
 
@@ -18,7 +20,7 @@ The sweep checks that every candidate agrees with the others; the
 agreement with the CPU oracle is checked by the GPU tests.
 
 Command line (writes the weights and a JSON report):
-    python -m paper_2011_08879_gb300.selector --train 1000:1500 --test 3000:3100 --out weights.json
+    python -m paper_2011_08879_gb300.selector --train 1000:2000 --test 3000:3200 --out weights.json
 """
 from __future__ import annotations
 
@@ -43,6 +45,8 @@ CANDIDATES = (
     ("ell", 0),
     ("sellp", 0),
     ("hybrid", 0),
+    ("csr", B.CFG_CSR_BINNED),
+    ("csr", B.CFG_CSR_SUBWARP_1),
 )
 CLASS_NAMES = ["%s/%d" % c for c in CANDIDATES]
 DEFAULT_WEIGHTS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "selector_weights.json")
@@ -65,9 +69,14 @@ def prepare(A, stream=0):
     return M
 
 
-def measure(M, reps=5, warmup=2, flush_bytes=256 << 20, check=True, seed=7):
+def measure(M, reps=5, warmup=2, flush_bytes=256 << 20, check=True, seed=7, spin_s=0.005):
     """Median time (s) of every candidate on handle M (NaN: not applicable),
-    plus the worst relative disagreement between candidates."""
+    plus the worst relative disagreement between candidates.
+
+    The GPU is first kept busy for spin_s (clocks leave their idle state
+    after the host-side set-up of the matrix), then the candidates are timed
+    round robin, one repetition of each per round with L2 flushed before
+    every run, so that slow drifts of the clock hit every candidate alike."""
     torch = _torch()
     dev = torch.device("cuda", torch.cuda.current_device())
     st = torch.cuda.current_stream()
@@ -78,40 +87,58 @@ def measure(M, reps=5, warmup=2, flush_bytes=256 << 20, check=True, seed=7):
     times = np.full(len(CANDIDATES), np.nan)
     ref = None
     worst = 0.0
-    for ci, (fmt, cfg) in enumerate(CANDIDATES):
+    live = []
+    for ci, (fmt, cfg) in enumerate(CANDIDATES):  # applicability, warm-up and the agreement check
         if not M.has(fmt):
             continue
         try:
             M.spmv(x, y, fmt=fmt, config=cfg, stream=st.cuda_stream)
         except B.GkoError:
             continue  # configuration does not apply to this matrix
-        ts = []
-        for r in range(warmup + reps):
-            flush.fill_(1.0)
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(st)
+        live.append(ci)
+        for _ in range(warmup - 1):
             M.spmv(x, y, fmt=fmt, config=cfg, stream=st.cuda_stream)
-            e1.record(st)
-            if r >= warmup:
-                ts.append((e0, e1))
-        torch.cuda.synchronize()
-        times[ci] = float(np.median([a.elapsed_time(b) for a, b in ts])) * 1e-3
         if check:
             if ref is None:
                 ref = y.clone()
                 scale = float(ref.abs().max()) + 1e-300
             else:
                 worst = max(worst, float((y - ref).abs().max()) / scale)
+    t_end = time.perf_counter() + spin_s
+    while time.perf_counter() < t_end:
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+    ev = {ci: [] for ci in live}
+    for _ in range(reps):
+        for ci in live:
+            fmt, cfg = CANDIDATES[ci]
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            M.spmv(x, y, fmt=fmt, config=cfg, stream=st.cuda_stream)
+            e1.record(st)
+            ev[ci].append((e0, e1))
+    torch.cuda.synchronize()
+    for ci in live:
+        times[ci] = float(np.median([a.elapsed_time(b) for a, b in ev[ci]])) * 1e-3
     return times, worst
 
 
-def targets(times, nnz):
-    """Regression targets: log10 of the time per stored entry, mask of the
-    measured candidates."""
+TARGET_CAP = 1.5  # log10 of the slowdown beyond which candidates count as equally bad
+
+
+def targets(times, nnz=None):
+    """Regression targets: log10 of each candidate's slowdown against the
+    matrix's fastest candidate, capped at TARGET_CAP (a candidate 30x slower
+    only needs to be predicted as clearly bad, not how bad), and the mask of
+    the measured candidates.  The argmin of the predictions is the choice,
+    which a per-matrix offset does not change; the relative targets remove
+    the common size-dependent part that absolute times would make the
+    network learn first."""
     with np.errstate(invalid="ignore", divide="ignore"):
-        t = np.log10(times / max(nnz, 1))
+        t = np.log10(times / np.nanmin(times))
     mask = np.isfinite(t).astype(np.float32)
-    return np.where(mask > 0, t, 0.0).astype(np.float32), mask
+    return np.where(mask > 0, np.minimum(t, TARGET_CAP), 0.0).astype(np.float32), mask
 
 
 # ------------------------------------------------------------------ sweep
@@ -232,17 +259,55 @@ def regret(times, choice):
     return t / best - 1.0
 
 
+def default_csr_class(F):
+    """Candidate index of the library's default CSR kernel (GKO_CFG_DEFAULT)
+    for each matrix, from its statistics (mean and max row length): rows of
+    close length (max <= 2 mean + 16, max <= 128) one thread per row up to 8
+    long, staged row blocks up to 20, four lanes per row beyond; skewed rows
+    the binned kernel."""
+    out = []
+    for f in F:
+        mean_len, max_len = f[2], f[4]
+        if max_len <= 128 and max_len <= 2.0 * mean_len + 16.0 and max_len >= 1:
+            cfg = B.CFG_CSR_SUBWARP_1 if max_len <= 8 else (B.CFG_CSR_ROWBLOCK if max_len <= 20 else B.CFG_CSR_SUBWARP_4)
+        else:
+            cfg = B.CFG_CSR_BINNED
+        out.append(CLASS_NAMES.index("csr/%d" % cfg))
+    return np.array(out, dtype=int)
+
+
 def evaluate(params, mean, scale, F, T):
     pred = predict(params, mean, scale, F)
     pred = np.where(np.isfinite(T), pred, np.inf)  # only candidates the matrix admits
     choice = np.argmin(pred, axis=1)
     r = regret(T, choice)
-    # the method without the selector: the library's default CSR kernel,
-    # and the single candidate that is best on average over the training set
-    csr_default = regret(T, np.zeros(len(T), dtype=int) + CLASS_NAMES.index("csr/%d" % B.CFG_CSR_NNZSPLIT))
+    # the method without the selector: the library's default CSR kernel
+    csr_default = regret(T, default_csr_class(F))
     return dict(mean=float(r.mean()), median=float(np.median(r)), p90=float(np.percentile(r, 90)),
-                max=float(r.max()), csr_nnzsplit_mean=float(csr_default.mean()),
+                max=float(r.max()), csr_default_mean=float(csr_default.mean()),
                 choices={CLASS_NAMES[c]: int((choice == c).sum()) for c in np.unique(choice)})
+
+
+def train_select(F, T, seeds=(0, 1, 2, 3, 4, 5), val_frac=0.2, epochs=600, log=None):
+    """Train one network per seed on (1 - val_frac) of the matrices and keep
+    the one with the lowest mean regret on the rest (model selection on a
+    validation split of the training matrices only); returns it retrained
+    on all of them with the chosen seed."""
+    rng = np.random.default_rng(12345)
+    order = rng.permutation(len(F))
+    n_val = max(1, int(len(F) * val_frac))
+    va, tr = order[:n_val], order[n_val:]
+    Y, Mk = (np.array(a) for a in zip(*[targets(t) for t in T]))
+    best = None
+    for sd in seeds:
+        p, mu, sc = train(F[tr], Y[tr], Mk[tr], epochs=epochs, seed=sd)
+        r = evaluate(p, mu, sc, F[va], T[va])["mean"]
+        if log:
+            log("seed %d validation regret %.4f" % (sd, r))
+        if best is None or r < best[0]:
+            best = (r, sd)
+    params, mean, scale = train(F, Y, Mk, epochs=epochs, seed=best[1])
+    return params, mean, scale, dict(seed=best[1], validation_regret=best[0])
 
 
 def save(path, params, mean, scale, report):
@@ -272,12 +337,14 @@ def _range(s):
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("--train", default="1000:1500")
-    ap.add_argument("--test", default="3000:3100")
+    ap.add_argument("--train", default="1000:2000")
+    ap.add_argument("--test", default="3000:3200")
     ap.add_argument("--workers", type=int, default=max(1, min(12, (os.cpu_count() or 2) - 2)))
     ap.add_argument("--epochs", type=int, default=600)
     ap.add_argument("--out", default=DEFAULT_WEIGHTS)
     ap.add_argument("--report", default="")
+    ap.add_argument("--save-sweep", default="", help="write the sweep (features, times, nnz) to this .npz")
+    ap.add_argument("--load-sweep", default="", help="train and evaluate on a saved sweep instead of timing")
     args = ap.parse_args(argv)
 
     def log(s):
@@ -285,12 +352,24 @@ def main(argv=None):
 
     t0 = time.time()
     tr, te = _range(args.train), _range(args.test)
-    Ftr, Ttr, Ntr, Str, w1 = sweep(tr, args.workers, log)
-    Fte, Tte, Nte, Ste, w2 = sweep(te, args.workers, log)
+    if args.load_sweep:
+        z = np.load(args.load_sweep, allow_pickle=False)
+        if list(z["classes"]) != CLASS_NAMES:
+            raise SystemExit("saved sweep has other candidates: %s" % list(z["classes"]))
+        Ftr, Ttr, Ntr, Str = z["Ftr"], z["Ttr"], z["Ntr"], list(z["Str"])
+        Fte, Tte, Nte, Ste = z["Fte"], z["Tte"], z["Nte"], list(z["Ste"])
+        w1 = w2 = float(z["worst"])
+        tr, te = list(z["seeds_tr"]), list(z["seeds_te"])
+    else:
+        Ftr, Ttr, Ntr, Str, w1 = sweep(tr, args.workers, log)
+        Fte, Tte, Nte, Ste, w2 = sweep(te, args.workers, log)
+        if args.save_sweep:
+            np.savez(args.save_sweep, classes=np.array(CLASS_NAMES), Ftr=Ftr, Ttr=Ttr, Ntr=Ntr, Str=np.array(Str),
+                     Fte=Fte, Tte=Tte, Nte=Nte, Ste=np.array(Ste), worst=max(w1, w2), seeds_tr=np.array(tr),
+                     seeds_te=np.array(te))
     t_sweep = time.time() - t0
-    Y, Mk = zip(*[targets(t, n) for t, n in zip(Ttr, Ntr)])
     t1 = time.time()
-    params, mean, scale = train(Ftr, np.array(Y), np.array(Mk), epochs=args.epochs, log=log)
+    params, mean, scale, sel_info = train_select(Ftr, Ttr, epochs=args.epochs, log=log)
     t_train = time.time() - t1
     rep = evaluate(params, mean, scale, Fte, Tte)
     rep_train = evaluate(params, mean, scale, Ftr, Ttr)
@@ -301,7 +380,7 @@ def main(argv=None):
     rep["fixed_best_mean"] = float(regret(Tte, np.full(len(Tte), fixed)).mean())
     # selector latency: features + forward for one matrix (host-timed)
     report = dict(test=rep, train_mean=rep_train["mean"], n_train=len(tr), n_test=len(te), sweep_s=t_sweep,
-                  train_s=t_train, max_candidate_disagreement=max(w1, w2),
+                  train_s=t_train, model_selection=sel_info, max_candidate_disagreement=max(w1, w2),
                   structures_test={s: Ste.count(s) for s in set(Ste)})
     save(args.out, params, mean, scale, report)
     out = json.dumps(report)
