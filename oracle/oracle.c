@@ -20,7 +20,8 @@
  * does not define follow their standard definitions: ELL and hybrid ELL+COO
  * (Bell and Garland, SC'09), SELL-P (Anzt, Tomov and Dongarra, 2014);
  * CG is the method of Hestenes and Stiefel (1952), also in the
- * single-reduction form of Chronopoulos and Gear (1989); Dot2 is Algorithm 5.3 of
+ * single-reduction form of Chronopoulos and Gear (1989) and preconditioned by
+ * the diagonal (Jacobi); Dot2 is Algorithm 5.3 of
  * Ogita, Rump and Oishi, "Accurate sum and dot product" (SISC 2005).
  */
 #include <math.h>
@@ -685,6 +686,102 @@ int orc_cg_single_reduction(int64_t n, const int32_t *row_ptr, const int32_t *co
     free(p);
     free(s);
     free(w);
+    return status;
+}
+
+/* CG preconditioned by the diagonal of A (Jacobi preconditioner, M = D):
+ * the textbook preconditioned conjugate gradient method (e.g. Saad,
+ * "Iterative Methods for Sparse Linear Systems", 2nd ed., Alg. 9.1):
+ *   r = b - A x0, z = D^-1 r, p = z, rho = r.z
+ *   repeat: q = A p; alpha = rho / (p.q); x += alpha p; r -= alpha q;
+ *           z = D^-1 r; rho' = r.z; beta = rho' / rho; p = z + beta p.
+ * Stopping on the unpreconditioned recursive residual ||r|| <= tol ||b||,
+ * with the same true-residual confirmation as orc_cg.  A zero or missing
+ * diagonal entry, a non-positive p.q or a NaN is a breakdown.  *iters
+ * counts the products q = A p. */
+int orc_pcg_jacobi(int64_t n, const int32_t *row_ptr, const int32_t *col, const double *val,
+                   const double *b, double *x, double tol, int maxit, int *iters, double *rel_res)
+{
+    double nb = nrm2(n, b);
+    *iters = 0;
+    if (nb == 0.0) {
+        for (int64_t i = 0; i < n; ++i)
+            x[i] = 0.0;
+        *rel_res = 0.0;
+        return ORC_OK;
+    }
+    size_t bytes = (size_t)(n > 0 ? n : 1) * sizeof(double);
+    double *r = (double *)malloc(bytes), *p = (double *)malloc(bytes),
+           *q = (double *)malloc(bytes), *z = (double *)malloc(bytes),
+           *d = (double *)malloc(bytes);
+    int status = ORC_NOT_CONVERGED, checks = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        d[i] = 0.0;
+        for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k)
+            if (col[k] == i)
+                d[i] = val[k];
+        if (!(d[i] != 0.0))
+            status = ORC_BREAKDOWN;
+    }
+    if (status == ORC_BREAKDOWN)
+        maxit = 0;
+    for (int64_t i = 0; i < n; ++i)
+        r[i] = b[i];
+    orc_spmv_csr(n, row_ptr, col, val, x, -1.0, 1.0, r);
+    for (int64_t i = 0; i < n; ++i) {
+        z[i] = r[i] / d[i];
+        p[i] = z[i];
+    }
+    double rho = orc_dot(n, r, z);
+    if (status != ORC_BREAKDOWN && sqrt(orc_dot(n, r, r)) <= tol * nb) {
+        status = ORC_OK;
+        maxit = 0;
+    }
+    for (int it = 0; it < maxit; ++it) {
+        orc_spmv_csr(n, row_ptr, col, val, p, 1.0, 0.0, q);
+        *iters = it + 1;
+        double pq = orc_dot(n, p, q);
+        if (!(pq > 0.0)) {
+            status = ORC_BREAKDOWN;
+            break;
+        }
+        double alpha = rho / pq;
+        for (int64_t i = 0; i < n; ++i) {
+            double t = alpha * p[i];
+            x[i] = x[i] + t;
+            double u = alpha * q[i];
+            r[i] = r[i] - u;
+            z[i] = r[i] / d[i];
+        }
+        double rr = orc_dot(n, r, r);
+        double rho_new = orc_dot(n, r, z);
+        if (!(rr == rr) || !(rho_new == rho_new)) {
+            status = ORC_BREAKDOWN;
+            break;
+        }
+        if (sqrt(rr) <= tol * nb) {
+            double t = orc_true_rel_residual(n, row_ptr, col, val, b, x);
+            ++checks;
+            if (t <= tol) {
+                status = ORC_OK;
+                break;
+            }
+            if (checks >= 4)
+                break;
+        }
+        double beta = rho_new / rho;
+        for (int64_t i = 0; i < n; ++i) {
+            double t = beta * p[i];
+            p[i] = z[i] + t;
+        }
+        rho = rho_new;
+    }
+    *rel_res = orc_true_rel_residual(n, row_ptr, col, val, b, x);
+    free(r);
+    free(p);
+    free(q);
+    free(z);
+    free(d);
     return status;
 }
 

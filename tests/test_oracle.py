@@ -362,6 +362,72 @@ def test_cg_single_reduction_special_cases(orc):
     assert st == orc.OK and it == 0
 
 
+def _scaled(A, s):
+    """D A D for the diagonal scaling s (SPD stays SPD)."""
+    rows = np.repeat(np.arange(A["n_rows"]), np.diff(A["row_ptr"]))
+    B = dict(A)
+    B["val"] = A["val"] * s[rows] * s[A["col_idx"]]
+    return B
+
+
+def test_pcg_jacobi_diagonal_matrix_one_step(orc):
+    """M = A when A is diagonal: the preconditioned system is the identity
+    and one step gives the exact solution."""
+    eigs = 1.0 + np.arange(40) * 0.37
+    A = _diag_spd(eigs)
+    b = syn.vector(40, 21)
+    x, st, it, res = orc.pcg_jacobi(A, b, tol=1e-14)
+    assert st == orc.OK and it == 1
+    assert np.allclose(x, b / eigs, rtol=1e-15, atol=0)
+
+
+def test_pcg_jacobi_constant_diagonal_equals_cg(orc):
+    """A constant diagonal makes D^-1 a multiple of the identity: the
+    iterates are those of plain CG (same steps, same solution)."""
+    A = syn.laplace2d(48)
+    n = A["n_rows"]
+    b = orc.spmv_csr(A, syn.vector(n, 22))
+    for k in (1, 5, 30):
+        xa, _, _, _ = orc.cg(A, b, maxit=k)
+        xb, _, _, _ = orc.pcg_jacobi(A, b, maxit=k)
+        assert np.linalg.norm(xa - xb) <= 1e-11 * np.linalg.norm(xa)
+    _, s0, i0, _ = orc.cg(A, b, tol=1e-10)
+    _, s1, i1, r1 = orc.pcg_jacobi(A, b, tol=1e-10)
+    assert s0 == s1 == orc.OK and abs(i0 - i1) <= 1 and r1 <= 1e-10
+
+
+def test_pcg_jacobi_removes_bad_row_scaling(orc):
+    """On D A D with a wildly varying D, Jacobi PCG needs about the steps
+    of A itself while plain CG needs many more; both reach the manufactured
+    solution."""
+    A0 = syn.laplace2d(32)
+    n = A0["n_rows"]
+    s = 10.0 ** (3.0 * syn.uniform01(23, 1, np.arange(n, dtype=np.uint64)))
+    A = _scaled(A0, s)
+    xt = syn.vector(n, 24)
+    b = orc.spmv_csr(A, xt)
+    xc, sc, ic, rc = orc.cg(A, b, tol=1e-10, maxit=20000)
+    xp, sp, ip, rp = orc.pcg_jacobi(A, b, tol=1e-10, maxit=20000)
+    _, _, i0, _ = orc.cg(A0, orc.spmv_csr(A0, xt), tol=1e-10)
+    assert sp == orc.OK and rp <= 1e-10
+    assert ip <= 1.5 * i0 + 10 and ic > 3 * ip
+    assert np.linalg.norm(xp - xt) <= 1e-5 * np.linalg.norm(xt)
+
+
+def test_pcg_jacobi_special_cases(orc):
+    A = syn.laplace2d(8)
+    n = A["n_rows"]
+    x, st, it, res = orc.pcg_jacobi(A, np.zeros(n), x0=np.ones(n))
+    assert st == orc.OK and it == 0 and np.all(x == 0)
+    b = orc.spmv_csr(A, syn.vector(n, 2))
+    x, st, it, res = orc.pcg_jacobi(A, b, maxit=2)
+    assert st == orc.NOT_CONVERGED and it == 2
+    Z = dict(A)
+    Z["val"] = np.where(A["col_idx"] == np.repeat(np.arange(n), np.diff(A["row_ptr"])), 0.0, A["val"])
+    x, st, it, res = orc.pcg_jacobi(Z, b)
+    assert st == orc.BREAKDOWN and it == 0
+
+
 def test_batched_cg(orc):
     B = syn.batched_spd(12, seed=8)
     x, st, it, res = orc.cg_batched(B, B["rhs"], tol=1e-10)
