@@ -413,7 +413,8 @@ def run_extras(gko, torch, dev, st):
     M.convert("ell", stream=st)
     # FP64 CG: Hestenes-Stiefel and single-reduction forms, CSR and ELL products
     for key, solve, fmt in (("fp64", M.cg, "csr"), ("fp64_single_reduction", M.cg_single_reduction, "csr"),
-                            ("fp64_ell", M.cg, "ell"), ("fp64_single_reduction_ell", M.cg_single_reduction, "ell")):
+                            ("fp64_ell", M.cg, "ell"), ("fp64_single_reduction_ell", M.cg_single_reduction, "ell"),
+                            ("fp64_jacobi_pcg_ell", M.pcg_jacobi, "ell")):
         for _ in range(2):
             x = torch.zeros_like(b)
             t, info = _time_call(torch, lambda: solve(b, x, tol=1e-10, maxit=20000, fmt=fmt, stream=st))

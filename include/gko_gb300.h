@@ -257,6 +257,22 @@ int gko_cg(const gko_matrix* A, int fmt, const double* b, double* x, double tol,
 int gko_cg_single_reduction(const gko_matrix* A, int fmt, const double* b, double* x, double tol, int maxit,
                             void* stream, gko_solve_info* info);
 
+/* Conjugate gradients preconditioned by the diagonal of A (Jacobi
+ * preconditioner M = diag(A)): the Krylov solver of Sec. 6.2 with the
+ * simplest preconditioner, the textbook preconditioned CG
+ *   r = b - A x0, z = M^-1 r, p = z, rho = r.z;
+ *   q = A p, alpha = rho / p.q, x += alpha p, r -= alpha q, z = M^-1 r,
+ *   rho' = r.z, beta = rho' / rho, p = z + beta p
+ * (z is never stored: the update kernel forms r.M^-1 r and ||r||^2 in one
+ * pass, the direction update reads r and the inverted diagonal).  Products
+ * with format fmt; the diagonal is read from the CSR part, which must be
+ * materialised.  Stops on the unpreconditioned recursive residual
+ * ||r|| <= tol ||b|| confirmed by the FP64 true residual (up to four
+ * times), at maxit or on breakdown; a zero or missing diagonal entry
+ * returns GKO_ERR_BREAKDOWN before any step.  Otherwise as gko_cg. */
+int gko_pcg_jacobi(const gko_matrix* A, int fmt, const double* b, double* x, double tol, int maxit, void* stream,
+                   gko_solve_info* info);
+
 /* Mixed-precision CG with FP64 iterative refinement.  The inner CG runs on
  * a copy of A stored in inner_dtype (GKO_F32 or GKO_BF16; off-diagonals
  * rounded to nearest-even, the diagonal a_ii + sum_j(|rn(a_ij)| - |a_ij|)

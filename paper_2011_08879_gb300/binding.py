@@ -60,6 +60,7 @@ _SIGS = {
     "gko_spmv_coo_noalloc": (_INT, [_I64, _I64, _I64, _P, _P, _P, _P, _P, _D, _D, _P, _P]),
     "gko_cg": (_INT, [_P, _INT, _P, _P, _D, _INT, _P, C.POINTER(SolveInfo)]),
     "gko_cg_single_reduction": (_INT, [_P, _INT, _P, _P, _D, _INT, _P, C.POINTER(SolveInfo)]),
+    "gko_pcg_jacobi": (_INT, [_P, _INT, _P, _P, _D, _INT, _P, C.POINTER(SolveInfo)]),
     "gko_cg_mixed": (_INT, [_P, _INT, _P, _P, _D, _INT, _D, _INT, _P, C.POINTER(SolveInfo)]),
     "gko_batch_create": (_INT, [_I64, _P, _P, _P, _P, _INT, _P, C.POINTER(_P)]),
     "gko_batch_destroy": (_INT, [_P]),
@@ -182,6 +183,16 @@ def gko_cg_single_reduction(A, fmt, b, x, tol, maxit, stream=0, raise_on=()) -> 
     s = lib.gko_cg_single_reduction(A, fmt, b, x, tol, maxit, stream, C.byref(info))
     allow = tuple(c for c in (ERR_NOT_CONVERGED, ERR_BREAKDOWN) if c not in raise_on)
     _check(s, "gko_cg_single_reduction", allow)
+    info.status = s
+    return info
+
+
+def gko_pcg_jacobi(A, fmt, b, x, tol, maxit, stream=0, raise_on=()) -> SolveInfo:
+    """As gko_cg, preconditioned by the diagonal of A."""
+    info = SolveInfo()
+    s = lib.gko_pcg_jacobi(A, fmt, b, x, tol, maxit, stream, C.byref(info))
+    allow = tuple(c for c in (ERR_NOT_CONVERGED, ERR_BREAKDOWN) if c not in raise_on)
+    _check(s, "gko_pcg_jacobi", allow)
     info.status = s
     return info
 

@@ -120,6 +120,102 @@ __global__ void __launch_bounds__(kRedThreads)
         p[i] = fma(beta, p[i], r[i]);
 }
 
+// ------------------------------------------------ Jacobi preconditioning
+
+// dinv[i] = 1 / a_ii (rows sorted by column: the first entry >= i); a zero
+// or missing diagonal sets *bad (the preconditioner does not exist)
+__global__ void diag_inv_kernel(int64_t n, const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                                const double* __restrict__ val, double* __restrict__ dinv, int32_t* bad)
+{
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        double d = 0.0;
+        for (int32_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k)
+            if (col[k] >= i) {
+                if (col[k] == i) d = val[k];
+                break;
+            }
+        dinv[i] = d != 0.0 ? 1.0 / d : 0.0;
+        if (!(d != 0.0)) atomicOr(bad, 1);
+    }
+}
+
+// Preconditioned CG step (z = D^-1 r is never stored):
+// x += alpha p; r -= alpha q; rr = r.r (stopping), rz = r.D^-1 r
+// (rho' for beta); stop tests on sqrt(rr) as in update_kernel
+__global__ void __launch_bounds__(kRedThreads)
+    pcg_update_kernel(int64_t n, double* __restrict__ x, double* __restrict__ r, const double* __restrict__ p,
+                      const double* __restrict__ q, const double* __restrict__ dinv, SolverState* s, double* part,
+                      cudaGraphConditionalHandle h)
+{
+    if (s->done) return;
+    const double alpha = s->alpha;
+    double rr = 0.0, rz = 0.0;
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(kRedThreads) + threadIdx.x; i < n;
+         i += static_cast<int64_t>(gridDim.x) * kRedThreads) {
+        x[i] = fma(alpha, p[i], x[i]);
+        const double ri = fma(-alpha, q[i], r[i]);
+        r[i] = ri;
+        rr = fma(ri, ri, rr);
+        rz = fma(ri, ri * dinv[i], rz);
+    }
+    grid_sum2(rr, rz, part, &s->ticket, [&](double rr_new, double rho_new) {
+        if (!(rr_new == rr_new) || !(rho_new == rho_new)) {
+            s->status = GKO_ERR_BREAKDOWN;
+            stop_loop(s, h);
+            return;
+        }
+        s->beta = rho_new / s->rho;
+        s->rho = rho_new;
+        s->dot_out = rr_new;
+        if (sqrt(rr_new) <= s->tol * s->stop_ref) {
+            s->conv = 1;
+            s->status = GKO_OK;
+            stop_loop(s, h);
+        } else if (s->iter >= s->maxit) {
+            s->status = GKO_ERR_NOT_CONVERGED;
+            stop_loop(s, h);
+        }
+    });
+}
+
+// p = D^-1 r + beta p (beta_mode 0: the state's beta; 1: beta = 0, the
+// initial direction)
+__global__ void __launch_bounds__(kRedThreads)
+    pcg_pupdate_kernel(int64_t n, double* __restrict__ p, const double* __restrict__ r,
+                       const double* __restrict__ dinv, const SolverState* s, int force, int initial)
+{
+    if (s->done && !force) return;
+    const double beta = initial ? 0.0 : s->beta;
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(kRedThreads) + threadIdx.x; i < n;
+         i += static_cast<int64_t>(gridDim.x) * kRedThreads)
+        p[i] = initial ? r[i] * dinv[i] : fma(beta, p[i], r[i] * dinv[i]);
+}
+
+// rho = r.D^-1 r and the initial stop test on ||r|| (state: rho, dot_out = r.r)
+__global__ void __launch_bounds__(kRedThreads)
+    pcg_init_dots_kernel(int64_t n, const double* __restrict__ r, const double* __restrict__ dinv, SolverState* s,
+                         double* part)
+{
+    double rr = 0.0, rz = 0.0;
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(kRedThreads) + threadIdx.x; i < n;
+         i += static_cast<int64_t>(gridDim.x) * kRedThreads) {
+        const double ri = r[i];
+        rr = fma(ri, ri, rr);
+        rz = fma(ri, ri * dinv[i], rz);
+    }
+    grid_sum2(rr, rz, part, &s->ticket, [&](double rr0, double rz0) {
+        s->rho = rz0;
+        s->rho0 = rz0;
+        s->dot_out = rr0;
+        if (sqrt(rr0) <= s->tol * s->stop_ref) {
+            s->conv = 1;
+            s->status = GKO_OK;
+            s->done = 1;
+        }
+    });
+}
+
 static int red_grid(int64_t n)
 {
     return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(kRedBlocks, (n + kRedThreads - 1) / kRedThreads)));
@@ -349,8 +445,10 @@ static void fill_info(gko_solve_info* info, int iters, int outer, double res, in
 
 // -------------------------------------------------------------- FP64 CG
 
-int cg_solve(const gko_matrix* A, int fmt, const double* b, double* x, double tol, int maxit, cudaStream_t st,
-             gko_solve_info* info)
+// Hestenes-Stiefel CG; jacobi: preconditioned by the diagonal of A (the
+// matrix's CSR part supplies the diagonal).
+static int cg_solve_impl(const gko_matrix* A, int fmt, const double* b, double* x, double tol, int maxit,
+                         cudaStream_t st, gko_solve_info* info, bool jacobi)
 {
     const int64_t n = A->n_rows;
     if (n == 0) {
@@ -358,14 +456,29 @@ int cg_solve(const gko_matrix* A, int fmt, const double* b, double* x, double to
         return GKO_OK;
     }
     Workspace ws(st);
-    double *r, *p, *q, *part;
+    double *r, *p, *q, *part, *dinv = nullptr;
     SolverState* ds;
     GKO_TRY(ws.get(&r, n));
     GKO_TRY(ws.get(&p, n));
     GKO_TRY(ws.get(&q, n));
-    GKO_TRY(ws.get(&part, kRedBlocks));
+    GKO_TRY(ws.get(&part, 2 * kRedBlocks));
     GKO_TRY(ws.get(&ds, 1));
     const int grid = red_grid(n);
+    if (jacobi) {
+        int32_t* bad;
+        GKO_TRY(ws.get(&dinv, n));
+        GKO_TRY(ws.get(&bad, 1));
+        GKO_CUDA(cudaMemsetAsync(bad, 0, sizeof(int32_t), st));
+        diag_inv_kernel<<<grid, kRedThreads, 0, st>>>(n, A->csr.row_ptr, A->csr.col, A->csr.val, dinv, bad);
+        int32_t hbad = 0;
+        GKO_CUDA(cudaMemcpyAsync(&hbad, bad, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        GKO_CUDA(cudaStreamSynchronize(st));
+        if (hbad) {
+            fill_info(info, 0, 0, -1.0, GKO_ERR_BREAKDOWN);
+            set_error("Jacobi preconditioner: a diagonal entry is zero or not stored");
+            return GKO_ERR_BREAKDOWN;
+        }
+    }
 
     SolverState hs = {};
     GKO_TRY(write_state(ds, &hs, st));
@@ -378,17 +491,22 @@ int cg_solve(const gko_matrix* A, int fmt, const double* b, double* x, double to
         fill_info(info, 0, 0, 0.0, GKO_OK);
         return GKO_OK;
     }
-    // r = b - A x, p = r, rho = r.r
+    // r = b - A x, p = r (D^-1 r), rho = r.r (r.D^-1 r)
     GKO_CUDA(cudaMemcpyAsync(r, b, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
     GKO_TRY(spmv_fmt(A, fmt, x, r, -1.0, 1.0, st));
-    GKO_CUDA(cudaMemcpyAsync(p, r, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
     hs = {};
     hs.tol = tol;
     hs.stop_ref = bnorm;
     hs.maxit = maxit;
     hs.status = GKO_ERR_NOT_CONVERGED;
     GKO_TRY(write_state(ds, &hs, st));
-    dot_kernel<double, kDotRhoInit><<<grid, kRedThreads, 0, st>>>(n, r, r, ds, part, 0);
+    if (jacobi) {
+        pcg_pupdate_kernel<<<grid, kRedThreads, 0, st>>>(n, p, r, dinv, ds, 1, 1);
+        pcg_init_dots_kernel<<<grid, kRedThreads, 0, st>>>(n, r, dinv, ds, part);
+    } else {
+        GKO_CUDA(cudaMemcpyAsync(p, r, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        dot_kernel<double, kDotRhoInit><<<grid, kRedThreads, 0, st>>>(n, r, r, ds, part, 0);
+    }
     GKO_TRY(read_state(&hs, ds, st));
     if (hs.conv) {  // r is the true residual here
         double res;
@@ -407,8 +525,13 @@ int cg_solve(const gko_matrix* A, int fmt, const double* b, double* x, double to
     GKO_TRY(build_while_graph(&gh, [&](cudaGraphConditionalHandle h, cudaStream_t cs) -> int {
         GKO_TRY(spmv_fmt(A, fmt, p, q, 1.0, 0.0, cs));
         dot_kernel<double, kDotPQ><<<grid, kRedThreads, 0, cs>>>(n, p, q, ds, part, h);
-        update_kernel<double><<<grid, kRedThreads, 0, cs>>>(n, x, r, p, q, ds, part, h);
-        pupdate_kernel<double><<<grid, kRedThreads, 0, cs>>>(n, p, r, ds, 0);
+        if (jacobi) {
+            pcg_update_kernel<<<grid, kRedThreads, 0, cs>>>(n, x, r, p, q, dinv, ds, part, h);
+            pcg_pupdate_kernel<<<grid, kRedThreads, 0, cs>>>(n, p, r, dinv, ds, 0, 0);
+        } else {
+            update_kernel<double><<<grid, kRedThreads, 0, cs>>>(n, x, r, p, q, ds, part, h);
+            pupdate_kernel<double><<<grid, kRedThreads, 0, cs>>>(n, p, r, ds, 0);
+        }
         GKO_CUDA(cudaGetLastError());
         return GKO_OK;
     }));
@@ -438,7 +561,10 @@ int cg_solve(const gko_matrix* A, int fmt, const double* b, double* x, double to
             hs.done = 0;
             hs.status = GKO_ERR_NOT_CONVERGED;
             GKO_CUDA(cudaMemcpyAsync(ds, &hs, sizeof(SolverState), cudaMemcpyHostToDevice, st));
-            pupdate_kernel<double><<<grid, kRedThreads, 0, st>>>(n, p, r, ds, 1);
+            if (jacobi)
+                pcg_pupdate_kernel<<<grid, kRedThreads, 0, st>>>(n, p, r, dinv, ds, 1, 0);
+            else
+                pupdate_kernel<double><<<grid, kRedThreads, 0, st>>>(n, p, r, ds, 1);
             res = -1.0;
             continue;
         }
@@ -450,6 +576,18 @@ int cg_solve(const gko_matrix* A, int fmt, const double* b, double* x, double to
     if (status != GKO_OK)
         set_error(status == GKO_ERR_BREAKDOWN ? "CG breakdown (p.q <= 0 or NaN)" : "CG reached maxit");
     return status;
+}
+
+int cg_solve(const gko_matrix* A, int fmt, const double* b, double* x, double tol, int maxit, cudaStream_t st,
+             gko_solve_info* info)
+{
+    return cg_solve_impl(A, fmt, b, x, tol, maxit, st, info, false);
+}
+
+int pcg_jacobi_solve(const gko_matrix* A, int fmt, const double* b, double* x, double tol, int maxit,
+                     cudaStream_t st, gko_solve_info* info)
+{
+    return cg_solve_impl(A, fmt, b, x, tol, maxit, st, info, true);
 }
 
 // ------------------------------------------------ single-reduction CG

@@ -220,6 +220,8 @@ int lp_ell_prepare(gko_matrix* A, bool bf16, cudaStream_t st, bool* usable);
 void lp_ell_free(gko_matrix* A);
 cudaError_t lp_ell_cg1(const gko_matrix* A, bool bf16, const float* r, float* w, Cg1Reduce red, cudaStream_t st);
 int lp_ell_grid(const gko_matrix* A);
+int pcg_jacobi_solve(const gko_matrix* A, int fmt, const double* b, double* x, double tol, int maxit,
+                     cudaStream_t st, gko_solve_info* info);
 int cg1_solve(const gko_matrix* A, int fmt, const double* b, double* x, double tol, int maxit,
               cudaStream_t st, gko_solve_info* info);
 int cg_mixed_solve(gko_matrix* A, int inner, const double* b, double* x, double tol, int maxit_outer,

@@ -127,6 +127,65 @@ def test_cg_single_reduction_special_cases(gko, dev, orc):
     assert info.status == gko.binding.ERR_BREAKDOWN
 
 
+@pytest.mark.parametrize("fmt", ["csr", "ell", "hybrid"])
+def test_pcg_jacobi_scaled_operator(gko, dev, orc, fmt):
+    """Diffusion operator rescaled by a diagonal spanning three decades: the
+    GPU's Jacobi PCG matches the oracle's step count and both reach the
+    manufactured solution; plain CG needs several times more steps."""
+    A0 = syn.diffusion7(24, 1.0, seed=6)
+    n = A0["n_rows"]
+    s = 10.0 ** (3.0 * syn.uniform01(25, 1, np.arange(n, dtype=np.uint64)))
+    rows = np.repeat(np.arange(n), np.diff(A0["row_ptr"]))
+    A = dict(A0)
+    A["val"] = A0["val"] * s[rows] * s[A0["col_idx"]]
+    xt = syn.vector(n, 26)
+    b = orc.spmv_csr(A, xt)
+    x_o, st_o, it_o, res_o = orc.pcg_jacobi(A, b, tol=1e-10, maxit=20000)
+    assert st_o == 0
+    M = gko.Matrix(A)
+    if fmt != "csr":
+        M.convert(fmt)
+    x = _t(np.zeros(n), dev)
+    info = M.pcg_jacobi(_t(b, dev), x, tol=1e-10, maxit=20000, fmt=fmt)
+    assert info.status == 0 and info.rel_residual <= 1e-10
+    assert abs(info.iterations - it_o) <= max(5, 0.02 * it_o), (info.iterations, it_o)
+    xg = x.cpu().numpy()
+    assert orc.true_rel_residual(A, b, xg) <= 1e-10
+    e_o = np.linalg.norm(x_o - xt) / np.linalg.norm(xt)
+    assert np.linalg.norm(xg - xt) / np.linalg.norm(xt) <= 10 * e_o + 1e-15
+    x2 = _t(np.zeros(n), dev)
+    info_cg = M.cg(_t(b, dev), x2, tol=1e-10, maxit=2000, fmt=fmt)
+    assert info_cg.iterations > 3 * info.iterations
+
+
+def test_pcg_jacobi_special_cases(gko, dev, orc):
+    A = syn.laplace2d(16)
+    n = A["n_rows"]
+    M = gko.Matrix(A)
+    x = _t(np.ones(n), dev)
+    info = M.pcg_jacobi(_t(np.zeros(n), dev), x)
+    assert info.status == 0 and info.iterations == 0 and float(x.abs().max()) == 0.0
+    b = orc.spmv_csr(A, syn.vector(n, 2))
+    x = _t(np.zeros(n), dev)
+    info = M.pcg_jacobi(_t(b, dev), x, maxit=3)
+    assert info.status == gko.binding.ERR_NOT_CONVERGED and info.iterations == 3
+    xo, _, _, _ = orc.pcg_jacobi(A, b, maxit=3)
+    assert np.linalg.norm(x.cpu().numpy() - xo) <= 1e-12 * np.linalg.norm(xo)
+    # constant diagonal: the same steps as plain CG
+    x = _t(np.zeros(n), dev)
+    info = M.pcg_jacobi(_t(b, dev), x, tol=1e-10)
+    x2 = _t(np.zeros(n), dev)
+    info2 = M.cg(_t(b, dev), x2, tol=1e-10)
+    assert abs(info.iterations - info2.iterations) <= 1
+    # a zero diagonal entry: breakdown before any step
+    Z = dict(A)
+    rows = np.repeat(np.arange(n), np.diff(A["row_ptr"]))
+    Z["val"] = np.where((A["col_idx"] == rows) & (rows == 7), 0.0, A["val"])
+    x = _t(np.zeros(n), dev)
+    info = gko.Matrix(Z).pcg_jacobi(_t(b, dev), x)
+    assert info.status == gko.binding.ERR_BREAKDOWN and info.iterations == 0
+
+
 def test_cg_special_cases(gko, dev, orc):
     A = syn.laplace2d(16)
     n = A["n_rows"]
