@@ -21,7 +21,7 @@
  * (Bell and Garland, SC'09), SELL-P (Anzt, Tomov and Dongarra, 2014);
  * CG is the method of Hestenes and Stiefel (1952), also in the
  * single-reduction form of Chronopoulos and Gear (1989) and preconditioned by
- * the diagonal (Jacobi); Dot2 is Algorithm 5.3 of
+ * the diagonal (Jacobi); BiCGSTAB is van der Vorst's (1992); Dot2 is Algorithm 5.3 of
  * Ogita, Rump and Oishi, "Accurate sum and dot product" (SISC 2005).
  */
 #include <math.h>
@@ -782,6 +782,144 @@ int orc_pcg_jacobi(int64_t n, const int32_t *row_ptr, const int32_t *col, const 
     free(q);
     free(z);
     free(d);
+    return status;
+}
+
+/* BiCGSTAB (van der Vorst, "Bi-CGSTAB: a fast and smoothly converging
+ * variant of Bi-CG for the solution of nonsymmetric linear systems", SISC
+ * 13, 1992) for general square A, shadow residual r^ = r0:
+ *   r = b - A x0, r^ = r, rho = alpha = omega = 1, v = p = 0
+ *   repeat: rho' = r^.r; beta = (rho'/rho)(alpha/omega); p = r + beta (p - omega v)
+ *           v = A p; alpha = rho' / (r^.v); s = r - alpha v
+ *           if ||s|| <= tol ||b||: x += alpha p, stop (half step)
+ *           t = A s; omega = (t.s)/(t.t); x += alpha p + omega s; r = s - omega t
+ *           rho = rho'
+ * Stopping on the recursive residual with the true-residual confirmation of
+ * orc_cg; rho' = 0, r^.v = 0, t.t = 0 (or omega = 0) or a NaN is a
+ * breakdown.  *iters counts full and half steps (each half step one
+ * product, a full step two). */
+int orc_bicgstab(int64_t n, const int32_t *row_ptr, const int32_t *col, const double *val,
+                 const double *b, double *x, double tol, int maxit, int *iters, double *rel_res)
+{
+    double nb = nrm2(n, b);
+    *iters = 0;
+    if (nb == 0.0) {
+        for (int64_t i = 0; i < n; ++i)
+            x[i] = 0.0;
+        *rel_res = 0.0;
+        return ORC_OK;
+    }
+    size_t bytes = (size_t)(n > 0 ? n : 1) * sizeof(double);
+    double *r = (double *)malloc(bytes), *rh = (double *)malloc(bytes), *p = (double *)malloc(bytes),
+           *v = (double *)malloc(bytes), *sv = (double *)malloc(bytes), *t = (double *)malloc(bytes);
+    for (int64_t i = 0; i < n; ++i)
+        r[i] = b[i];
+    orc_spmv_csr(n, row_ptr, col, val, x, -1.0, 1.0, r);
+    for (int64_t i = 0; i < n; ++i) {
+        rh[i] = r[i];
+        p[i] = 0.0;
+        v[i] = 0.0;
+    }
+    double rho = 1.0, alpha = 1.0, omega = 1.0;
+    int status = ORC_NOT_CONVERGED, checks = 0;
+    if (nrm2(n, r) <= tol * nb) {
+        status = ORC_OK;
+        maxit = 0;
+    }
+    for (int it = 0; it < maxit; ++it) {
+        double rho_new = orc_dot(n, rh, r);
+        if (!(rho_new != 0.0) || !(rho_new == rho_new)) {
+            status = ORC_BREAKDOWN;
+            break;
+        }
+        double beta = (rho_new / rho) * (alpha / omega);
+        for (int64_t i = 0; i < n; ++i) {
+            double u = omega * v[i];
+            double w = p[i] - u;
+            double z = beta * w;
+            p[i] = r[i] + z;
+        }
+        orc_spmv_csr(n, row_ptr, col, val, p, 1.0, 0.0, v);
+        double rv = orc_dot(n, rh, v);
+        if (!(rv != 0.0) || !(rv == rv)) {
+            status = ORC_BREAKDOWN;
+            break;
+        }
+        alpha = rho_new / rv;
+        for (int64_t i = 0; i < n; ++i) {
+            double u = alpha * v[i];
+            sv[i] = r[i] - u;
+        }
+        *iters = it + 1;
+        if (nrm2(n, sv) <= tol * nb) { /* half step */
+            for (int64_t i = 0; i < n; ++i) {
+                double u = alpha * p[i];
+                x[i] = x[i] + u;
+            }
+            double tr = orc_true_rel_residual(n, row_ptr, col, val, b, x);
+            ++checks;
+            if (tr <= tol) {
+                status = ORC_OK;
+                break;
+            }
+            if (checks >= 4)
+                break;
+            /* unconfirmed: restart from the true residual of this iterate */
+            for (int64_t i = 0; i < n; ++i)
+                r[i] = b[i];
+            orc_spmv_csr(n, row_ptr, col, val, x, -1.0, 1.0, r);
+            for (int64_t i = 0; i < n; ++i) {
+                rh[i] = r[i];
+                p[i] = 0.0;
+                v[i] = 0.0;
+            }
+            rho = alpha = omega = 1.0;
+            continue;
+        }
+        orc_spmv_csr(n, row_ptr, col, val, sv, 1.0, 0.0, t);
+        double tt = orc_dot(n, t, t);
+        double ts = orc_dot(n, t, sv);
+        if (!(tt > 0.0) || !(ts == ts)) {
+            status = ORC_BREAKDOWN;
+            break;
+        }
+        omega = ts / tt;
+        if (!(omega != 0.0)) {
+            status = ORC_BREAKDOWN;
+            break;
+        }
+        for (int64_t i = 0; i < n; ++i) {
+            double u = alpha * p[i];
+            double w = omega * sv[i];
+            x[i] = x[i] + u;
+            x[i] = x[i] + w;
+            double z = omega * t[i];
+            r[i] = sv[i] - z;
+        }
+        rho = rho_new;
+        double nr = nrm2(n, r);
+        if (!(nr == nr)) {
+            status = ORC_BREAKDOWN;
+            break;
+        }
+        if (nr <= tol * nb) {
+            double tr = orc_true_rel_residual(n, row_ptr, col, val, b, x);
+            ++checks;
+            if (tr <= tol) {
+                status = ORC_OK;
+                break;
+            }
+            if (checks >= 4)
+                break;
+        }
+    }
+    *rel_res = orc_true_rel_residual(n, row_ptr, col, val, b, x);
+    free(r);
+    free(rh);
+    free(p);
+    free(v);
+    free(sv);
+    free(t);
     return status;
 }
 

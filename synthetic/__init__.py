@@ -172,6 +172,22 @@ def laplace2d(nx: int = 128) -> dict:
     return _csr_from_sorted(n, n, rows[order], cols[order], vals[order], grid=(nx, nx))
 
 
+def convdiff2d(nx: int = 64, wind: float = 0.5) -> dict:
+    """Nonsymmetric 2D convection-diffusion operator on an nx x nx grid: the
+    5-point Laplacian (diagonal 4, neighbours -1, Dirichlet, row i + nx*j)
+    plus a centred first difference along i with weight `wind` (east
+    neighbour -1 + wind/2, west neighbour -1 - wind/2)."""
+    A = laplace2d(nx)
+    n = A["n_rows"]
+    rows = np.repeat(np.arange(n, dtype=np.int64), np.diff(A["row_ptr"]))
+    d = A["col_idx"].astype(np.int64) - rows
+    v = A["val"].copy()
+    v[d == 1] += 0.5 * wind
+    v[d == -1] -= 0.5 * wind
+    A["val"] = v
+    return A
+
+
 def stencil27(nx: int = 128, seed: int = 2) -> dict:
     """3D 27-point stencil pattern on an nx^3 grid (row i + nx*j + nx^2*k),
     out-of-grid neighbours dropped, values uniform in [-1, 1)."""

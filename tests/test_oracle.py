@@ -428,6 +428,70 @@ def test_pcg_jacobi_special_cases(orc):
     assert st == orc.BREAKDOWN and it == 0
 
 
+def test_bicgstab_scaled_identity_one_step(orc):
+    """A = c I: v = c p, alpha = 1/c, s = 0 after the first half step, so
+    x = b / c exactly (a closed form of one step)."""
+    n = 50
+    A = _diag_spd(np.full(n, 2.5))
+    b = syn.vector(n, 31)
+    x, st, it, res = orc.bicgstab(A, b, tol=1e-14)
+    assert st == orc.OK and it == 1
+    assert np.allclose(x, b / 2.5, rtol=1e-15, atol=0)
+
+
+def test_bicgstab_matches_dense_solve(orc):
+    """Small nonsymmetric systems (random sparse, made diagonally dominant)
+    against numpy's dense LU solve."""
+    for seed in (41, 42, 43):
+        A = syn.random_csr(120, 120, 6, seed=seed)
+        n = 120
+        rows = np.repeat(np.arange(n), np.diff(A["row_ptr"]))
+        D = dense(A)
+        D = D + np.diag(1.0 + np.abs(D).sum(axis=1))
+        # write the dominant diagonal back into a CSR with every diagonal stored
+        Dm = np.where(np.abs(D) > 0, D, 0.0)
+        rp = np.concatenate([[0], np.cumsum((Dm != 0).sum(axis=1))]).astype(np.int32)
+        ci = np.nonzero(Dm)[1].astype(np.int32)
+        B = dict(n_rows=n, n_cols=n, row_ptr=rp, col_idx=ci, val=Dm[Dm != 0])
+        b = syn.vector(n, seed)
+        x, st, it, res = orc.bicgstab(B, b, tol=1e-13)
+        assert st == orc.OK and res <= 1e-13
+        assert np.allclose(x, np.linalg.solve(Dm, b), rtol=1e-10, atol=1e-12)
+
+
+def test_bicgstab_convection_diffusion(orc):
+    """Nonsymmetric convection-diffusion: BiCGSTAB reaches the manufactured
+    solution; its recursive residual agrees with b - A x at the end."""
+    A = syn.convdiff2d(48, 0.8)
+    n = A["n_rows"]
+    D = dense(A)
+    assert not np.allclose(D, D.T)
+    xt = syn.vector(n, 32)
+    b = orc.spmv_csr(A, xt)
+    x, st, it, res = orc.bicgstab(A, b, tol=1e-10)
+    assert st == orc.OK and res <= 1e-10
+    cond = np.linalg.cond(D)
+    assert np.linalg.norm(x - xt) <= cond * 1e-10 * np.linalg.norm(xt)
+    assert it < n // 4
+
+
+def test_bicgstab_special_cases(orc):
+    A = syn.convdiff2d(8, 0.5)
+    n = A["n_rows"]
+    x, st, it, res = orc.bicgstab(A, np.zeros(n), x0=np.ones(n))
+    assert st == orc.OK and it == 0 and np.all(x == 0)
+    b = orc.spmv_csr(A, syn.vector(n, 2))
+    x, st, it, res = orc.bicgstab(A, b, maxit=2)
+    assert st == orc.NOT_CONVERGED and it == 2
+    x, st, it, res = orc.bicgstab(A, b, x0=syn.vector(n, 2))
+    assert st == orc.OK and it == 0
+    # rho' = r^.r = 0 cannot happen for r != 0; A = 0 gives r^.v = 0: breakdown
+    Z = dict(A)
+    Z["val"] = np.zeros_like(A["val"])
+    x, st, it, res = orc.bicgstab(Z, b)
+    assert st == orc.BREAKDOWN
+
+
 def test_batched_cg(orc):
     B = syn.batched_spd(12, seed=8)
     x, st, it, res = orc.cg_batched(B, B["rhs"], tol=1e-10)
