@@ -439,6 +439,28 @@ def test_bicgstab_scaled_identity_one_step(orc):
     assert np.allclose(x, b / 2.5, rtol=1e-15, atol=0)
 
 
+def test_bicgstab_finite_termination(orc):
+    """BiCGSTAB's residual is psi_k(A) phi_k(A) r0 with phi_k the BiCG
+    polynomial, which annihilates r0 once k reaches the degree of the
+    minimal polynomial: a diagonalizable nonsymmetric matrix with three
+    distinct eigenvalues (upper-triangular 2x2 blocks with eigenvalue pairs
+    from {1, 2, 3}) is solved in at most three steps."""
+    blocks = [((1.0, 0.7), (0.0, 2.0)), ((2.0, 0.3), (0.0, 3.0)), ((3.0, -0.5), (0.0, 1.0))]
+    nb = 30
+    rp, ci, va = [0], [], []
+    for k in range(nb):
+        (a, b_), (_, c) = blocks[k % 3]
+        r0 = 2 * k
+        ci += [r0, r0 + 1]; va += [a, b_]; rp.append(len(ci))
+        ci += [r0 + 1]; va += [c]; rp.append(len(ci))
+    A = dict(n_rows=2 * nb, n_cols=2 * nb, row_ptr=np.array(rp, np.int32), col_idx=np.array(ci, np.int32),
+             val=np.array(va))
+    b = syn.vector(2 * nb, 33)
+    x, st, it, res = orc.bicgstab(A, b, tol=1e-12)
+    assert st == orc.OK and it <= 3, (st, it, res)
+    assert np.allclose(dense(A) @ x, b, rtol=0, atol=1e-11)
+
+
 def test_bicgstab_matches_dense_solve(orc):
     """Small nonsymmetric systems (random sparse, made diagonally dominant)
     against numpy's dense LU solve."""
