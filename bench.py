@@ -436,6 +436,22 @@ def run_extras(gko, torch, dev, st):
     res["speedup_fp32_vs_best_fp64"] = round(best64 / res["fp32"]["s"], 3)
     res["speedup_bf16_vs_best_fp64"] = round(best64 / res["bf16"]["s"], 3)
     out["cg_diffusion7_160"] = res
+    # BiCGSTAB on a nonsymmetric convection-diffusion operator (1024^2 grid)
+    C = syn.convdiff2d(1024, 0.8)
+    n = C["n_rows"]
+    M = gko.Matrix(C, stream=st)
+    M.convert("ell", stream=st)
+    xt = torch.from_numpy(syn.vector(n, 8)).to(dev)
+    b = torch.empty_like(xt)
+    M.spmv(xt, b, stream=st)
+    res = {}
+    for fmt in ("csr", "ell"):
+        for _ in range(2):
+            x = torch.zeros_like(b)
+            t, info = _time_call(torch, lambda: M.bicgstab(b, x, tol=1e-10, maxit=20000, fmt=fmt, stream=st))
+        res[fmt] = {"s": round(t, 4), "steps": info.iterations, "rel_residual": info.rel_residual,
+                    "status": info.status}
+    out["bicgstab_convdiff2d_1024"] = res
     B = load_workload("batched_4096")
     G = gko.Batch(B, stream=st)
     rhs = torch.from_numpy(B["rhs"]).to(dev)

@@ -273,6 +273,23 @@ int gko_cg_single_reduction(const gko_matrix* A, int fmt, const double* b, doubl
 int gko_pcg_jacobi(const gko_matrix* A, int fmt, const double* b, double* x, double tol, int maxit, void* stream,
                    gko_solve_info* info);
 
+/* BiCGSTAB (van der Vorst, SIAM J. Sci. Stat. Comput. 13, 1992) on A x = b
+ * for a general (nonsymmetric) square A, a Krylov solver of Sec. 6.2 for
+ * systems CG does not cover.  Shadow residual r^ = r0; per step
+ *   rho' = r^.r, beta = (rho'/rho)(alpha/omega), p = r + beta (p - omega v),
+ *   v = A p, alpha = rho' / r^.v, s = r - alpha v,
+ *   t = A s, omega = t.s / t.t, x += alpha p + omega s, r = s - omega t
+ * (two products with format fmt, FP64 throughout, scalars on the device,
+ * the loop inside a CUDA graph).  When ||s|| <= tol ||b|| the step ends
+ * half way (x += alpha p).  Converged steps are confirmed by the FP64 true
+ * residual (up to four times): an unconfirmed half step restarts from the
+ * true residual, an unconfirmed full step continues.  r^.v = 0, t.t = 0,
+ * omega = 0, rho' = 0 or a NaN is GKO_ERR_BREAKDOWN; maxit steps
+ * GKO_ERR_NOT_CONVERGED.  info->iterations counts steps (half or full).
+ * ||b|| = 0 returns x = 0.  Synchronises the stream. */
+int gko_bicgstab(const gko_matrix* A, int fmt, const double* b, double* x, double tol, int maxit, void* stream,
+                 gko_solve_info* info);
+
 /* Mixed-precision CG with FP64 iterative refinement.  The inner CG runs on
  * a copy of A stored in inner_dtype (GKO_F32 or GKO_BF16; off-diagonals
  * rounded to nearest-even, the diagonal a_ii + sum_j(|rn(a_ij)| - |a_ij|)

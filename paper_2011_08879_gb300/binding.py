@@ -61,6 +61,7 @@ _SIGS = {
     "gko_cg": (_INT, [_P, _INT, _P, _P, _D, _INT, _P, C.POINTER(SolveInfo)]),
     "gko_cg_single_reduction": (_INT, [_P, _INT, _P, _P, _D, _INT, _P, C.POINTER(SolveInfo)]),
     "gko_pcg_jacobi": (_INT, [_P, _INT, _P, _P, _D, _INT, _P, C.POINTER(SolveInfo)]),
+    "gko_bicgstab": (_INT, [_P, _INT, _P, _P, _D, _INT, _P, C.POINTER(SolveInfo)]),
     "gko_cg_mixed": (_INT, [_P, _INT, _P, _P, _D, _INT, _D, _INT, _P, C.POINTER(SolveInfo)]),
     "gko_batch_create": (_INT, [_I64, _P, _P, _P, _P, _INT, _P, C.POINTER(_P)]),
     "gko_batch_destroy": (_INT, [_P]),
@@ -193,6 +194,16 @@ def gko_pcg_jacobi(A, fmt, b, x, tol, maxit, stream=0, raise_on=()) -> SolveInfo
     s = lib.gko_pcg_jacobi(A, fmt, b, x, tol, maxit, stream, C.byref(info))
     allow = tuple(c for c in (ERR_NOT_CONVERGED, ERR_BREAKDOWN) if c not in raise_on)
     _check(s, "gko_pcg_jacobi", allow)
+    info.status = s
+    return info
+
+
+def gko_bicgstab(A, fmt, b, x, tol, maxit, stream=0, raise_on=()) -> SolveInfo:
+    """BiCGSTAB; NOT_CONVERGED and BREAKDOWN are reported in info.status."""
+    info = SolveInfo()
+    s = lib.gko_bicgstab(A, fmt, b, x, tol, maxit, stream, C.byref(info))
+    allow = tuple(c for c in (ERR_NOT_CONVERGED, ERR_BREAKDOWN) if c not in raise_on)
+    _check(s, "gko_bicgstab", allow)
     info.status = s
     return info
 

@@ -706,6 +706,331 @@ int cg1_solve(const gko_matrix* A, int fmt, const double* b, double* x, double t
     return status;
 }
 
+// ------------------------------------------------------------ BiCGSTAB
+
+// Device-resident scalars of BiCGSTAB (van der Vorst 1992).
+struct BicgState {
+    double rho;       // r^.r of the current residual (rho' of the coming step)
+    double alpha, omega, beta;
+    double rv, ss, tt, ts, rr;
+    double stop_ref, tol;
+    int32_t iter, maxit, done, status, conv, half;
+    uint32_t ticket;
+};
+
+__device__ __forceinline__ void bicg_stop(BicgState* s, cudaGraphConditionalHandle h)
+{
+    s->done = 1;
+    if (h) cudaGraphSetConditional(h, 0);
+}
+
+// p = r + beta (p - omega v)
+__global__ void __launch_bounds__(kRedThreads)
+    bicg_p_kernel(int64_t n, double* __restrict__ p, const double* __restrict__ r, const double* __restrict__ v,
+                  const BicgState* s)
+{
+    if (s->done) return;
+    const double beta = s->beta, omega = s->omega;
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(kRedThreads) + threadIdx.x; i < n;
+         i += static_cast<int64_t>(gridDim.x) * kRedThreads)
+        p[i] = fma(beta, fma(-omega, v[i], p[i]), r[i]);
+}
+
+// alpha = rho / (r^.v)
+__global__ void __launch_bounds__(kRedThreads)
+    bicg_alpha_kernel(int64_t n, const double* __restrict__ rh, const double* __restrict__ v, BicgState* s,
+                      double* part, cudaGraphConditionalHandle h)
+{
+    if (s->done) return;
+    double acc = 0.0;
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(kRedThreads) + threadIdx.x; i < n;
+         i += static_cast<int64_t>(gridDim.x) * kRedThreads)
+        acc = fma(rh[i], v[i], acc);
+    grid_sum(acc, part, &s->ticket, [&](double rv) {
+        s->rv = rv;
+        if (!(rv != 0.0) || !(rv == rv)) {
+            s->status = GKO_ERR_BREAKDOWN;
+            bicg_stop(s, h);
+            return;
+        }
+        s->alpha = s->rho / rv;
+    });
+}
+
+// s = r - alpha v, ss = s.s; a small s ends the step half way (x += alpha p
+// is then taken by the host-side finish)
+__global__ void __launch_bounds__(kRedThreads)
+    bicg_s_kernel(int64_t n, double* __restrict__ sv, const double* __restrict__ r, const double* __restrict__ v,
+                  BicgState* s, double* part, cudaGraphConditionalHandle h)
+{
+    if (s->done) return;
+    const double alpha = s->alpha;
+    double acc = 0.0;
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(kRedThreads) + threadIdx.x; i < n;
+         i += static_cast<int64_t>(gridDim.x) * kRedThreads) {
+        const double si = fma(-alpha, v[i], r[i]);
+        sv[i] = si;
+        acc = fma(si, si, acc);
+    }
+    grid_sum(acc, part, &s->ticket, [&](double ss) {
+        s->ss = ss;
+        if (!(ss == ss)) {
+            s->status = GKO_ERR_BREAKDOWN;
+            bicg_stop(s, h);
+        } else if (sqrt(ss) <= s->tol * s->stop_ref) {
+            s->half = 1;
+            s->conv = 1;
+            s->status = GKO_OK;
+            bicg_stop(s, h);
+        }
+    });
+}
+
+// omega = (t.s) / (t.t)
+__global__ void __launch_bounds__(kRedThreads)
+    bicg_omega_kernel(int64_t n, const double* __restrict__ t, const double* __restrict__ sv, BicgState* s,
+                      double* part, cudaGraphConditionalHandle h)
+{
+    if (s->done) return;
+    double tt = 0.0, ts = 0.0;
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(kRedThreads) + threadIdx.x; i < n;
+         i += static_cast<int64_t>(gridDim.x) * kRedThreads) {
+        const double ti = t[i];
+        tt = fma(ti, ti, tt);
+        ts = fma(ti, sv[i], ts);
+    }
+    grid_sum2(tt, ts, part, &s->ticket, [&](double tt_, double ts_) {
+        s->tt = tt_;
+        s->ts = ts_;
+        const double omega = ts_ / tt_;
+        if (!(tt_ > 0.0) || !(omega != 0.0) || !(omega == omega)) {
+            s->status = GKO_ERR_BREAKDOWN;
+            bicg_stop(s, h);
+            return;
+        }
+        s->omega = omega;
+    });
+}
+
+// x += alpha p + omega s; r = s - omega t; rho' = r^.r, rr = r.r; then the
+// next step's beta and the stop tests
+__global__ void __launch_bounds__(kRedThreads)
+    bicg_xr_kernel(int64_t n, double* __restrict__ x, double* __restrict__ r, const double* __restrict__ p,
+                   const double* __restrict__ sv, const double* __restrict__ t, const double* __restrict__ rh,
+                   BicgState* s, double* part, cudaGraphConditionalHandle h)
+{
+    if (s->done) return;
+    const double alpha = s->alpha, omega = s->omega;
+    double rho = 0.0, rr = 0.0;
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(kRedThreads) + threadIdx.x; i < n;
+         i += static_cast<int64_t>(gridDim.x) * kRedThreads) {
+        x[i] = fma(omega, sv[i], fma(alpha, p[i], x[i]));
+        const double ri = fma(-omega, t[i], sv[i]);
+        r[i] = ri;
+        rho = fma(rh[i], ri, rho);
+        rr = fma(ri, ri, rr);
+    }
+    grid_sum2(rho, rr, part, &s->ticket, [&](double rho_next, double rr_) {
+        s->iter += 1;
+        s->rr = rr_;
+        if (!(rr_ == rr_) || !(rho_next == rho_next)) {
+            s->status = GKO_ERR_BREAKDOWN;
+            bicg_stop(s, h);
+            return;
+        }
+        s->beta = (rho_next / s->rho) * (s->alpha / s->omega);
+        s->rho = rho_next;
+        if (sqrt(rr_) <= s->tol * s->stop_ref) {
+            s->conv = 1;
+            s->status = GKO_OK;
+            bicg_stop(s, h);
+        } else if (s->iter >= s->maxit) {
+            s->status = GKO_ERR_NOT_CONVERGED;
+            bicg_stop(s, h);
+        } else if (!(rho_next != 0.0)) {
+            s->status = GKO_ERR_BREAKDOWN;
+            bicg_stop(s, h);
+        }
+    });
+}
+
+// x += alpha p (the half step)
+__global__ void bicg_half_kernel(int64_t n, double* __restrict__ x, const double* __restrict__ p,
+                                 const BicgState* s)
+{
+    const double alpha = s->alpha;
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+        x[i] = fma(alpha, p[i], x[i]);
+}
+
+// r^ = r; p = v = 0; rho = r^.r (and rr); used at the start and to restart
+// from a true residual that did not confirm a half step
+__global__ void __launch_bounds__(kRedThreads)
+    bicg_restart_kernel(int64_t n, const double* __restrict__ r, double* __restrict__ rh, double* __restrict__ p,
+                        double* __restrict__ v, BicgState* s, double* part)
+{
+    double acc = 0.0;
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(kRedThreads) + threadIdx.x; i < n;
+         i += static_cast<int64_t>(gridDim.x) * kRedThreads) {
+        const double ri = r[i];
+        rh[i] = ri;
+        p[i] = 0.0;
+        v[i] = 0.0;
+        acc = fma(ri, ri, acc);
+    }
+    grid_sum(acc, part, &s->ticket, [&](double rr) {
+        s->rho = rr;
+        s->rr = rr;
+        s->alpha = s->omega = 1.0;
+        s->beta = 0.0;
+        s->conv = s->half = s->done = 0;
+        s->status = GKO_ERR_NOT_CONVERGED;
+        if (sqrt(rr) <= s->tol * s->stop_ref) {
+            s->conv = 1;
+            s->status = GKO_OK;
+            s->done = 1;
+        } else if (!(rr == rr)) {
+            s->status = GKO_ERR_BREAKDOWN;
+            s->done = 1;
+        }
+    });
+}
+
+// BiCGSTAB on A x = b (general square A).  Steps: p update, v = A p,
+// alpha, s = r - alpha v (+ ||s||), t = A s, omega, x/r update (+ r^.r,
+// ||r||): seven launches per step inside the graph's WHILE node.  A step
+// that ends half way (||s|| small) or a converged step is confirmed by the
+// FP64 true residual; an unconfirmed half step restarts from the true
+// residual (r^ = r), an unconfirmed full step continues (up to four checks).
+int bicgstab_solve(const gko_matrix* A, int fmt, const double* b, double* x, double tol, int maxit,
+                   cudaStream_t st, gko_solve_info* info)
+{
+    const int64_t n = A->n_rows;
+    if (n == 0) {
+        fill_info(info, 0, 0, 0.0, GKO_OK);
+        return GKO_OK;
+    }
+    Workspace ws(st);
+    double *r, *rh, *p, *v, *sv, *t, *part;
+    SolverState* ds;
+    BicgState* bs;
+    GKO_TRY(ws.get(&r, n));
+    GKO_TRY(ws.get(&rh, n));
+    GKO_TRY(ws.get(&p, n));
+    GKO_TRY(ws.get(&v, n));
+    GKO_TRY(ws.get(&sv, n));
+    GKO_TRY(ws.get(&t, n));
+    GKO_TRY(ws.get(&part, 2 * kRedBlocks));
+    GKO_TRY(ws.get(&ds, 1));
+    GKO_TRY(ws.get(&bs, 1));
+    const int grid = red_grid(n);
+
+    SolverState hs = {};
+    GKO_TRY(write_state(ds, &hs, st));
+    dot_kernel<double, kDotStore><<<grid, kRedThreads, 0, st>>>(n, b, b, ds, part, 0);
+    GKO_TRY(read_state(&hs, ds, st));
+    const double bnorm = std::sqrt(hs.dot_out);
+    if (bnorm == 0.0) {
+        GKO_CUDA(cudaMemsetAsync(x, 0, n * sizeof(double), st));
+        GKO_CUDA(cudaStreamSynchronize(st));
+        fill_info(info, 0, 0, 0.0, GKO_OK);
+        return GKO_OK;
+    }
+    BicgState hb = {};
+    hb.tol = tol;
+    hb.stop_ref = bnorm;
+    hb.maxit = maxit;
+    hb.status = GKO_ERR_NOT_CONVERGED;
+    auto put = [&]() -> int {
+        GKO_CUDA(cudaMemcpyAsync(bs, &hb, sizeof(BicgState), cudaMemcpyHostToDevice, st));
+        return GKO_OK;
+    };
+    auto get = [&]() -> int {
+        GKO_CUDA(cudaMemcpyAsync(&hb, bs, sizeof(BicgState), cudaMemcpyDeviceToHost, st));
+        GKO_CUDA(cudaStreamSynchronize(st));
+        return GKO_OK;
+    };
+    auto restart = [&]() -> int {  // r = b - A x, r^ = r, p = v = 0
+        GKO_CUDA(cudaMemcpyAsync(r, b, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        GKO_TRY(spmv_fmt(A, fmt, x, r, -1.0, 1.0, st));
+        bicg_restart_kernel<<<grid, kRedThreads, 0, st>>>(n, r, rh, p, v, bs, part);
+        GKO_CUDA(cudaGetLastError());
+        return get();
+    };
+    GKO_TRY(put());
+    GKO_TRY(restart());
+    double res = -1.0;
+    if (hb.conv || maxit == 0 || hb.status == GKO_ERR_BREAKDOWN) {
+        GKO_TRY(true_residual(A, fmt, b, x, t, ds, part, bnorm, st, &res));
+        const int st0 = hb.conv ? GKO_OK : hb.status;
+        fill_info(info, 0, 0, res, st0);
+        return st0;
+    }
+
+    GraphHolder gh;
+    GKO_TRY(build_while_graph(&gh, [&](cudaGraphConditionalHandle h, cudaStream_t cs) -> int {
+        bicg_p_kernel<<<grid, kRedThreads, 0, cs>>>(n, p, r, v, bs);
+        GKO_TRY(spmv_fmt(A, fmt, p, v, 1.0, 0.0, cs));
+        bicg_alpha_kernel<<<grid, kRedThreads, 0, cs>>>(n, rh, v, bs, part, h);
+        bicg_s_kernel<<<grid, kRedThreads, 0, cs>>>(n, sv, r, v, bs, part, h);
+        GKO_TRY(spmv_fmt(A, fmt, sv, t, 1.0, 0.0, cs));
+        bicg_omega_kernel<<<grid, kRedThreads, 0, cs>>>(n, t, sv, bs, part, h);
+        bicg_xr_kernel<<<grid, kRedThreads, 0, cs>>>(n, x, r, p, sv, t, rh, bs, part, h);
+        GKO_CUDA(cudaGetLastError());
+        return GKO_OK;
+    }));
+
+    int status = GKO_ERR_NOT_CONVERGED, checks = 0, steps = 0;
+    while (true) {
+        GKO_CUDA(cudaGraphLaunch(gh.exec, st));
+        GKO_TRY(get());
+        steps = hb.iter + (hb.half ? 1 : 0);
+        if (hb.status == GKO_ERR_BREAKDOWN) {
+            status = GKO_ERR_BREAKDOWN;
+            break;
+        }
+        if (hb.conv) {
+            if (hb.half) {
+                bicg_half_kernel<<<grid, kRedThreads, 0, st>>>(n, x, p, bs);
+                GKO_CUDA(cudaGetLastError());
+            }
+            GKO_TRY(true_residual(A, fmt, b, x, t, ds, part, bnorm, st, &res));
+            ++checks;
+            if (res <= tol) {
+                status = GKO_OK;
+                break;
+            }
+            if (checks >= 4 || steps >= maxit) {
+                status = GKO_ERR_NOT_CONVERGED;
+                break;
+            }
+            const int it_done = steps;
+            if (hb.half) {  // restart from the true residual of the half-step iterate
+                GKO_TRY(restart());
+                hb.iter = it_done;
+                hb.half = 0;
+                GKO_TRY(put());
+            } else {  // continue from the recursive residual
+                hb.conv = 0;
+                hb.done = 0;
+                hb.status = GKO_ERR_NOT_CONVERGED;
+                GKO_TRY(put());
+            }
+            res = -1.0;
+            continue;
+        }
+        status = GKO_ERR_NOT_CONVERGED;  // maxit
+        break;
+    }
+    if (res < 0.0) GKO_TRY(true_residual(A, fmt, b, x, t, ds, part, bnorm, st, &res));
+    fill_info(info, steps, 0, res, status);
+    if (status != GKO_OK)
+        set_error(status == GKO_ERR_BREAKDOWN ? "BiCGSTAB breakdown (r^.v, t.t or omega zero, or NaN)"
+                                              : "BiCGSTAB reached maxit");
+    return status;
+}
+
 // ------------------------------------------- mixed precision refinement
 
 // IEEE binary64 -> bfloat16, round to nearest, ties to even, from the bit

@@ -222,6 +222,8 @@ cudaError_t lp_ell_cg1(const gko_matrix* A, bool bf16, const float* r, float* w,
 int lp_ell_grid(const gko_matrix* A);
 int pcg_jacobi_solve(const gko_matrix* A, int fmt, const double* b, double* x, double tol, int maxit,
                      cudaStream_t st, gko_solve_info* info);
+int bicgstab_solve(const gko_matrix* A, int fmt, const double* b, double* x, double tol, int maxit,
+                   cudaStream_t st, gko_solve_info* info);
 int cg1_solve(const gko_matrix* A, int fmt, const double* b, double* x, double tol, int maxit,
               cudaStream_t st, gko_solve_info* info);
 int cg_mixed_solve(gko_matrix* A, int inner, const double* b, double* x, double tol, int maxit_outer,
