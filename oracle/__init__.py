@@ -81,6 +81,7 @@ def _declare(L):
         "orc_cg_single_reduction": (_INT, [_I64, _P, _P, _P, _P, _P, _D, _INT, _P, _P]),
         "orc_pcg_jacobi": (_INT, [_I64, _P, _P, _P, _P, _P, _D, _INT, _P, _P]),
         "orc_bicgstab": (_INT, [_I64, _P, _P, _P, _P, _P, _D, _INT, _P, _P]),
+        "orc_spmm_csr": (None, [_I64, _P, _P, _P, _I64, _P, _I64, _D, _D, _P, _I64]),
         "orc_cg_batched": (_INT, [_I64, _P, _P, _P, _P, _P, _P, _D, _INT, _P, _P, _P]),
         "orc_round_bf16": (_D, [_D, _INT]),
         "orc_round_fp32": (_D, [_D, _INT]),
@@ -117,6 +118,16 @@ def spmv_csr(A, x, alpha=1.0, beta=0.0, y=None):
     out = np.zeros(n) if y is None else np.array(y, dtype=np.float64, copy=True)
     lib().orc_spmv_csr(n, _p(rp), _p(ci), _p(v), _p(x), alpha, beta, _p(out))
     return out
+
+
+def spmm_csr(A, X, alpha=1.0, beta=0.0, Y=None):
+    """Y = alpha A X + beta Y for row-major dense blocks X (n_cols x k)."""
+    n, rp, ci, v = _csr(A)
+    X = _c(X, np.float64)
+    k = X.shape[1]
+    Y = np.zeros((n, k)) if Y is None else np.array(Y, dtype=np.float64, copy=True, order="C")
+    lib().orc_spmm_csr(n, _p(rp), _p(ci), _p(v), k, _p(X), k, alpha, beta, _p(Y), k)
+    return Y
 
 
 def spmv_dot2(A, x, alpha=1.0, beta=0.0, y=None):

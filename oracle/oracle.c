@@ -514,6 +514,32 @@ double orc_true_rel_residual(int64_t n, const int32_t *row_ptr, const int32_t *c
     return res;
 }
 
+/* Multiple right-hand sides: Y = alpha A X + beta Y for dense blocks X
+ * (n_cols x k) and Y (n_rows x k) stored row-major with leading dimensions
+ * ldx, ldy: column c of the block is the product of A with column c of X,
+ * each summed as orc_spmv_csr sums a row (ascending column order, separate
+ * multiply and add).  beta == 0: Y is not read. */
+void orc_spmm_csr(int64_t n, const int32_t *row_ptr, const int32_t *col, const double *val,
+                  int64_t k, const double *x, int64_t ldx, double alpha, double beta, double *y,
+                  int64_t ldy)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        for (int64_t c = 0; c < k; ++c) {
+            double s = 0.0;
+            for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+                double t = val[e] * x[(int64_t)col[e] * ldx + c];
+                s = s + t;
+            }
+            double out = alpha * s;
+            if (beta != 0.0) {
+                double u = beta * y[i * ldy + c];
+                out = out + u;
+            }
+            y[i * ldy + c] = out;
+        }
+    }
+}
+
 /* ------------------------------------------------------------------- CG */
 
 /* Conjugate gradients (Hestenes and Stiefel 1952), the Krylov solver of

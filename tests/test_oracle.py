@@ -514,6 +514,25 @@ def test_bicgstab_special_cases(orc):
     assert st == orc.BREAKDOWN
 
 
+def test_spmm_columns_are_spmvs_and_identity_gives_dense(orc):
+    """SpMM pins: with X = the identity the block is the dense matrix
+    (brute force); every column equals the SpMV of that column (integer
+    values: exact); alpha/beta as in SpMV."""
+    A = syn.random_csr(37, 23, 5, seed=51, empty_frac=0.2)
+    D = dense(A)
+    Y = orc.spmm_csr(A, np.eye(23))
+    assert np.array_equal(Y, D)
+    rng = np.random.default_rng(52)
+    Ai = dict(A)
+    Ai["val"] = rng.integers(-5, 6, size=len(A["val"])).astype(np.float64)
+    X = rng.integers(-5, 6, size=(23, 6)).astype(np.float64)
+    Y0 = rng.integers(-5, 6, size=(37, 6)).astype(np.float64)
+    Y = orc.spmm_csr(Ai, X, 2.0, -1.0, Y0)
+    assert np.array_equal(Y, 2.0 * dense(Ai) @ X - Y0)
+    for c in range(6):
+        assert np.array_equal(Y[:, c], orc.spmv_csr(Ai, X[:, c], 2.0, -1.0, Y0[:, c]))
+
+
 def test_batched_cg(orc):
     B = syn.batched_spd(12, seed=8)
     x, st, it, res = orc.cg_batched(B, B["rhs"], tol=1e-10)
