@@ -436,6 +436,28 @@ def run_extras(gko, torch, dev, st):
     res["speedup_fp32_vs_best_fp64"] = round(best64 / res["fp32"]["s"], 3)
     res["speedup_bf16_vs_best_fp64"] = round(best64 / res["bf16"]["s"], 3)
     out["cg_diffusion7_160"] = res
+    # multi-RHS SpMM (k = 8) on the 27-point stencil against 8 SpMVs
+    S = load_workload("stencil27_128")
+    M = gko.Matrix(S, stream=st)
+    k = 8
+    Xb = torch.rand((S["n_cols"], k), dtype=torch.float64, device=dev)
+    Yb = torch.empty((S["n_rows"], k), dtype=torch.float64, device=dev)
+    xs1 = [Xb[:, c].contiguous() for c in range(k)]
+    y1 = torch.empty(S["n_rows"], dtype=torch.float64, device=dev)
+    for _ in range(3):
+        M.spmm(Xb, Yb, stream=st)
+    ts, t8 = [], []
+    for _ in range(5):
+        t, _r = _time_call(torch, lambda: M.spmm(Xb, Yb, stream=st))
+        ts.append(t)
+        t, _r = _time_call(torch, lambda: [M.spmv(xs1[c], y1, stream=st) for c in range(k)])
+        t8.append(t)
+    nnz = len(S["val"])
+    t_mm, t_mv = statistics.median(ts), statistics.median(t8)
+    out["spmm_stencil27_k8"] = {"s": round(t_mm, 6), "eight_spmv_s": round(t_mv, 6),
+                                "speedup_vs_spmv": round(t_mv / t_mm, 3),
+                                "fp64_tfma_s": round(nnz * k / t_mm / 1e12, 4),
+                                "note": "bound by the FP64 pipe (one FMA per entry and column; ~0.6 TFMA/s measured)"}
     # BiCGSTAB on a nonsymmetric convection-diffusion operator (1024^2 grid)
     C = syn.convdiff2d(1024, 0.8)
     n = C["n_rows"]

@@ -193,6 +193,16 @@ int gko_spmv_config(int fmt, int config, const gko_matrix* A, const double* x, d
 int gko_spmv_host(int fmt, const gko_matrix* A, const double* x_host, double* y_host, double alpha,
                   double beta, void* stream);
 
+/* Several right-hand sides at once (Sec. 6.1's product applied to a block
+ * of k vectors): Y = alpha * A * X + beta * Y with X (n_cols x k) and Y
+ * (n_rows x k) dense, row-major (element (i, c) at i*ld + c), leading
+ * dimensions ldx, ldy >= max(k, 1); device pointers, caller-owned, not
+ * aliased.  Reads the CSR format (must be materialised).  Each Y column is
+ * the product with the same X column, within the accuracy stated for
+ * gko_spmv; beta == 0: Y is not read.  k = 0 does nothing.  Asynchronous. */
+int gko_spmm(const gko_matrix* A, int64_t k, const double* x, int64_t ldx, double* y, int64_t ldy, double alpha,
+             double beta, void* stream);
+
 /* COO SpMV that allocates no memory at all.  The paper has no counterpart:
  * this entry point exists for callers that cannot call cudaMalloc (or any
  * allocator) while they run -- code captured into CUDA graphs or replayed

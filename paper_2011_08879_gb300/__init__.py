@@ -135,6 +135,21 @@ class Matrix:
             binding.gko_spmv(_fmt(fmt), self.handle, xp, yp, alpha, beta, _stream(stream))
         return y
 
+    def spmm(self, X, Y, alpha=1.0, beta=0.0, stream=None):
+        """Y = alpha A X + beta Y; X (n_cols x k), Y (n_rows x k): row-major
+        (C-contiguous) float64 CUDA tensors."""
+        import torch
+        for t, rows, name in ((X, self.n_cols, "X"), (Y, self.n_rows, "Y")):
+            if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.dim() == 2
+                    and t.is_contiguous() and t.shape[0] == rows):
+                raise TypeError("%s must be a contiguous float64 CUDA tensor with %d rows" % (name, rows))
+        if X.shape[1] != Y.shape[1]:
+            raise ValueError("X and Y need the same number of columns")
+        k = X.shape[1]
+        binding.gko_spmm(self.handle, k, X.data_ptr(), max(k, 1), Y.data_ptr(), max(k, 1), alpha, beta,
+                         _stream(stream))
+        return Y
+
     def spmv_host(self, x, y, alpha=1.0, beta=0.0, fmt="csr", stream=None):
         """x, y: host float64 arrays (numpy or pinned CPU tensors)."""
         def ptr(a):

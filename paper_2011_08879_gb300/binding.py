@@ -62,6 +62,7 @@ _SIGS = {
     "gko_cg_single_reduction": (_INT, [_P, _INT, _P, _P, _D, _INT, _P, C.POINTER(SolveInfo)]),
     "gko_pcg_jacobi": (_INT, [_P, _INT, _P, _P, _D, _INT, _P, C.POINTER(SolveInfo)]),
     "gko_bicgstab": (_INT, [_P, _INT, _P, _P, _D, _INT, _P, C.POINTER(SolveInfo)]),
+    "gko_spmm": (_INT, [_P, _I64, _P, _I64, _P, _I64, _D, _D, _P]),
     "gko_cg_mixed": (_INT, [_P, _INT, _P, _P, _D, _INT, _D, _INT, _P, C.POINTER(SolveInfo)]),
     "gko_batch_create": (_INT, [_I64, _P, _P, _P, _P, _INT, _P, C.POINTER(_P)]),
     "gko_batch_destroy": (_INT, [_P]),
@@ -206,6 +207,11 @@ def gko_bicgstab(A, fmt, b, x, tol, maxit, stream=0, raise_on=()) -> SolveInfo:
     _check(s, "gko_bicgstab", allow)
     info.status = s
     return info
+
+
+def gko_spmm(A, k, x, ldx, y, ldy, alpha=1.0, beta=0.0, stream=0) -> None:
+    """Y = alpha A X + beta Y (row-major blocks; device pointers)."""
+    _check(lib.gko_spmm(A, k, x, ldx, y, ldy, alpha, beta, stream), "gko_spmm")
 
 
 def gko_cg_mixed(A, inner_dtype, b, x, tol, maxit_outer, inner_tol, inner_maxit, stream=0) -> SolveInfo:

@@ -322,6 +322,18 @@ int gko_spmv_config(int fmt, int config, const gko_matrix* A, const double* x, d
     return spmv_dispatch(fmt, config, A, x, y, alpha, beta, static_cast<cudaStream_t>(stream));
 }
 
+int gko_spmm(const gko_matrix* A, int64_t k, const double* x, int64_t ldx, double* y, int64_t ldy, double alpha,
+             double beta, void* stream)
+{
+    if (!A) return fail(GKO_ERR_INVALID_ARG, "NULL handle");
+    if (!A->has[GKO_FMT_CSR]) return fail(GKO_ERR_FORMAT_UNAVAILABLE, "SpMM reads the CSR format");
+    if (k < 0 || ldx < k || ldy < k || ldx < 1 || ldy < 1)
+        return fail(GKO_ERR_INVALID_ARG, "k >= 0 and leading dimensions >= max(k, 1) required");
+    if (k > 0 && ((A->n_cols > 0 && !x) || (A->n_rows > 0 && !y))) return fail(GKO_ERR_INVALID_ARG, "NULL block");
+    GKO_TRY(check_device(A));
+    return spmm_csr(A, k, x, ldx, y, ldy, alpha, beta, static_cast<cudaStream_t>(stream));
+}
+
 int gko_spmv_host(int fmt, const gko_matrix* A, const double* x_host, double* y_host, double alpha, double beta,
                   void* stream)
 {
