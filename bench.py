@@ -79,19 +79,10 @@ def spmv_bytes(fmt, info, n, m, nnz, s_v=8):
     raise KeyError(fmt)
 
 
-CSR_BIN_EDGES = (8, 20, 48, 128, 512)  # row-length bins of the binned CSR kernel
-
-
 def csr_default_launches(A):
-    """Launches of the default CSR SpMV: one kernel for rows of close length
-    (max <= 2 mean + 16, max <= 128), else one per non-empty length bin."""
-    L = np.diff(np.asarray(A["row_ptr"], dtype=np.int64))
-    if len(L) == 0 or L.sum() == 0:
-        return 1
-    if L.max() <= 128 and L.max() <= 2.0 * L.mean() + 16.0:
-        return 1
-    bins = np.searchsorted(np.array(CSR_BIN_EDGES), L, side="left")
-    return int(len(np.unique(bins)))
+    """Launches of the default CSR SpMV: one kernel (uniform rows: subwarp
+    or row-block kernel; skewed rows: the one-launch binned kernel)."""
+    return 1
 
 
 def kernel_launches(fmt, nnz_or_coo, tile=3840, csr_launches=1):

@@ -811,6 +811,8 @@ void free_format(gko_matrix* A, int fmt)
             dev_free(A->csr.val);
             dev_free(A->csr.thr_row);
             dev_free(A->csr.bin_rows);
+            dev_free(A->csr.bin_tasks);
+            A->csr.n_bin_tasks = 0;
             seg_free(&A->csr.seg);
             break;
         case GKO_FMT_COO:

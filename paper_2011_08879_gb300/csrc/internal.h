@@ -81,6 +81,8 @@ struct CsrPart {
     int32_t band = -1;  // max |i - j| (computed at analysis), -1 unknown
     int32_t* bin_rows = nullptr;  // rows grouped by length bin (binned kernel)
     int64_t bin_off[7] = {0, 0, 0, 0, 0, 0, 0};
+    int4* bin_tasks = nullptr;    // (start, count, bin, 0) chunks of bin_rows in row order
+    int64_t n_bin_tasks = 0;
 };
 constexpr int kCsrBins = 6;
 

@@ -7,6 +7,8 @@
 //    it (the default for skewed rows);
 //  * banded kernel: the x window of a row block staged in shared memory.
 #include <algorithm>
+#include <utility>
+#include <vector>
 
 #include "common.cuh"
 #include "internal.h"
@@ -81,8 +83,50 @@ __global__ void bin_scatter_kernel(int64_t n_rows, const int32_t* __restrict__ r
     if (r < n_rows && csr_bin(row_ptr[r + 1] - row_ptr[r]) == b) out[off[r]] = static_cast<int32_t>(r);
 }
 
-// Build bin_rows (the rows grouped by bin, ascending inside each bin) and
-// the bin offsets.  Synchronises the stream (bin sizes are read back).
+// Rows per task of the one-launch binned kernel, by bin: four passes of a
+// 256-thread CTA over subwarps of 1, 2, 4, 8, 32 lanes; one long row per
+// task in the last bin.
+constexpr int kBinSW[kCsrBins] = {1, 2, 4, 8, 32, 0};
+constexpr int kTaskPasses = 4;
+static int bin_task_rows(int b) { return kBinSW[b] ? 256 / kBinSW[b] * kTaskPasses : 1; }
+
+// Tasks of the one-launch binned kernel: chunks of bin_rows (a bin's rows,
+// bin_task_rows(b) at a time) ordered by their first row, so the CTAs that
+// run together work on neighbouring rows whatever their bins (their
+// matrix sectors and x stay in L2 between them).  One int4 per task:
+// (start in bin_rows, row count, bin, 0).
+static int csr_build_bin_tasks(gko_matrix* A, cudaStream_t st)
+{
+    CsrPart& c = A->csr;
+    dev_free(c.bin_tasks);
+    c.n_bin_tasks = 0;
+    const int64_t n = A->n_rows;
+    if (n == 0) return GKO_OK;
+    std::vector<int32_t> rows(static_cast<size_t>(n));
+    GKO_CUDA(cudaMemcpyAsync(rows.data(), c.bin_rows, n * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    GKO_CUDA(cudaStreamSynchronize(st));
+    std::vector<std::pair<int32_t, int4>> t;
+    for (int b = 0; b < kCsrBins; ++b) {
+        const int64_t per = bin_task_rows(b);
+        for (int64_t q = c.bin_off[b]; q < c.bin_off[b + 1]; q += per) {
+            const int64_t cnt = std::min<int64_t>(per, c.bin_off[b + 1] - q);
+            t.push_back({rows[q], make_int4(static_cast<int>(q), static_cast<int>(cnt), b, 0)});
+        }
+    }
+    std::stable_sort(t.begin(), t.end(), [](const std::pair<int32_t, int4>& a, const std::pair<int32_t, int4>& b) {
+        return a.first < b.first;
+    });
+    std::vector<int4> h(t.size());
+    for (size_t i = 0; i < t.size(); ++i) h[i] = t[i].second;
+    GKO_TRY(dev_alloc(&c.bin_tasks, static_cast<int64_t>(h.size())));
+    GKO_CUDA(cudaMemcpyAsync(c.bin_tasks, h.data(), h.size() * sizeof(int4), cudaMemcpyHostToDevice, st));
+    GKO_CUDA(cudaStreamSynchronize(st));
+    c.n_bin_tasks = static_cast<int64_t>(h.size());
+    return GKO_OK;
+}
+
+// Build bin_rows (the rows grouped by bin, ascending inside each bin), the
+// bin offsets and the task list.  Synchronises the stream.
 static int csr_build_bins(gko_matrix* A, cudaStream_t st)
 {
     CsrPart& c = A->csr;
@@ -115,6 +159,7 @@ static int csr_build_bins(gko_matrix* A, cudaStream_t st)
     cudaFree(flag);
     cudaFree(off);
     if (s == GKO_OK) GKO_CUDA(cudaGetLastError());
+    if (s == GKO_OK) s = csr_build_bin_tasks(A, st);
     return s;
 }
 
@@ -272,26 +317,25 @@ __device__ __forceinline__ void fma4(int32_t k, int32_t k1, const int32_t* __res
     if (c[3] >= 0) a1 = fma(v[3], xv[3], a1);
 }
 
-// The subwarp-per-row kernel over a list of rows (one bin of the binned
-// kernel): subwarp s of the warp takes rows[base + s], its lanes step
-// through the row four entries at a time (fma4).  On matrices whose columns
-// are spread at random (power-law rows over 2M columns) every gather is a
-// separate 32-byte L2 sector; GB300 serves such gathers at ~270 G/s (one
-// per SM clock), which bounds those products, not HBM bandwidth.
+// One CTA per task: the task's rows of one bin, by subwarps of SW lanes
+// (warp w of the CTA takes row groups w, w + 8, ...), four entries per lane
+// in flight (fma4).  On matrices whose columns are spread at random
+// (power-law rows over 2M columns) every gather is a separate 32-byte L2
+// sector; GB300 serves such gathers at ~270 G/s (one per SM clock), which
+// bounds those products, not HBM bandwidth.
 template <int SW, bool kAlpha, bool kBeta>
-__global__ void __launch_bounds__(256)
-    csr_list_kernel(int64_t count, const int32_t* __restrict__ rows, const int32_t* __restrict__ row_ptr,
-                    const int32_t* __restrict__ col, const double* __restrict__ val, const double* __restrict__ x,
-                    double* __restrict__ y, double alpha, double beta)
+__device__ __forceinline__ void task_rows(const int32_t* __restrict__ rows, int count,
+                                          const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                                          const double* __restrict__ val, const double* __restrict__ x,
+                                          double* __restrict__ y, double alpha, double beta)
 {
     using G = subwarp<SW>;
     constexpr int kRowsPerWarp = kWarp / SW;
     const int lane = G::rank();
     const int sub = (threadIdx.x % kWarp) / SW;
-    const int64_t warp = (blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x) / kWarp;
-    const int64_t n_warps = static_cast<int64_t>(gridDim.x) * blockDim.x / kWarp;
-    for (int64_t base = warp * kRowsPerWarp; base < count; base += n_warps * kRowsPerWarp) {
-        const int64_t q = base + sub;
+    const int w = threadIdx.x / kWarp;
+    for (int base = w * kRowsPerWarp; base < count; base += (256 / kWarp) * kRowsPerWarp) {
+        const int q = base + sub;
         const int32_t r = q < count ? rows[q] : 0;
         double a0 = 0.0, a1 = 0.0;
         if (q < count) {
@@ -303,84 +347,66 @@ __global__ void __launch_bounds__(256)
     }
 }
 
-// One CTA of 256 threads per long row (rows[i] for i = block, block + grid,
-// ...): entries four per thread at a time (fma4), two FMA chains, then
-// warp sums and the 8 warp totals added in warp order (deterministic).
 template <bool kAlpha, bool kBeta>
 __global__ void __launch_bounds__(256)
-    csr_list_block_kernel(int64_t count, const int32_t* __restrict__ rows, const int32_t* __restrict__ row_ptr,
-                          const int32_t* __restrict__ col, const double* __restrict__ val,
-                          const double* __restrict__ x, double* __restrict__ y, double alpha, double beta)
+    csr_binned_kernel(const int4* __restrict__ tasks, const int32_t* __restrict__ bin_rows,
+                      const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                      const double* __restrict__ val, const double* __restrict__ x, double* __restrict__ y,
+                      double alpha, double beta)
 {
     __shared__ double sh[8];
-    for (int64_t q = blockIdx.x; q < count; q += gridDim.x) {
-        const int32_t r = rows[q];
-        const int32_t k0 = row_ptr[r], k1 = row_ptr[r + 1];
-        double a0 = 0.0, a1 = 0.0;
-        for (int32_t k = k0 + static_cast<int32_t>(threadIdx.x); k < k1; k += 1024)
-            fma4<256>(k, k1, col, val, x, a0, a1);
-        const double t = subwarp<32>::reduce_sum(a0 + a1);
-        if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = t;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double tot = 0.0;
-            for (int w = 0; w < 8; ++w) tot += sh[w];
-            seg_store<kAlpha, kBeta>(y, r, tot, alpha, beta);
+    const int4 t = tasks[blockIdx.x];
+    const int32_t* rows = bin_rows + t.x;
+    switch (t.z) {
+        case 0: task_rows<1, kAlpha, kBeta>(rows, t.y, row_ptr, col, val, x, y, alpha, beta); break;
+        case 1: task_rows<2, kAlpha, kBeta>(rows, t.y, row_ptr, col, val, x, y, alpha, beta); break;
+        case 2: task_rows<4, kAlpha, kBeta>(rows, t.y, row_ptr, col, val, x, y, alpha, beta); break;
+        case 3: task_rows<8, kAlpha, kBeta>(rows, t.y, row_ptr, col, val, x, y, alpha, beta); break;
+        case 4: task_rows<32, kAlpha, kBeta>(rows, t.y, row_ptr, col, val, x, y, alpha, beta); break;
+        default: {  // one long row, the whole CTA
+            const int32_t r = rows[0];
+            const int32_t k0 = row_ptr[r], k1 = row_ptr[r + 1];
+            double a0 = 0.0, a1 = 0.0;
+            for (int32_t k = k0 + static_cast<int32_t>(threadIdx.x); k < k1; k += 1024)
+                fma4<256>(k, k1, col, val, x, a0, a1);
+            const double s = subwarp<32>::reduce_sum(a0 + a1);
+            if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                double tot = 0.0;
+                for (int w = 0; w < 8; ++w) tot += sh[w];
+                seg_store<kAlpha, kBeta>(y, r, tot, alpha, beta);
+            }
         }
-        __syncthreads();
     }
-}
-
-template <int SW, bool kAlpha, bool kBeta>
-static void launch_list(int64_t count, const int32_t* rows, const gko_matrix* A, const double* x, double* y,
-                        double alpha, double beta, cudaStream_t st)
-{
-    if (count <= 0) return;
-    const CsrPart& c = A->csr;
-    if (SW == 0) {
-        const int grid = static_cast<int>(std::min<int64_t>(count, 152LL * 8));
-        csr_list_block_kernel<kAlpha, kBeta><<<grid, 256, 0, st>>>(count, rows, c.row_ptr, c.col, c.val, x, y, alpha,
-                                                                  beta);
-        return;
-    }
-    constexpr int kSW = SW > 0 ? SW : 1;
-    const int64_t rows_per_block = 256 / kSW;
-    const int grid = static_cast<int>(std::min<int64_t>((count + rows_per_block - 1) / rows_per_block, 152LL * 16));
-    csr_list_kernel<kSW, kAlpha, kBeta><<<grid, 256, 0, st>>>(count, rows, c.row_ptr, c.col, c.val, x, y, alpha,
-                                                              beta);
 }
 
 // Binned CSR SpMV: every row is computed once by the kernel of its length
 // bin (1, 2, 4, 8 or 32 lanes per row, or a whole CTA for rows longer than
 // 512), so rows of any length mix take full occupancy, each entry one FMA,
-// and no partial sums cross threads except the lanes of one row.
-template <bool kAlpha, bool kBeta>
-static void launch_binned_ab(const gko_matrix* A, const double* x, double* y, double alpha, double beta,
-                             cudaStream_t st)
-{
-    const CsrPart& c = A->csr;
-    auto cnt = [&](int b) { return c.bin_off[b + 1] - c.bin_off[b]; };
-    auto rows = [&](int b) { return c.bin_rows + c.bin_off[b]; };
-    launch_list<1, kAlpha, kBeta>(cnt(0), rows(0), A, x, y, alpha, beta, st);
-    launch_list<2, kAlpha, kBeta>(cnt(1), rows(1), A, x, y, alpha, beta, st);
-    launch_list<4, kAlpha, kBeta>(cnt(2), rows(2), A, x, y, alpha, beta, st);
-    launch_list<8, kAlpha, kBeta>(cnt(3), rows(3), A, x, y, alpha, beta, st);
-    launch_list<32, kAlpha, kBeta>(cnt(4), rows(4), A, x, y, alpha, beta, st);
-    launch_list<0, kAlpha, kBeta>(cnt(5), rows(5), A, x, y, alpha, beta, st);
-}
-
+// and no partial sums cross threads except the lanes of one row.  All bins
+// go in one launch (csr_binned_kernel over the task list, in row order).
 static void launch_binned(const gko_matrix* A, const double* x, double* y, double alpha, double beta,
                           cudaStream_t st)
 {
+    const CsrPart& c = A->csr;
     const bool a = alpha != 1.0, b = beta != 0.0;
-    if (a && b)
-        launch_binned_ab<true, true>(A, x, y, alpha, beta, st);
-    else if (a)
-        launch_binned_ab<true, false>(A, x, y, alpha, beta, st);
-    else if (b)
-        launch_binned_ab<false, true>(A, x, y, alpha, beta, st);
-    else
-        launch_binned_ab<false, false>(A, x, y, alpha, beta, st);
+    if (c.n_bin_tasks > 0) {  // tasks <= rows < 2^31
+        const unsigned g = static_cast<unsigned>(c.n_bin_tasks);
+#define GKO_BT(KA, KB) \
+    csr_binned_kernel<KA, KB><<<g, 256, 0, st>>>(c.bin_tasks, c.bin_rows, c.row_ptr, c.col, c.val, x, y, alpha, beta)
+        if (a && b)
+            GKO_BT(true, true);
+        else if (a)
+            GKO_BT(true, false);
+        else if (b)
+            GKO_BT(false, true);
+        else
+            GKO_BT(false, false);
+#undef GKO_BT
+        return;
+    }
+    scale_vector(A->n_rows, y, beta, st);  // no rows (n = 0): only the beta scaling
 }
 
 // --------------------------------------------------- load-balanced launch
@@ -435,8 +461,8 @@ int launch_seg(int64_t n_rows, int64_t nnz, const int32_t* row_ptr, const int32_
 // 73 % of HBM bandwidth vs 61 % for the staged row blocks), staged row blocks
 // up to 20 (random banded, 16 per row: 69 %), four lanes per row beyond
 // (27-point 128^3: 69 % vs 58 %); skewed rows take the row-length bins
-// (power-law 2M rows, mean 20, max 20k: 327 us vs 439 us for the equal-nnz
-// split; random gathers of x bound that matrix, see csr_list_kernel).
+// (power-law 2M rows, mean 20, max 20k: 229 us vs 439 us for the equal-nnz
+// split; random gathers of x bound that matrix, see task_rows).
 int default_csr_config(const gko_matrix* A)
 {
     if (!rowblock_preferred(A)) return GKO_CFG_CSR_BINNED;
