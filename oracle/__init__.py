@@ -82,6 +82,7 @@ def _declare(L):
         "orc_pcg_jacobi": (_INT, [_I64, _P, _P, _P, _P, _P, _D, _INT, _P, _P]),
         "orc_bicgstab": (_INT, [_I64, _P, _P, _P, _P, _P, _D, _INT, _P, _P]),
         "orc_spmm_csr": (None, [_I64, _P, _P, _P, _I64, _P, _I64, _D, _D, _P, _I64]),
+        "orc_gmres": (_INT, [_I64, _P, _P, _P, _P, _P, _D, _INT, _INT, _P, _P]),
         "orc_cg_batched": (_INT, [_I64, _P, _P, _P, _P, _P, _P, _D, _INT, _P, _P, _P]),
         "orc_round_bf16": (_D, [_D, _INT]),
         "orc_round_fp32": (_D, [_D, _INT]),
@@ -330,6 +331,17 @@ def bicgstab(A, b, x0=None, tol=1e-10, maxit=10000):
     x = np.zeros(n) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
     it, res = C.c_int(0), C.c_double(0.0)
     st = lib().orc_bicgstab(n, _p(rp), _p(ci), _p(v), _p(b), _p(x), tol, maxit, C.byref(it), C.byref(res))
+    return x, int(st), it.value, res.value
+
+
+def gmres(A, b, x0=None, tol=1e-10, restart=30, maxit=10000):
+    """Restarted GMRES(restart).  Returns (x, status, Arnoldi steps, true
+    rel. residual)."""
+    n, rp, ci, v = _csr(A)
+    b = _c(b, np.float64)
+    x = np.zeros(n) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
+    it, res = C.c_int(0), C.c_double(0.0)
+    st = lib().orc_gmres(n, _p(rp), _p(ci), _p(v), _p(b), _p(x), tol, restart, maxit, C.byref(it), C.byref(res))
     return x, int(st), it.value, res.value
 
 

@@ -21,7 +21,8 @@
  * (Bell and Garland, SC'09), SELL-P (Anzt, Tomov and Dongarra, 2014);
  * CG is the method of Hestenes and Stiefel (1952), also in the
  * single-reduction form of Chronopoulos and Gear (1989) and preconditioned by
- * the diagonal (Jacobi); BiCGSTAB is van der Vorst's (1992); Dot2 is Algorithm 5.3 of
+ * the diagonal (Jacobi); BiCGSTAB is van der Vorst's (1992), GMRES Saad and
+ * Schultz's (1986); Dot2 is Algorithm 5.3 of
  * Ogita, Rump and Oishi, "Accurate sum and dot product" (SISC 2005).
  */
 #include <math.h>
@@ -946,6 +947,126 @@ int orc_bicgstab(int64_t n, const int32_t *row_ptr, const int32_t *col, const do
     free(v);
     free(sv);
     free(t);
+    return status;
+}
+
+/* Restarted GMRES(m) (Saad and Schultz, SISC 7, 1986) for general square
+ * A: each cycle builds the Arnoldi basis v_1 = r/||r||, v_{j+1} from A v_j
+ * orthogonalised against v_1..v_j by modified Gram-Schmidt, reduces the
+ * Hessenberg matrix to triangular form by Givens rotations (whose last
+ * right-hand side entry is the residual norm of the least-squares
+ * minimiser), stops the cycle at j = m or when that norm is <= tol ||b||,
+ * solves the triangular system and updates x; then r = b - A x (the true
+ * residual) starts the next cycle.  Converged when the true residual
+ * confirms; *iters counts Arnoldi steps (products with A after the first
+ * residual of each cycle).  A zero subdiagonal before convergence (lucky
+ * breakdown) ends the cycle with the exact solution of the subspace. */
+int orc_gmres(int64_t n, const int32_t *row_ptr, const int32_t *col, const double *val,
+              const double *b, double *x, double tol, int m, int maxit, int *iters,
+              double *rel_res)
+{
+    double nb = nrm2(n, b);
+    *iters = 0;
+    if (nb == 0.0) {
+        for (int64_t i = 0; i < n; ++i)
+            x[i] = 0.0;
+        *rel_res = 0.0;
+        return ORC_OK;
+    }
+    if (m < 1)
+        m = 1;
+    size_t nn = (size_t)(n > 0 ? n : 1);
+    double *V = (double *)malloc(nn * (size_t)(m + 1) * sizeof(double));
+    double *r = (double *)malloc(nn * sizeof(double)), *w = (double *)malloc(nn * sizeof(double));
+    double *H = (double *)calloc((size_t)(m + 1) * (size_t)m, sizeof(double));
+    double *cs = (double *)malloc((size_t)m * sizeof(double)), *sn = (double *)malloc((size_t)m * sizeof(double));
+    double *g = (double *)malloc((size_t)(m + 1) * sizeof(double)), *yv = (double *)malloc((size_t)m * sizeof(double));
+    int status = ORC_NOT_CONVERGED, total = 0;
+    while (1) {
+        for (int64_t i = 0; i < n; ++i)
+            r[i] = b[i];
+        orc_spmv_csr(n, row_ptr, col, val, x, -1.0, 1.0, r);
+        double beta = nrm2(n, r);
+        if (!(beta == beta)) {
+            status = ORC_BREAKDOWN;
+            break;
+        }
+        if (beta <= tol * nb) {
+            status = ORC_OK;
+            break;
+        }
+        if (total >= maxit)
+            break;
+        for (int64_t i = 0; i < n; ++i)
+            V[i] = r[i] / beta;
+        for (int k = 0; k <= m; ++k)
+            g[k] = 0.0;
+        g[0] = beta;
+        int j = 0;
+        for (; j < m && total < maxit; ++j) {
+            orc_spmv_csr(n, row_ptr, col, val, V + (size_t)j * nn, 1.0, 0.0, w);
+            total += 1;
+            for (int i = 0; i <= j; ++i) { /* modified Gram-Schmidt */
+                double h = orc_dot(n, w, V + (size_t)i * nn);
+                H[(size_t)i * m + j] = h;
+                for (int64_t q = 0; q < n; ++q) {
+                    double t = h * V[(size_t)i * nn + q];
+                    w[q] = w[q] - t;
+                }
+            }
+            double hn = nrm2(n, w);
+            H[(size_t)(j + 1) * m + j] = hn;
+            if (hn > 0.0)
+                for (int64_t q = 0; q < n; ++q)
+                    V[(size_t)(j + 1) * nn + q] = w[q] / hn;
+            for (int i = 0; i < j; ++i) { /* earlier rotations on the new column */
+                double a = H[(size_t)i * m + j], c = H[(size_t)(i + 1) * m + j];
+                H[(size_t)i * m + j] = cs[i] * a + sn[i] * c;
+                H[(size_t)(i + 1) * m + j] = -sn[i] * a + cs[i] * c;
+            }
+            double a = H[(size_t)j * m + j], c = H[(size_t)(j + 1) * m + j];
+            double d = sqrt(a * a + c * c);
+            if (!(d > 0.0)) {
+                status = ORC_BREAKDOWN;
+                break;
+            }
+            cs[j] = a / d;
+            sn[j] = c / d;
+            H[(size_t)j * m + j] = d;
+            H[(size_t)(j + 1) * m + j] = 0.0;
+            g[j + 1] = -sn[j] * g[j];
+            g[j] = cs[j] * g[j];
+            if (fabs(g[j + 1]) <= tol * nb || !(hn > 0.0)) {
+                j += 1;
+                break;
+            }
+        }
+        if (status == ORC_BREAKDOWN)
+            break;
+        for (int i = j - 1; i >= 0; --i) { /* back substitution */
+            double s = g[i];
+            for (int k = i + 1; k < j; ++k) {
+                double t = H[(size_t)i * m + k] * yv[k];
+                s = s - t;
+            }
+            yv[i] = s / H[(size_t)i * m + i];
+        }
+        for (int i = 0; i < j; ++i)
+            for (int64_t q = 0; q < n; ++q) {
+                double t = yv[i] * V[(size_t)i * nn + q];
+                x[q] = x[q] + t;
+            }
+    }
+    *iters = total;
+    *rel_res = orc_true_rel_residual(n, row_ptr, col, val, b, x);
+    free(V);
+    free(r);
+    free(w);
+    free(H);
+    free(cs);
+    free(sn);
+    free(g);
+    free(yv);
     return status;
 }
 

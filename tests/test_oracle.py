@@ -533,6 +533,62 @@ def test_spmm_columns_are_spmvs_and_identity_gives_dense(orc):
         assert np.array_equal(Y[:, c], orc.spmv_csr(Ai, X[:, c], 2.0, -1.0, Y0[:, c]))
 
 
+def test_gmres_finite_termination(orc):
+    """m distinct eigenvalues (the 3-eigenvalue nonsymmetric block matrix of
+    the BiCGSTAB pin): GMRES without restart solves in at most 3 steps."""
+    blocks = [((1.0, 0.7), (0.0, 2.0)), ((2.0, 0.3), (0.0, 3.0)), ((3.0, -0.5), (0.0, 1.0))]
+    nb = 30
+    rp, ci, va = [0], [], []
+    for k in range(nb):
+        (a, b_), (_, c) = blocks[k % 3]
+        r0 = 2 * k
+        ci += [r0, r0 + 1]; va += [a, b_]; rp.append(len(ci))
+        ci += [r0 + 1]; va += [c]; rp.append(len(ci))
+    A = dict(n_rows=2 * nb, n_cols=2 * nb, row_ptr=np.array(rp, np.int32), col_idx=np.array(ci, np.int32),
+             val=np.array(va))
+    b = syn.vector(2 * nb, 34)
+    x, st, it, res = orc.gmres(A, b, tol=1e-12, restart=50)
+    assert st == orc.OK and it <= 3, (st, it)
+
+
+def test_gmres_minimal_residual_below_cg(orc):
+    """GMRES minimises ||b - A x|| over the Krylov space that CG's iterate
+    also lies in: after k steps (no restart, x0 = 0) its true residual is no
+    larger than CG's on an SPD matrix."""
+    A = syn.diffusion7(8, 1.0, seed=5)
+    n = A["n_rows"]
+    b = syn.vector(n, 35)
+    for k in (1, 2, 5, 10, 20):
+        _, _, _, rg = orc.gmres(A, b, tol=1e-300, restart=100, maxit=k)
+        _, _, _, rc = orc.cg(A, b, tol=1e-300, maxit=k)
+        assert rg <= rc * (1 + 1e-10), (k, rg, rc)
+
+
+def test_gmres_matches_dense_and_restarts(orc):
+    A = syn.convdiff2d(24, 0.8)
+    n = A["n_rows"]
+    xt = syn.vector(n, 36)
+    b = orc.spmv_csr(A, xt)
+    x, st, it, res = orc.gmres(A, b, tol=1e-11, restart=40)
+    assert st == orc.OK and res <= 1e-11
+    assert np.allclose(x, np.linalg.solve(dense(A), b), rtol=1e-8, atol=1e-10)
+    # a shorter restart needs at least as many steps and still converges
+    x2, st2, it2, res2 = orc.gmres(A, b, tol=1e-11, restart=10)
+    assert st2 == orc.OK and it2 >= it
+
+
+def test_gmres_special_cases(orc):
+    A = syn.convdiff2d(8, 0.5)
+    n = A["n_rows"]
+    x, st, it, res = orc.gmres(A, np.zeros(n), x0=np.ones(n))
+    assert st == orc.OK and it == 0 and np.all(x == 0)
+    b = orc.spmv_csr(A, syn.vector(n, 2))
+    x, st, it, res = orc.gmres(A, b, maxit=3)
+    assert st == orc.NOT_CONVERGED and it == 3
+    x, st, it, res = orc.gmres(A, b, x0=syn.vector(n, 2))
+    assert st == orc.OK and it == 0
+
+
 def test_batched_cg(orc):
     B = syn.batched_spd(12, seed=8)
     x, st, it, res = orc.cg_batched(B, B["rhs"], tol=1e-10)
