@@ -465,6 +465,11 @@ def run_extras(gko, torch, dev, st):
         res[fmt] = {"s": round(t, 4), "steps": info.iterations, "rel_residual": info.rel_residual,
                     "status": info.status}
     out["bicgstab_convdiff2d_1024"] = res
+    for _ in range(2):
+        x = torch.zeros_like(b)
+        t, info = _time_call(torch, lambda: M.gmres(b, x, tol=1e-10, restart=30, maxit=20000, fmt="ell", stream=st))
+    out["gmres30_convdiff2d_1024"] = {"s": round(t, 4), "steps": info.iterations, "rel_residual": info.rel_residual,
+                                      "status": info.status}
     B = load_workload("batched_4096")
     G = gko.Batch(B, stream=st)
     rhs = torch.from_numpy(B["rhs"]).to(dev)

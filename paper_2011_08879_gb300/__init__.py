@@ -173,6 +173,10 @@ class Matrix:
         return binding.gko_bicgstab(self.handle, _fmt(fmt), _dev_f64(b, self.n_rows, "b"),
                                     _dev_f64(x, self.n_rows, "x"), tol, maxit, _stream(stream))
 
+    def gmres(self, b, x, tol=1e-10, restart=30, maxit=10000, fmt="csr", stream=None):
+        return binding.gko_gmres(self.handle, _fmt(fmt), _dev_f64(b, self.n_rows, "b"),
+                                 _dev_f64(x, self.n_rows, "x"), tol, restart, maxit, _stream(stream))
+
     def cg_mixed(self, b, x, inner="fp32", tol=1e-10, maxit_outer=50, inner_tol=None, inner_maxit=100000,
                  stream=None):
         """inner_tol None: 1e-2 for FP32 storage, 1e-1 for BF16 (the fastest

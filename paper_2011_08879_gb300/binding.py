@@ -63,6 +63,7 @@ _SIGS = {
     "gko_pcg_jacobi": (_INT, [_P, _INT, _P, _P, _D, _INT, _P, C.POINTER(SolveInfo)]),
     "gko_bicgstab": (_INT, [_P, _INT, _P, _P, _D, _INT, _P, C.POINTER(SolveInfo)]),
     "gko_spmm": (_INT, [_P, _I64, _P, _I64, _P, _I64, _D, _D, _P]),
+    "gko_gmres": (_INT, [_P, _INT, _P, _P, _D, _INT, _INT, _P, C.POINTER(SolveInfo)]),
     "gko_cg_mixed": (_INT, [_P, _INT, _P, _P, _D, _INT, _D, _INT, _P, C.POINTER(SolveInfo)]),
     "gko_batch_create": (_INT, [_I64, _P, _P, _P, _P, _INT, _P, C.POINTER(_P)]),
     "gko_batch_destroy": (_INT, [_P]),
@@ -212,6 +213,16 @@ def gko_bicgstab(A, fmt, b, x, tol, maxit, stream=0, raise_on=()) -> SolveInfo:
 def gko_spmm(A, k, x, ldx, y, ldy, alpha=1.0, beta=0.0, stream=0) -> None:
     """Y = alpha A X + beta Y (row-major blocks; device pointers)."""
     _check(lib.gko_spmm(A, k, x, ldx, y, ldy, alpha, beta, stream), "gko_spmm")
+
+
+def gko_gmres(A, fmt, b, x, tol, restart, maxit, stream=0, raise_on=()) -> SolveInfo:
+    """Restarted GMRES; NOT_CONVERGED and BREAKDOWN are reported in info.status."""
+    info = SolveInfo()
+    s = lib.gko_gmres(A, fmt, b, x, tol, restart, maxit, stream, C.byref(info))
+    allow = tuple(c for c in (ERR_NOT_CONVERGED, ERR_BREAKDOWN) if c not in raise_on)
+    _check(s, "gko_gmres", allow)
+    info.status = s
+    return info
 
 
 def gko_cg_mixed(A, inner_dtype, b, x, tol, maxit_outer, inner_tol, inner_maxit, stream=0) -> SolveInfo:

@@ -408,6 +408,20 @@ int gko_bicgstab(const gko_matrix* A, int fmt, const double* b, double* x, doubl
     return bicgstab_solve(A, fmt, b, x, tol, maxit, static_cast<cudaStream_t>(stream), info);
 }
 
+int gko_gmres(const gko_matrix* A, int fmt, const double* b, double* x, double tol, int restart, int maxit,
+              void* stream, gko_solve_info* info)
+{
+    if (!A) return fail(GKO_ERR_INVALID_ARG, "NULL handle");
+    if (A->n_rows != A->n_cols) return fail(GKO_ERR_DIM_MISMATCH, "GMRES needs a square matrix");
+    if (!valid_fmt(fmt)) return fail(GKO_ERR_INVALID_ARG, "unknown format");
+    if (!A->has[fmt]) return fail(GKO_ERR_FORMAT_UNAVAILABLE, "format not materialised");
+    if (A->n_rows > 0 && (!b || !x)) return fail(GKO_ERR_INVALID_ARG, "NULL vector");
+    if (!(tol >= 0.0) || maxit < 0 || restart < 1 || restart > 127)
+        return fail(GKO_ERR_INVALID_ARG, "tol >= 0, maxit >= 0 and 1 <= restart <= 127 required");
+    GKO_TRY(check_device(A));
+    return gmres_solve(A, fmt, b, x, tol, restart, maxit, static_cast<cudaStream_t>(stream), info);
+}
+
 int gko_cg_mixed(gko_matrix* A, int inner_dtype, const double* b, double* x, double tol, int maxit_outer,
                  double inner_tol, int inner_maxit, void* stream, gko_solve_info* info)
 {

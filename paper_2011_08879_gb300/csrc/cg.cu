@@ -18,6 +18,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <vector>
 
 #include "common.cuh"
 #include "internal.h"
@@ -1028,6 +1029,219 @@ int bicgstab_solve(const gko_matrix* A, int fmt, const double* b, double* x, dou
     if (status != GKO_OK)
         set_error(status == GKO_ERR_BREAKDOWN ? "BiCGSTAB breakdown (r^.v, t.t or omega zero, or NaN)"
                                               : "BiCGSTAB reached maxit");
+    return status;
+}
+
+// --------------------------------------------------------------- GMRES
+
+constexpr int kGmChunk = 8;  // basis vectors per multi-dot / combination launch
+
+// part[blk * ldp + c0 + c] = the block's share of V_{c0+c} . w (c < cnt)
+__global__ void __launch_bounds__(kRedThreads)
+    gm_multidot_kernel(int64_t n, const double* __restrict__ V, int64_t ldv, int c0, int cnt,
+                       const double* __restrict__ w, double* __restrict__ part, int ldp)
+{
+    __shared__ double sh[kGmChunk][kRedThreads / 32];
+    double acc[kGmChunk];
+#pragma unroll
+    for (int c = 0; c < kGmChunk; ++c) acc[c] = 0.0;
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(kRedThreads) + threadIdx.x; i < n;
+         i += static_cast<int64_t>(gridDim.x) * kRedThreads) {
+        const double wi = w[i];
+#pragma unroll
+        for (int c = 0; c < kGmChunk; ++c)
+            if (c < cnt) acc[c] = fma(V[(c0 + c) * ldv + i], wi, acc[c]);
+    }
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+#pragma unroll
+    for (int c = 0; c < kGmChunk; ++c) {
+        double v = acc[c];
+        for (int o = 16; o; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) sh[c][wp] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < cnt) {
+        double t = 0.0;
+        for (int k = 0; k < kRedThreads / 32; ++k) t += sh[threadIdx.x][k];
+        part[blockIdx.x * static_cast<int64_t>(ldp) + c0 + threadIdx.x] = t;
+    }
+}
+
+// h[c] = sum over blocks (in block order) of part[b * ldp + c], c < ncols
+__global__ void gm_reduce_kernel(int nblocks, int ncols, const double* __restrict__ part, int ldp,
+                                 double* __restrict__ h)
+{
+    for (int c = threadIdx.x; c < ncols; c += blockDim.x) {
+        double t = 0.0;
+        for (int b = 0; b < nblocks; ++b) t += part[b * static_cast<int64_t>(ldp) + c];
+        h[c] = t;
+    }
+}
+
+// w -= sum_{c < ncols} h[c] V_c  (sgn = -1) or x += sum y[c] V_c (sgn = +1)
+__global__ void __launch_bounds__(kRedThreads)
+    gm_combine_kernel(int64_t n, double* __restrict__ w, const double* __restrict__ V, int64_t ldv, int ncols,
+                      const double* __restrict__ h, double sgn)
+{
+    __shared__ double hs[128];
+    for (int c = threadIdx.x; c < ncols; c += blockDim.x) hs[c] = sgn * h[c];
+    __syncthreads();
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(kRedThreads) + threadIdx.x; i < n;
+         i += static_cast<int64_t>(gridDim.x) * kRedThreads) {
+        double t = w[i];
+        for (int c = 0; c < ncols; ++c) t = fma(hs[c], V[c * ldv + i], t);
+        w[i] = t;
+    }
+}
+
+// out = w / s (s on the device)
+__global__ void gm_scale_kernel(int64_t n, double* __restrict__ out, const double* __restrict__ w, double s)
+{
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+        out[i] = w[i] / s;
+}
+
+// Restarted GMRES(m) (Saad and Schultz 1986) for general square A.  The
+// Arnoldi basis V (m + 1 vectors of n) lives in device memory; A v_j is
+// orthogonalised by classical Gram-Schmidt applied twice (each pass: one
+// multi-dot launch per 8 basis vectors with fixed-order partial sums, one
+// combination launch), its norm taken by one grid reduction; the (j + 2)
+// Hessenberg entries go to the host, which applies the Givens rotations and
+// reads the residual estimate (one synchronisation per step).  A cycle
+// ends at m steps or when the estimate is <= tol ||b||; x += V y, and the
+// next cycle starts from the FP64 true residual, which decides convergence.
+int gmres_solve(const gko_matrix* A, int fmt, const double* b, double* x, double tol, int m, int maxit,
+                cudaStream_t st, gko_solve_info* info)
+{
+    const int64_t n = A->n_rows;
+    if (n == 0) {
+        fill_info(info, 0, 0, 0.0, GKO_OK);
+        return GKO_OK;
+    }
+    Workspace ws(st);
+    double *V, *w, *part, *h, *hsum;
+    SolverState* ds;
+    const int grid = red_grid(n);
+    GKO_TRY(ws.get(&V, n * (m + 1)));
+    GKO_TRY(ws.get(&w, n));
+    GKO_TRY(ws.get(&part, static_cast<int64_t>(kRedBlocks) * (m + 1) + 2 * kRedBlocks));
+    GKO_TRY(ws.get(&h, m + 1));
+    GKO_TRY(ws.get(&hsum, m + 1));
+    GKO_TRY(ws.get(&ds, 1));
+    SolverState hs = {};
+    GKO_TRY(write_state(ds, &hs, st));
+    auto norm = [&](const double* v, double* out) -> int {
+        dot_kernel<double, kDotStore><<<grid, kRedThreads, 0, st>>>(n, v, v, ds, part, 0);
+        GKO_TRY(read_state(&hs, ds, st));
+        *out = std::sqrt(hs.dot_out);
+        return GKO_OK;
+    };
+    double bnorm;
+    GKO_TRY(norm(b, &bnorm));
+    if (bnorm == 0.0) {
+        GKO_CUDA(cudaMemsetAsync(x, 0, n * sizeof(double), st));
+        GKO_CUDA(cudaStreamSynchronize(st));
+        fill_info(info, 0, 0, 0.0, GKO_OK);
+        return GKO_OK;
+    }
+    // V_c . w for c < ncols into h (device)
+    auto multidot = [&](int ncols, const double* vec) -> int {
+        for (int c0 = 0; c0 < ncols; c0 += kGmChunk)
+            gm_multidot_kernel<<<grid, kRedThreads, 0, st>>>(n, V, n, c0, std::min(kGmChunk, ncols - c0), vec, part,
+                                                              m + 1);
+        gm_reduce_kernel<<<1, 128, 0, st>>>(grid, ncols, part, m + 1, h);
+        GKO_CUDA(cudaGetLastError());
+        return GKO_OK;
+    };
+    std::vector<double> H(static_cast<size_t>(m + 1) * m, 0.0), cs(m), sn(m), g(m + 1), yv(m), hh(m + 2);
+    int status = GKO_ERR_NOT_CONVERGED, total = 0;
+    double res = -1.0;
+    while (true) {
+        // r = b - A x into V_0, beta = ||r||
+        GKO_CUDA(cudaMemcpyAsync(V, b, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        GKO_TRY(spmv_fmt(A, fmt, x, V, -1.0, 1.0, st));
+        double beta;
+        GKO_TRY(norm(V, &beta));
+        res = beta / bnorm;
+        if (!(beta == beta)) {
+            status = GKO_ERR_BREAKDOWN;
+            break;
+        }
+        if (beta <= tol * bnorm) {
+            status = GKO_OK;
+            break;
+        }
+        if (total >= maxit) break;
+        gm_scale_kernel<<<grid, kRedThreads, 0, st>>>(n, V, V, beta);
+        std::fill(g.begin(), g.end(), 0.0);
+        g[0] = beta;
+        int j = 0;
+        bool broke = false;
+        for (; j < m && total < maxit; ++j) {
+            double* vj1 = V + (j + 1) * n;
+            GKO_TRY(spmv_fmt(A, fmt, V + j * n, w, 1.0, 0.0, st));
+            total += 1;
+            // classical Gram-Schmidt, twice
+            std::fill(hh.begin(), hh.end(), 0.0);
+            for (int pass = 0; pass < 2; ++pass) {
+                GKO_TRY(multidot(j + 1, w));
+                gm_combine_kernel<<<grid, kRedThreads, 0, st>>>(n, w, V, n, j + 1, h, -1.0);
+                std::vector<double> hp(j + 1);
+                GKO_CUDA(cudaMemcpyAsync(hp.data(), h, (j + 1) * sizeof(double), cudaMemcpyDeviceToHost, st));
+                GKO_CUDA(cudaStreamSynchronize(st));
+                for (int i = 0; i <= j; ++i) hh[i] += hp[i];
+            }
+            double hn;
+            GKO_TRY(norm(w, &hn));
+            if (!(hn == hn)) {
+                broke = true;
+                break;
+            }
+            if (hn > 0.0) gm_scale_kernel<<<grid, kRedThreads, 0, st>>>(n, vj1, w, hn);
+            for (int i = 0; i <= j; ++i) H[static_cast<size_t>(i) * m + j] = hh[i];
+            H[static_cast<size_t>(j + 1) * m + j] = hn;
+            for (int i = 0; i < j; ++i) {  // earlier rotations on the new column
+                const double a = H[static_cast<size_t>(i) * m + j], c = H[static_cast<size_t>(i + 1) * m + j];
+                H[static_cast<size_t>(i) * m + j] = cs[i] * a + sn[i] * c;
+                H[static_cast<size_t>(i + 1) * m + j] = -sn[i] * a + cs[i] * c;
+            }
+            const double a = H[static_cast<size_t>(j) * m + j], c = H[static_cast<size_t>(j + 1) * m + j];
+            const double d = std::sqrt(a * a + c * c);
+            if (!(d > 0.0)) {
+                broke = true;
+                break;
+            }
+            cs[j] = a / d;
+            sn[j] = c / d;
+            H[static_cast<size_t>(j) * m + j] = d;
+            H[static_cast<size_t>(j + 1) * m + j] = 0.0;
+            g[j + 1] = -sn[j] * g[j];
+            g[j] = cs[j] * g[j];
+            if (std::fabs(g[j + 1]) <= tol * bnorm || !(hn > 0.0)) {
+                j += 1;
+                break;
+            }
+        }
+        if (broke) {
+            status = GKO_ERR_BREAKDOWN;
+            break;
+        }
+        for (int i = j - 1; i >= 0; --i) {  // back substitution
+            double sacc = g[i];
+            for (int k = i + 1; k < j; ++k) sacc -= H[static_cast<size_t>(i) * m + k] * yv[k];
+            yv[i] = sacc / H[static_cast<size_t>(i) * m + i];
+        }
+        if (j > 0) {
+            GKO_CUDA(cudaMemcpyAsync(hsum, yv.data(), j * sizeof(double), cudaMemcpyHostToDevice, st));
+            gm_combine_kernel<<<grid, kRedThreads, 0, st>>>(n, x, V, n, j, hsum, 1.0);
+            GKO_CUDA(cudaGetLastError());
+        }
+    }
+    GKO_CUDA(cudaStreamSynchronize(st));
+    fill_info(info, total, 0, res, status);
+    if (status != GKO_OK)
+        set_error(status == GKO_ERR_BREAKDOWN ? "GMRES breakdown (NaN or zero rotation)" : "GMRES reached maxit");
     return status;
 }
 

@@ -228,6 +228,8 @@ int bicgstab_solve(const gko_matrix* A, int fmt, const double* b, double* x, dou
                    cudaStream_t st, gko_solve_info* info);
 int spmm_csr(const gko_matrix* A, int64_t k, const double* x, int64_t ldx, double* y, int64_t ldy, double alpha,
              double beta, cudaStream_t st);
+int gmres_solve(const gko_matrix* A, int fmt, const double* b, double* x, double tol, int m, int maxit,
+                cudaStream_t st, gko_solve_info* info);
 int cg1_solve(const gko_matrix* A, int fmt, const double* b, double* x, double tol, int maxit,
               cudaStream_t st, gko_solve_info* info);
 int cg_mixed_solve(gko_matrix* A, int inner, const double* b, double* x, double tol, int maxit_outer,
