@@ -88,6 +88,7 @@ def _declare(L):
         "orc_round_fp32": (_D, [_D, _INT]),
         "orc_round_matrix": (None, [_I64, _P, _P, _P, _INT, _P]),
         "orc_cg_mixed": (_INT, [_I64, _P, _P, _P, _P, _P, _P, _D, _INT, _D, _INT, _P, _P, _P]),
+        "orc_cg_mixed_precond": (_INT, [_I64, _P, _P, _P, _P, _P, _P, _D, _INT, _D, _INT, _INT, _P, _P, _P]),
         "orc_cholesky_solve": (_INT, [_I64, _P, _P, _P]),
         "orc_features": (None, [_I64, _P, _P, _P]),
     }
@@ -376,16 +377,21 @@ def round_matrix(A, prec):
 
 
 def cg_mixed(A, b, prec="fp32", x0=None, tol=1e-10, maxit_outer=100, inner_tol=1e-4,
-             inner_maxit=100000):
-    """Mixed-precision CG with FP64 refinement.
+             inner_maxit=100000, precond="none"):
+    """Mixed-precision CG with FP64 refinement (precond "jacobi": the inner
+    CG preconditioned by the diagonal of the rounded matrix).
     Returns (x, status, outer corrections, inner iterations, true rel. residual)."""
     n, rp, ci, v = _csr(A)
     vlo = round_matrix(A, prec)
     b = _c(b, np.float64)
     x = np.zeros(n) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
     o, i, res = C.c_int(0), C.c_int(0), C.c_double(0.0)
-    st = lib().orc_cg_mixed(n, _p(rp), _p(ci), _p(v), _p(vlo), _p(b), _p(x), tol, maxit_outer,
-                            inner_tol, inner_maxit, C.byref(o), C.byref(i), C.byref(res))
+    if precond == "jacobi":
+        st = lib().orc_cg_mixed_precond(n, _p(rp), _p(ci), _p(v), _p(vlo), _p(b), _p(x), tol, maxit_outer,
+                                        inner_tol, inner_maxit, 1, C.byref(o), C.byref(i), C.byref(res))
+    else:
+        st = lib().orc_cg_mixed(n, _p(rp), _p(ci), _p(v), _p(vlo), _p(b), _p(x), tol, maxit_outer,
+                                inner_tol, inner_maxit, C.byref(o), C.byref(i), C.byref(res))
     return x, int(st), o.value, i.value, res.value
 
 

@@ -1163,10 +1163,10 @@ void orc_round_matrix(int64_t n, const int32_t *row_ptr, const int32_t *col,
  * to FP32) to relative recursive residual inner_tol or inner_maxit steps;
  * then x += ||r|| d in FP64.  x holds the initial guess.  Counts outer
  * corrections in *outer and inner CG steps in *inner. */
-int orc_cg_mixed(int64_t n, const int32_t *row_ptr, const int32_t *col,
-                 const double *val, const double *val_lo, const double *b, double *x,
-                 double tol, int maxit_outer, double inner_tol, int inner_maxit,
-                 int *outer, int *inner, double *rel_res)
+int orc_cg_mixed_precond(int64_t n, const int32_t *row_ptr, const int32_t *col,
+                         const double *val, const double *val_lo, const double *b, double *x,
+                         double tol, int maxit_outer, double inner_tol, int inner_maxit, int precond,
+                         int *outer, int *inner, double *rel_res)
 {
     double nb = nrm2(n, b);
     *outer = 0;
@@ -1181,10 +1181,21 @@ int orc_cg_mixed(int64_t n, const int32_t *row_ptr, const int32_t *col,
     double *r = (double *)malloc(nn * sizeof(double));
     float *rl = (float *)malloc(nn * sizeof(float)), *d = (float *)malloc(nn * sizeof(float)),
           *p = (float *)malloc(nn * sizeof(float)), *q = (float *)malloc(nn * sizeof(float)),
-          *vl = (float *)malloc((size_t)(row_ptr[n] > 0 ? row_ptr[n] : 1) * sizeof(float));
+          *vl = (float *)malloc((size_t)(row_ptr[n] > 0 ? row_ptr[n] : 1) * sizeof(float)),
+          *z = (float *)malloc(nn * sizeof(float)), *dl = (float *)malloc(nn * sizeof(float));
     for (int64_t k = 0; k < row_ptr[n]; ++k)
         vl[k] = (float)val_lo[k]; /* exact: val_lo holds FP32/BF16 values */
     int status = ORC_NOT_CONVERGED;
+    for (int64_t i = 0; i < n; ++i) { /* diagonal of A_lo (Jacobi) */
+        dl[i] = 0.0f;
+        for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k)
+            if (col[k] == i)
+                dl[i] = vl[k];
+        if (precond && !(dl[i] != 0.0f))
+            status = ORC_BREAKDOWN;
+    }
+    if (status == ORC_BREAKDOWN)
+        maxit_outer = 0;
     for (int o = 0; o <= maxit_outer; ++o) {
         for (int64_t i = 0; i < n; ++i)
             r[i] = b[i];
@@ -1197,15 +1208,17 @@ int orc_cg_mixed(int64_t n, const int32_t *row_ptr, const int32_t *col,
         if (o == maxit_outer)
             break;
         *outer = o + 1;
-        /* inner CG on A_lo d = r / ||r||, d0 = 0 */
+        /* inner CG on A_lo d = r / ||r||, d0 = 0, preconditioned by
+         * M = diag(A_lo) when precond (z = M^-1 r; else z = r) */
         for (int64_t i = 0; i < n; ++i) {
             rl[i] = (float)(r[i] / nr);
             d[i] = 0.0f;
-            p[i] = rl[i];
+            z[i] = precond ? rl[i] / dl[i] : rl[i];
+            p[i] = z[i];
         }
         double rho_d = 0.0;
         for (int64_t i = 0; i < n; ++i)
-            rho_d = rho_d + (double)rl[i] * (double)rl[i];
+            rho_d = rho_d + (double)rl[i] * (double)z[i];
         float rho = (float)rho_d;
         float rho0 = rho;
         for (int it = 0; it < inner_maxit; ++it) {
@@ -1230,17 +1243,18 @@ int orc_cg_mixed(int64_t n, const int32_t *row_ptr, const int32_t *col,
                 d[i] = d[i] + t;
                 float u = alpha * q[i];
                 rl[i] = rl[i] - u;
+                z[i] = precond ? rl[i] / dl[i] : rl[i];
             }
             double rn_d = 0.0;
             for (int64_t i = 0; i < n; ++i)
-                rn_d = rn_d + (double)rl[i] * (double)rl[i];
+                rn_d = rn_d + (double)rl[i] * (double)z[i];
             float rho_new = (float)rn_d;
             if (sqrtf(rho_new) <= (float)inner_tol * sqrtf(rho0))
                 break;
             float beta = rho_new / rho;
             for (int64_t i = 0; i < n; ++i) {
                 float t = beta * p[i];
-                p[i] = rl[i] + t;
+                p[i] = z[i] + t;
             }
             rho = rho_new;
         }
@@ -1256,7 +1270,19 @@ int orc_cg_mixed(int64_t n, const int32_t *row_ptr, const int32_t *col,
     free(p);
     free(q);
     free(vl);
+    free(z);
+    free(dl);
     return status;
+}
+
+/* The unpreconditioned inner solve (z = r). */
+int orc_cg_mixed(int64_t n, const int32_t *row_ptr, const int32_t *col,
+                 const double *val, const double *val_lo, const double *b, double *x,
+                 double tol, int maxit_outer, double inner_tol, int inner_maxit,
+                 int *outer, int *inner, double *rel_res)
+{
+    return orc_cg_mixed_precond(n, row_ptr, col, val, val_lo, b, x, tol, maxit_outer, inner_tol,
+                                inner_maxit, 0, outer, inner, rel_res);
 }
 
 /* ------------------------------------------------------- dense Cholesky */

@@ -589,6 +589,33 @@ def test_gmres_special_cases(orc):
     assert st == orc.OK and it == 0
 
 
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_mixed_cg_jacobi_inner(orc, prec):
+    """Jacobi-preconditioned inner solve: it reaches the FP64 residual with
+    several times fewer inner steps than the unpreconditioned inner solve
+    (FP32 storage: diffusion operator rescaled over three decades; BF16
+    storage, whose 8-bit significand cannot hold that scaled operator: the
+    variable-coefficient diffusion operator itself); a constant diagonal
+    (Laplacian) leaves the inner iterates unchanged."""
+    A0 = syn.diffusion7(12, 1.0, seed=6)
+    n = A0["n_rows"]
+    if prec == "fp32":
+        s = 10.0 ** (3.0 * syn.uniform01(27, 1, np.arange(n, dtype=np.uint64)))
+        A, factor = _scaled(A0, s), 3
+    else:
+        A, factor = A0, 1
+    b = orc.spmv_csr(A, syn.vector(n, 28))
+    xj, stj, oj, ij, rj = orc.cg_mixed(A, b, prec, tol=1e-10, inner_tol=1e-2, precond="jacobi")
+    xn, stn, on, in_, rn = orc.cg_mixed(A, b, prec, tol=1e-10, inner_tol=1e-2, maxit_outer=400)
+    assert stj == orc.OK and rj <= 1e-10
+    assert ij * factor < in_, (ij, in_)
+    L = syn.laplace2d(20)
+    bl = orc.spmv_csr(L, syn.vector(400, 29))
+    r1 = orc.cg_mixed(L, bl, prec, tol=1e-10, inner_tol=1e-3)
+    r2 = orc.cg_mixed(L, bl, prec, tol=1e-10, inner_tol=1e-3, precond="jacobi")
+    assert r1[2] == r2[2] and abs(r1[3] - r2[3]) <= 2 and r2[4] <= 1e-10
+
+
 def test_batched_cg(orc):
     B = syn.batched_spd(12, seed=8)
     x, st, it, res = orc.cg_batched(B, B["rhs"], tol=1e-10)
