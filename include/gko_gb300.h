@@ -74,6 +74,9 @@ enum {
 /* Value types. */
 enum { GKO_F64 = 0, GKO_F32 = 1, GKO_BF16 = 2 };
 
+/* Preconditioners of the mixed-precision inner solve. */
+enum { GKO_PRECOND_NONE = 0, GKO_PRECOND_JACOBI = 1 };
+
 /* Kernel configurations accepted by gko_spmv_config (the candidates of the
  * exhaustive sweep / selector).  GKO_CFG_DEFAULT lets the library choose. */
 enum {
@@ -330,6 +333,18 @@ int gko_gmres(const gko_matrix* A, int fmt, const double* b, double* x, double t
 int gko_cg_mixed(gko_matrix* A, int inner_dtype, const double* b, double* x, double tol,
                  int maxit_outer, double inner_tol, int inner_maxit, void* stream,
                  gko_solve_info* info);
+
+/* gko_cg_mixed with a preconditioner for the inner solve: precond
+ * GKO_PRECOND_JACOBI preconditions the inner CG by M = diag(A_lo), the
+ * rounded matrix's diagonal (its inverse kept in FP32): u = M^-1 r is what
+ * the inner product gathers, gamma = r.u and delta = (A_lo u).u drive the
+ * single-reduction step, and the inner stop is relative in the M^-1 norm
+ * (sqrt(r.u)).  The outer FP64 residual still decides convergence.  A zero
+ * or missing diagonal entry of A_lo returns GKO_ERR_BREAKDOWN before any
+ * step.  GKO_PRECOND_NONE is gko_cg_mixed. */
+int gko_cg_mixed_precond(gko_matrix* A, int inner_dtype, int precond, const double* b, double* x, double tol,
+                         int maxit_outer, double inner_tol, int inner_maxit, void* stream,
+                         gko_solve_info* info);
 
 /* ------------------------------------------------------------- batched */
 

@@ -178,12 +178,17 @@ class Matrix:
                                  _dev_f64(x, self.n_rows, "x"), tol, restart, maxit, _stream(stream))
 
     def cg_mixed(self, b, x, inner="fp32", tol=1e-10, maxit_outer=50, inner_tol=None, inner_maxit=100000,
-                 stream=None):
+                 stream=None, precond="none"):
         """inner_tol None: 1e-2 for FP32 storage, 1e-1 for BF16 (the fastest
-        settings measured on a 160^3 variable-coefficient diffusion operator)."""
+        settings measured on a 160^3 variable-coefficient diffusion operator).
+        precond "jacobi": the inner solve preconditioned by diag(A_lo)."""
         dt = binding.BF16 if inner == "bf16" else binding.F32
         if inner_tol is None:
             inner_tol = 1e-1 if inner == "bf16" else 1e-2
+        if precond == "jacobi":
+            return binding.gko_cg_mixed_precond(self.handle, dt, binding.PRECOND_JACOBI, _dev_f64(b, self.n_rows, "b"),
+                                                _dev_f64(x, self.n_rows, "x"), tol, maxit_outer, inner_tol,
+                                                inner_maxit, _stream(stream))
         return binding.gko_cg_mixed(self.handle, dt, _dev_f64(b, self.n_rows, "b"), _dev_f64(x, self.n_rows, "x"),
                                     tol, maxit_outer, inner_tol, inner_maxit, _stream(stream))
 

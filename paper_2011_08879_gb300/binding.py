@@ -64,6 +64,7 @@ _SIGS = {
     "gko_bicgstab": (_INT, [_P, _INT, _P, _P, _D, _INT, _P, C.POINTER(SolveInfo)]),
     "gko_spmm": (_INT, [_P, _I64, _P, _I64, _P, _I64, _D, _D, _P]),
     "gko_gmres": (_INT, [_P, _INT, _P, _P, _D, _INT, _INT, _P, C.POINTER(SolveInfo)]),
+    "gko_cg_mixed_precond": (_INT, [_P, _INT, _INT, _P, _P, _D, _INT, _D, _INT, _P, C.POINTER(SolveInfo)]),
     "gko_cg_mixed": (_INT, [_P, _INT, _P, _P, _D, _INT, _D, _INT, _P, C.POINTER(SolveInfo)]),
     "gko_batch_create": (_INT, [_I64, _P, _P, _P, _P, _INT, _P, C.POINTER(_P)]),
     "gko_batch_destroy": (_INT, [_P]),
@@ -229,6 +230,19 @@ def gko_cg_mixed(A, inner_dtype, b, x, tol, maxit_outer, inner_tol, inner_maxit,
     info = SolveInfo()
     s = lib.gko_cg_mixed(A, inner_dtype, b, x, tol, maxit_outer, inner_tol, inner_maxit, stream, C.byref(info))
     _check(s, "gko_cg_mixed", (ERR_NOT_CONVERGED, ERR_BREAKDOWN))
+    info.status = s
+    return info
+
+
+PRECOND_NONE, PRECOND_JACOBI = 0, 1
+
+
+def gko_cg_mixed_precond(A, inner_dtype, precond, b, x, tol, maxit_outer, inner_tol, inner_maxit,
+                         stream=0) -> SolveInfo:
+    info = SolveInfo()
+    s = lib.gko_cg_mixed_precond(A, inner_dtype, precond, b, x, tol, maxit_outer, inner_tol, inner_maxit, stream,
+                                 C.byref(info))
+    _check(s, "gko_cg_mixed_precond", (ERR_NOT_CONVERGED, ERR_BREAKDOWN))
     info.status = s
     return info
 

@@ -425,7 +425,16 @@ int gko_gmres(const gko_matrix* A, int fmt, const double* b, double* x, double t
 int gko_cg_mixed(gko_matrix* A, int inner_dtype, const double* b, double* x, double tol, int maxit_outer,
                  double inner_tol, int inner_maxit, void* stream, gko_solve_info* info)
 {
+    return gko_cg_mixed_precond(A, inner_dtype, GKO_PRECOND_NONE, b, x, tol, maxit_outer, inner_tol, inner_maxit,
+                                stream, info);
+}
+
+int gko_cg_mixed_precond(gko_matrix* A, int inner_dtype, int precond, const double* b, double* x, double tol,
+                         int maxit_outer, double inner_tol, int inner_maxit, void* stream, gko_solve_info* info)
+{
     if (!A) return fail(GKO_ERR_INVALID_ARG, "NULL handle");
+    if (precond != GKO_PRECOND_NONE && precond != GKO_PRECOND_JACOBI)
+        return fail(GKO_ERR_INVALID_ARG, "precond must be GKO_PRECOND_NONE or GKO_PRECOND_JACOBI");
     if (A->n_rows != A->n_cols) return fail(GKO_ERR_DIM_MISMATCH, "CG needs a square matrix");
     if (inner_dtype != GKO_F32 && inner_dtype != GKO_BF16)
         return fail(GKO_ERR_INVALID_ARG, "inner_dtype must be GKO_F32 or GKO_BF16");
@@ -435,7 +444,7 @@ int gko_cg_mixed(gko_matrix* A, int inner_dtype, const double* b, double* x, dou
         return fail(GKO_ERR_INVALID_ARG, "bad tolerance or iteration limit");
     GKO_TRY(check_device(A));
     return cg_mixed_solve(A, inner_dtype, b, x, tol, maxit_outer, inner_tol, inner_maxit,
-                          static_cast<cudaStream_t>(stream), info);
+                          static_cast<cudaStream_t>(stream), info, precond);
 }
 
 int gko_features(const gko_matrix* A, double* out, void* stream)

@@ -240,10 +240,14 @@ struct Vec16<double> {
 // with alpha, beta from the product kernel's scalar step (s = A p is carried
 // by recurrence, so no second product or reduction is needed).  kVec: all
 // vectors 16-byte aligned, moved as 128-bit words.
-template <typename T, bool kVec>
+// kPrec: preconditioned by a diagonal (dinv = its inverse): p = u + beta p
+// with u = dinv r the preconditioned residual, and u is refreshed from the
+// updated r.
+template <typename T, bool kVec, bool kPrec = false>
 __global__ void __launch_bounds__(kRedThreads)
     cg1_update_kernel(int64_t n, T* __restrict__ x, T* __restrict__ r, T* __restrict__ p, T* __restrict__ s,
-                      const T* __restrict__ w, const SolverState* st)
+                      const T* __restrict__ w, const SolverState* st, const T* __restrict__ dinv = nullptr,
+                      T* __restrict__ u = nullptr)
 {
     if (st->done) return;
     const T alpha = static_cast<T>(st->alpha), beta = static_cast<T>(st->beta);
@@ -259,47 +263,58 @@ __global__ void __launch_bounds__(kRedThreads)
         };
         const int64_t nv = n / W;
         for (int64_t i = tid; i < nv; i += nth) {
-            U rv, wv, pv, sv, xv;
+            U rv, wv, pv, sv, xv, uv, dv;
             rv.v = reinterpret_cast<const V*>(r)[i];
             wv.v = reinterpret_cast<const V*>(w)[i];
             pv.v = reinterpret_cast<const V*>(p)[i];
             sv.v = reinterpret_cast<const V*>(s)[i];
             xv.v = reinterpret_cast<const V*>(x)[i];
+            if (kPrec) {
+                uv.v = reinterpret_cast<const V*>(u)[i];
+                dv.v = reinterpret_cast<const V*>(dinv)[i];
+            }
 #pragma unroll
             for (int k = 0; k < W; ++k) {
-                pv.a[k] = fma(beta, pv.a[k], rv.a[k]);
+                pv.a[k] = fma(beta, pv.a[k], kPrec ? uv.a[k] : rv.a[k]);
                 sv.a[k] = fma(beta, sv.a[k], wv.a[k]);
                 xv.a[k] = fma(alpha, pv.a[k], xv.a[k]);
                 rv.a[k] = fma(-alpha, sv.a[k], rv.a[k]);
+                if (kPrec) uv.a[k] = dv.a[k] * rv.a[k];
             }
             reinterpret_cast<V*>(p)[i] = pv.v;
             reinterpret_cast<V*>(s)[i] = sv.v;
             reinterpret_cast<V*>(x)[i] = xv.v;
             reinterpret_cast<V*>(r)[i] = rv.v;
+            if (kPrec) reinterpret_cast<V*>(u)[i] = uv.v;
         }
         i0 = nv * W;
     }
     for (int64_t i = i0 + tid; i < n; i += nth) {
-        const T pi = fma(beta, p[i], r[i]);
+        const T pi = fma(beta, p[i], kPrec ? u[i] : r[i]);
         const T si = fma(beta, s[i], w[i]);
         p[i] = pi;
         s[i] = si;
         x[i] = fma(alpha, pi, x[i]);
-        r[i] = fma(-alpha, si, r[i]);
+        const T ri = fma(-alpha, si, r[i]);
+        r[i] = ri;
+        if (kPrec) u[i] = dinv[i] * ri;
     }
 }
 
 // gamma = r.r and delta = w.r with one grid reduction ending in the scalar
 // step (for products by kernels that do not fuse the dots themselves)
+// (with a preconditioner: gamma = rd.u and delta = w.u for u = M^-1 rd; here
+// u is passed as r and the residual as rd; rd = r without one)
 template <typename T>
 __global__ void __launch_bounds__(kRedThreads)
-    cg1_dots_kernel(int64_t n, const T* __restrict__ r, const T* __restrict__ w, Cg1Reduce red)
+    cg1_dots_kernel(int64_t n, const T* __restrict__ r, const T* __restrict__ rd, const T* __restrict__ w,
+                    Cg1Reduce red)
 {
     T g = T(0), d = T(0);
     for (int64_t i = blockIdx.x * static_cast<int64_t>(kRedThreads) + threadIdx.x; i < n;
          i += static_cast<int64_t>(gridDim.x) * kRedThreads) {
         const T ri = r[i];
-        g = fma(ri, ri, g);
+        g = fma(rd[i], ri, g);
         d = fma(w[i], ri, d);
     }
     SolverState* s = red.s;
@@ -315,23 +330,50 @@ static int upd_grid(int64_t n)
 
 template <typename T>
 static void launch_cg1_update(int64_t n, T* x, T* r, T* p, T* s, const T* w, const SolverState* st,
-                              cudaStream_t cs)
+                              cudaStream_t cs, const T* dinv = nullptr, T* u = nullptr)
 {
     const bool vec = ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(r) |
                        reinterpret_cast<uintptr_t>(p) | reinterpret_cast<uintptr_t>(s) |
-                       reinterpret_cast<uintptr_t>(w)) & 15) == 0;
-    if (vec)
+                       reinterpret_cast<uintptr_t>(w) | reinterpret_cast<uintptr_t>(dinv) |
+                       reinterpret_cast<uintptr_t>(u)) & 15) == 0;
+    if (dinv) {
+        if (vec)
+            cg1_update_kernel<T, true, true><<<upd_grid(n), kRedThreads, 0, cs>>>(n, x, r, p, s, w, st, dinv, u);
+        else
+            cg1_update_kernel<T, false, true><<<upd_grid(n), kRedThreads, 0, cs>>>(n, x, r, p, s, w, st, dinv, u);
+    } else if (vec) {
         cg1_update_kernel<T, true><<<upd_grid(n), kRedThreads, 0, cs>>>(n, x, r, p, s, w, st);
-    else
+    } else {
         cg1_update_kernel<T, false><<<upd_grid(n), kRedThreads, 0, cs>>>(n, x, r, p, s, w, st);
+    }
+}
+
+// dinv[i] = 1 / (diagonal of the rounded matrix A_lo) in FP32 (values in CSR
+// order: float, or bf16 bits); a zero or missing diagonal sets *bad
+template <int kBf16>
+__global__ void diag_lo_inv_kernel(int64_t n, const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                                   const float* __restrict__ v32, const uint16_t* __restrict__ v16,
+                                   float* __restrict__ dinv, int32_t* bad)
+{
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        float d = 0.0f;
+        for (int32_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k)
+            if (col[k] >= i) {
+                if (col[k] == i) d = kBf16 ? __uint_as_float(static_cast<uint32_t>(v16[k]) << 16) : v32[k];
+                break;
+            }
+        dinv[i] = d != 0.0f ? 1.0f / d : 0.0f;
+        if (!(d != 0.0f)) atomicOr(bad, 1);
+    }
 }
 
 // ----------------------------------------------------------- workspace
 
+// Stream-ordered work arrays of one solve, freed when it returns.
 struct Workspace {
     cudaStream_t st;
-    void* ptrs[16] = {nullptr};
-    int n = 0;
+    std::vector<void*> ptrs;
     explicit Workspace(cudaStream_t s) : st(s) {}
     template <typename T>
     int get(T** p, int64_t count)
@@ -339,12 +381,12 @@ struct Workspace {
         *p = nullptr;
         cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(p), std::max<int64_t>(count, 1) * sizeof(T), st);
         if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync (solver workspace)");
-        ptrs[n++] = *p;
+        ptrs.push_back(*p);
         return GKO_OK;
     }
     ~Workspace()
     {
-        for (int i = 0; i < n; ++i) cudaFreeAsync(ptrs[i], st);
+        for (void* q : ptrs) cudaFreeAsync(q, st);
     }
 };
 
@@ -604,7 +646,7 @@ static int cg1_product_f64(const gko_matrix* A, int fmt, const double* r, double
         return e == cudaSuccess ? GKO_OK : cuda_fail(e, "single-reduction CG product");
     }
     GKO_TRY(spmv_fmt(A, fmt, r, w, 1.0, 0.0, cs));
-    cg1_dots_kernel<double><<<grid, kRedThreads, 0, cs>>>(n, r, w, red);
+    cg1_dots_kernel<double><<<grid, kRedThreads, 0, cs>>>(n, r, r, w, red);
     GKO_CUDA(cudaGetLastError());
     return GKO_OK;
 }
@@ -1314,16 +1356,19 @@ __global__ void lowprec_kernel(int64_t n, const int32_t* __restrict__ row_ptr, c
     }
 }
 
-// rl = float(r / nr); d = p = s = 0
+// rl = float(r / nr); d = p = s = 0; with a preconditioner u = dinv rl
 __global__ void inner_init_kernel(int64_t n, const double* __restrict__ r, double nr, float* __restrict__ rl,
-                                  float* __restrict__ d, float* __restrict__ p, float* __restrict__ s)
+                                  float* __restrict__ d, float* __restrict__ p, float* __restrict__ s,
+                                  const float* __restrict__ dinv, float* __restrict__ u)
 {
     for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
          i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-        rl[i] = __double2float_rn(r[i] / nr);
+        const float v = __double2float_rn(r[i] / nr);
+        rl[i] = v;
         d[i] = 0.0f;
         p[i] = 0.0f;
         s[i] = 0.0f;
+        if (dinv) u[i] = dinv[i] * v;
     }
 }
 
@@ -1354,7 +1399,7 @@ static cudaError_t inner_spmv(const gko_matrix* A, const V* val, SegScratchT<flo
 }
 
 int cg_mixed_solve(gko_matrix* A, int inner, const double* b, double* x, double tol, int maxit_outer,
-                   double inner_tol, int inner_maxit, cudaStream_t st, gko_solve_info* info)
+                   double inner_tol, int inner_maxit, cudaStream_t st, gko_solve_info* info, int precond)
 {
     const int64_t n = A->n_rows, nnz = A->nnz;
     if (n == 0) {
@@ -1381,7 +1426,7 @@ int cg_mixed_solve(gko_matrix* A, int inner, const double* b, double* x, double 
 
     Workspace ws(st);
     double *r, *part;
-    float *rl, *d, *p, *sv, *w;
+    float *rl, *d, *p, *sv, *w, *dinv = nullptr, *u = nullptr;
     SolverState *ds, *di;
     GKO_TRY(ws.get(&r, n));
     GKO_TRY(ws.get(&part, 2 * std::max(kRedBlocks, use_ell ? lp_ell_grid(A) : 0)));
@@ -1392,6 +1437,29 @@ int cg_mixed_solve(gko_matrix* A, int inner, const double* b, double* x, double 
     GKO_TRY(ws.get(&w, n));
     GKO_TRY(ws.get(&ds, 1));
     GKO_TRY(ws.get(&di, 1));
+    const bool jac = precond == GKO_PRECOND_JACOBI;
+    if (jac) {  // M = diag(A_lo)
+        int32_t* bad;
+        GKO_TRY(ws.get(&dinv, n));
+        GKO_TRY(ws.get(&u, n));
+        GKO_TRY(ws.get(&bad, 1));
+        GKO_CUDA(cudaMemsetAsync(bad, 0, sizeof(int32_t), st));
+        if (bf16)
+            diag_lo_inv_kernel<1><<<red_grid(n), kRedThreads, 0, st>>>(n, A->csr.row_ptr, A->csr.col, nullptr,
+                                                                        A->val_bf16, dinv, bad);
+        else
+            diag_lo_inv_kernel<0><<<red_grid(n), kRedThreads, 0, st>>>(n, A->csr.row_ptr, A->csr.col, A->val_f32,
+                                                                        nullptr, dinv, bad);
+        int32_t hbad = 0;
+        GKO_CUDA(cudaMemcpyAsync(&hbad, bad, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        GKO_CUDA(cudaStreamSynchronize(st));
+        if (hbad) {
+            fill_info(info, 0, 0, -1.0, GKO_ERR_BREAKDOWN);
+            set_error("Jacobi preconditioner: a diagonal entry of the rounded matrix is zero or not stored");
+            return GKO_ERR_BREAKDOWN;
+        }
+    }
+    float* ux = jac ? u : rl;  // the vector the product gathers (u = M^-1 rl, or rl itself)
     const int64_t tiles = std::max<int64_t>(1, (nnz + SegShape<kSegP>::kTile - 1) / SegShape<kSegP>::kTile);
     SegScratchT<float> sc;
     GKO_TRY(ws.get(&sc.tail_val, tiles));
@@ -1418,25 +1486,25 @@ int cg_mixed_solve(gko_matrix* A, int inner, const double* b, double* x, double 
     // A_lo when its padding is small, else row-block CSR; otherwise the
     // load-balanced product + one dot kernel), then
     // p = rl + beta p, s = w + beta s, d += alpha p, rl -= alpha s
-    const bool fused = nnz > 0 && rowblock_preferred(A);
+    const bool fused = nnz > 0 && rowblock_preferred(A) && !jac;
     GraphHolder gh;
     GKO_TRY(build_while_graph(&gh, [&](cudaGraphConditionalHandle h, cudaStream_t cs) -> int {
         const Cg1Reduce red{di, part, A->d_err, h};
         cudaError_t e;
         if (use_ell) {
-            e = lp_ell_cg1(A, bf16, rl, w, red, cs);
+            e = lp_ell_cg1(A, bf16, ux, rl, w, red, cs);
         } else if (fused) {
             e = bf16 ? rowblock_cg1_bf16(A, A->val_bf16, rl, w, red, cs) : rowblock_cg1_f32(A, A->val_f32, rl, w, red, cs);
         } else {
-            e = bf16 ? inner_spmv<__nv_bfloat16>(A, reinterpret_cast<const __nv_bfloat16*>(A->val_bf16), sc, rl, w, cs)
-                     : inner_spmv<float>(A, A->val_f32, sc, rl, w, cs);
+            e = bf16 ? inner_spmv<__nv_bfloat16>(A, reinterpret_cast<const __nv_bfloat16*>(A->val_bf16), sc, ux, w, cs)
+                     : inner_spmv<float>(A, A->val_f32, sc, ux, w, cs);
             if (e == cudaSuccess) {
-                cg1_dots_kernel<float><<<grid, kRedThreads, 0, cs>>>(n, rl, w, red);
+                cg1_dots_kernel<float><<<grid, kRedThreads, 0, cs>>>(n, ux, rl, w, red);
                 e = cudaGetLastError();
             }
         }
         if (e != cudaSuccess) return cuda_fail(e, "inner CG product launch");
-        launch_cg1_update<float>(n, d, rl, p, sv, w, di, cs);
+        launch_cg1_update<float>(n, d, rl, p, sv, w, di, cs, dinv, u);
         GKO_CUDA(cudaGetLastError());
         return GKO_OK;
     }));
@@ -1461,7 +1529,7 @@ int cg_mixed_solve(gko_matrix* A, int inner, const double* b, double* x, double 
         }
         if (o == maxit_outer) break;
         outer = o + 1;
-        inner_init_kernel<<<grid, kRedThreads, 0, st>>>(n, r, nr, rl, d, p, sv);
+        inner_init_kernel<<<grid, kRedThreads, 0, st>>>(n, r, nr, rl, d, p, sv, dinv, u);
         SolverState is = {};
         is.tol = inner_tol;
         is.rel_inner = 1;

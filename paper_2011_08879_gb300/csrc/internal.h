@@ -220,7 +220,8 @@ int cg_solve(const gko_matrix* A, int fmt, const double* b, double* x, double to
              cudaStream_t st, gko_solve_info* info);
 int lp_ell_prepare(gko_matrix* A, bool bf16, cudaStream_t st, bool* usable);
 void lp_ell_free(gko_matrix* A);
-cudaError_t lp_ell_cg1(const gko_matrix* A, bool bf16, const float* r, float* w, Cg1Reduce red, cudaStream_t st);
+cudaError_t lp_ell_cg1(const gko_matrix* A, bool bf16, const float* r, const float* rd, float* w, Cg1Reduce red,
+                       cudaStream_t st);
 int lp_ell_grid(const gko_matrix* A);
 int pcg_jacobi_solve(const gko_matrix* A, int fmt, const double* b, double* x, double tol, int maxit,
                      cudaStream_t st, gko_solve_info* info);
@@ -233,7 +234,7 @@ int gmres_solve(const gko_matrix* A, int fmt, const double* b, double* x, double
 int cg1_solve(const gko_matrix* A, int fmt, const double* b, double* x, double tol, int maxit,
               cudaStream_t st, gko_solve_info* info);
 int cg_mixed_solve(gko_matrix* A, int inner, const double* b, double* x, double tol, int maxit_outer,
-                   double inner_tol, int inner_maxit, cudaStream_t st, gko_solve_info* info);
+                   double inner_tol, int inner_maxit, cudaStream_t st, gko_solve_info* info, int precond);
 
 // selector (selector.cu)
 int features_compute(const gko_matrix* A, double* out_host, cudaStream_t st);

@@ -13,7 +13,9 @@
 // and indices with one vector load each (128-bit for FP32 values / int32
 // indices, 64-bit for BF16 / int16), marked evict-first (the matrix is read
 // once per step; the solver's vectors stay in L2).  The thread then adds
-// r_i^2 and w_i r_i of its rows to the step's two dots; one grid reduction
+// rd_i r_i and w_i r_i of its rows to the step's two dots (rd = r without a
+// preconditioner; with one, r is the preconditioned residual u = M^-1 rd
+// and rd the residual); one grid reduction
 // (block partials, then a one-block kernel that sums them in block order)
 // ends in the CG scalar step.  A ticket atomic and fence at the end of every
 // block of this short kernel would cost more than that extra launch.
@@ -200,7 +202,8 @@ constexpr int lp_rows() { return 16 / static_cast<int>(sizeof(V)); }
 template <typename V, typename I, int KC>
 __global__ void __launch_bounds__(kLpThreads)
     lp_ell_cg1_kernel(int64_t n, int64_t n_pad, int K, const I* __restrict__ col, const V* __restrict__ val,
-                      const float* __restrict__ r, float* __restrict__ w, double* __restrict__ part)
+                      const float* __restrict__ r, const float* __restrict__ rd, float* __restrict__ w,
+                      double* __restrict__ part)
 {
     constexpr int G = lp_rows<V>();
     if (KC > 0) K = KC;
@@ -233,8 +236,9 @@ __global__ void __launch_bounds__(kLpThreads)
 #pragma unroll
             for (int h = 0; h < G; h += 4) {
                 const float4 rr = *reinterpret_cast<const float4*>(r + row0 + h);
+                const float4 rv = *reinterpret_cast<const float4*>(rd + row0 + h);
                 *reinterpret_cast<float4*>(w + row0 + h) = make_float4(a[h], a[h + 1], a[h + 2], a[h + 3]);
-                g = fmaf(rr.x, rr.x, fmaf(rr.y, rr.y, fmaf(rr.z, rr.z, fmaf(rr.w, rr.w, g))));
+                g = fmaf(rv.x, rr.x, fmaf(rv.y, rr.y, fmaf(rv.z, rr.z, fmaf(rv.w, rr.w, g))));
                 d = fmaf(a[h], rr.x, fmaf(a[h + 1], rr.y, fmaf(a[h + 2], rr.z, fmaf(a[h + 3], rr.w, d))));
             }
         } else {
@@ -243,7 +247,7 @@ __global__ void __launch_bounds__(kLpThreads)
                 if (row0 + u < n) {
                     const float ri = r[row0 + u];
                     w[row0 + u] = a[u];
-                    g = fmaf(ri, ri, g);
+                    g = fmaf(rd[row0 + u], ri, g);
                     d = fmaf(a[u], ri, d);
                 }
         }
@@ -309,8 +313,8 @@ constexpr int kLpStageBytes = 48 * 1024;
 template <typename V, typename I, int KC>
 __global__ void __launch_bounds__(kLpThreads, 2)
     lp_ell_tma_cg1_kernel(int64_t n, int64_t n_pad, int K, int R, const I* __restrict__ col,
-                          const V* __restrict__ val, const float* __restrict__ r, float* __restrict__ w,
-                          uint32_t* err, Cg1Reduce red)
+                          const V* __restrict__ val, const float* __restrict__ r, const float* __restrict__ rd,
+                          float* __restrict__ w, uint32_t* err, Cg1Reduce red)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ uint64_t bar[2];
@@ -401,8 +405,9 @@ __global__ void __launch_bounds__(kLpThreads, 2)
             }
             if (i0 + 4 <= n) {
                 const float4 rr = *reinterpret_cast<const float4*>(r + i0);
+                const float4 rv = *reinterpret_cast<const float4*>(rd + i0);
                 *reinterpret_cast<float4*>(w + i0) = make_float4(a[0], a[1], a[2], a[3]);
-                g = fmaf(rr.x, rr.x, fmaf(rr.y, rr.y, fmaf(rr.z, rr.z, fmaf(rr.w, rr.w, g))));
+                g = fmaf(rv.x, rr.x, fmaf(rv.y, rr.y, fmaf(rv.z, rr.z, fmaf(rv.w, rr.w, g))));
                 d = fmaf(a[0], rr.x, fmaf(a[1], rr.y, fmaf(a[2], rr.z, fmaf(a[3], rr.w, d))));
             } else {
 #pragma unroll
@@ -410,7 +415,7 @@ __global__ void __launch_bounds__(kLpThreads, 2)
                     if (i0 + u < n) {
                         const float ri = r[i0 + u];
                         w[i0 + u] = a[u];
-                        g = fmaf(ri, ri, g);
+                        g = fmaf(rd[i0 + u], ri, g);
                         d = fmaf(a[u], ri, d);
                     }
             }
@@ -429,8 +434,8 @@ __global__ void __launch_bounds__(kLpThreads, 2)
 }
 
 template <typename V, typename I, int KC>
-static cudaError_t launch_lp_tma_k(const gko_matrix* A, const V* val, const float* r, float* w, Cg1Reduce red,
-                                   int R, int grid, cudaStream_t st)
+static cudaError_t launch_lp_tma_k(const gko_matrix* A, const V* val, const float* r, const float* rd, float* w,
+                                   Cg1Reduce red, int R, int grid, cudaStream_t st)
 {
     const LowPrecEll& E = A->lp_ell;
     static bool attr = false;
@@ -441,13 +446,13 @@ static cudaError_t launch_lp_tma_k(const gko_matrix* A, const V* val, const floa
         attr = true;
     }
     lp_ell_tma_cg1_kernel<V, I, KC><<<grid, kLpThreads, 2 * kLpStageBytes, st>>>(
-        A->n_rows, E.n_pad, static_cast<int>(E.K), R, static_cast<const I*>(E.col), val, r, w, A->d_err, red);
+        A->n_rows, E.n_pad, static_cast<int>(E.K), R, static_cast<const I*>(E.col), val, r, rd, w, A->d_err, red);
     return cudaGetLastError();
 }
 
 template <typename V, typename I>
-static cudaError_t launch_lp_tma(const gko_matrix* A, const V* val, const float* r, float* w, Cg1Reduce red,
-                                 cudaStream_t st)
+static cudaError_t launch_lp_tma(const gko_matrix* A, const V* val, const float* r, const float* rd, float* w,
+                                 Cg1Reduce red, cudaStream_t st)
 {
     const LowPrecEll& E = A->lp_ell;
     const int K = static_cast<int>(E.K);
@@ -458,17 +463,17 @@ static cudaError_t launch_lp_tma(const gko_matrix* A, const V* val, const float*
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int grid = static_cast<int>(std::min<int64_t>(n_stages, 2 * std::max(sms, 1)));
     switch (K) {
-        case 5: return launch_lp_tma_k<V, I, 5>(A, val, r, w, red, R, grid, st);
-        case 7: return launch_lp_tma_k<V, I, 7>(A, val, r, w, red, R, grid, st);
-        default: return launch_lp_tma_k<V, I, 0>(A, val, r, w, red, R, grid, st);
+        case 5: return launch_lp_tma_k<V, I, 5>(A, val, r, rd, w, red, R, grid, st);
+        case 7: return launch_lp_tma_k<V, I, 7>(A, val, r, rd, w, red, R, grid, st);
+        default: return launch_lp_tma_k<V, I, 0>(A, val, r, rd, w, red, R, grid, st);
     }
 }
 
 int lp_ell_grid(const gko_matrix* A);
 
 template <typename V, typename I>
-static cudaError_t launch_lp(const gko_matrix* A, const V* val, const float* r, float* w, Cg1Reduce red,
-                             cudaStream_t st)
+static cudaError_t launch_lp(const gko_matrix* A, const V* val, const float* r, const float* rd, float* w,
+                             Cg1Reduce red, cudaStream_t st)
 {
     const LowPrecEll& E = A->lp_ell;
     const int64_t groups = E.n_pad / lp_rows<V>();
@@ -478,7 +483,7 @@ static cudaError_t launch_lp(const gko_matrix* A, const V* val, const float* r, 
     switch (K) {
 #define GKO_LP(KC)                                                                                         \
     case KC:                                                                                               \
-        lp_ell_cg1_kernel<V, I, KC><<<grid, kLpThreads, 0, st>>>(A->n_rows, E.n_pad, K, c, val, r, w, red.part); \
+        lp_ell_cg1_kernel<V, I, KC><<<grid, kLpThreads, 0, st>>>(A->n_rows, E.n_pad, K, c, val, r, rd, w, red.part); \
         break
         GKO_LP(1);
         GKO_LP(2);
@@ -490,13 +495,14 @@ static cudaError_t launch_lp(const gko_matrix* A, const V* val, const float* r, 
         GKO_LP(8);
 #undef GKO_LP
         default:
-            lp_ell_cg1_kernel<V, I, 0><<<grid, kLpThreads, 0, st>>>(A->n_rows, E.n_pad, K, c, val, r, w, red.part);
+            lp_ell_cg1_kernel<V, I, 0><<<grid, kLpThreads, 0, st>>>(A->n_rows, E.n_pad, K, c, val, r, rd, w, red.part);
     }
     cg1_finish_kernel<<<1, kFinishThreads, 0, st>>>(grid, red.part, red);
     return cudaGetLastError();
 }
 
-cudaError_t lp_ell_cg1(const gko_matrix* A, bool bf16, const float* r, float* w, Cg1Reduce red, cudaStream_t st)
+cudaError_t lp_ell_cg1(const gko_matrix* A, bool bf16, const float* r, const float* rd, float* w, Cg1Reduce red,
+                       cudaStream_t st)
 {
     const LowPrecEll& E = A->lp_ell;
     const int K = static_cast<int>(E.K);
@@ -504,16 +510,16 @@ cudaError_t lp_ell_cg1(const gko_matrix* A, bool bf16, const float* r, float* w,
                           : (E.idx16 ? lp_stage_rows<float, int16_t>(K) : lp_stage_rows<float, int32_t>(K)) >= 1024;
     if (tma) {
         if (bf16)
-            return E.idx16 ? launch_lp_tma<uint16_t, int16_t>(A, E.val_bf16, r, w, red, st)
-                           : launch_lp_tma<uint16_t, int32_t>(A, E.val_bf16, r, w, red, st);
-        return E.idx16 ? launch_lp_tma<float, int16_t>(A, E.val_f32, r, w, red, st)
-                       : launch_lp_tma<float, int32_t>(A, E.val_f32, r, w, red, st);
+            return E.idx16 ? launch_lp_tma<uint16_t, int16_t>(A, E.val_bf16, r, rd, w, red, st)
+                           : launch_lp_tma<uint16_t, int32_t>(A, E.val_bf16, r, rd, w, red, st);
+        return E.idx16 ? launch_lp_tma<float, int16_t>(A, E.val_f32, r, rd, w, red, st)
+                       : launch_lp_tma<float, int32_t>(A, E.val_f32, r, rd, w, red, st);
     }
     if (bf16)
-        return E.idx16 ? launch_lp<uint16_t, int16_t>(A, E.val_bf16, r, w, red, st)
-                       : launch_lp<uint16_t, int32_t>(A, E.val_bf16, r, w, red, st);
-    return E.idx16 ? launch_lp<float, int16_t>(A, E.val_f32, r, w, red, st)
-                   : launch_lp<float, int32_t>(A, E.val_f32, r, w, red, st);
+        return E.idx16 ? launch_lp<uint16_t, int16_t>(A, E.val_bf16, r, rd, w, red, st)
+                       : launch_lp<uint16_t, int32_t>(A, E.val_bf16, r, rd, w, red, st);
+    return E.idx16 ? launch_lp<float, int16_t>(A, E.val_f32, r, rd, w, red, st)
+                   : launch_lp<float, int32_t>(A, E.val_f32, r, rd, w, red, st);
 }
 
 // blocks of the product kernel (its reduction needs 2 doubles per block)

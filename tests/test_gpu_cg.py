@@ -298,6 +298,36 @@ def test_mixed_cg_wide_band(gko, dev, orc, prec):
     assert abs(info.outer_iterations - outer_o) <= 2, (info.outer_iterations, outer_o)
 
 
+@pytest.mark.parametrize("prec,case", [("fp32", "scaled"), ("bf16", "diffusion"), ("fp32", "skewed")])
+def test_mixed_cg_jacobi(gko, dev, orc, prec, case):
+    """Jacobi-preconditioned inner solve against the oracle's: outer
+    corrections within 2, both at the FP64 residual; paths: ELL inner copy
+    (scaled / variable-coefficient diffusion) and load-balanced product +
+    dot kernel (skewed rows)."""
+    if case == "skewed":
+        A = _skewed_spd(20000, 33)
+    else:
+        A = syn.diffusion7(32, 1.0, seed=6)
+        if case == "scaled":
+            n = A["n_rows"]
+            s = 10.0 ** (3.0 * syn.uniform01(27, 1, np.arange(n, dtype=np.uint64)))
+            rows = np.repeat(np.arange(n), np.diff(A["row_ptr"]))
+            A = dict(A)
+            A["val"] = A["val"] * s[rows] * s[A["col_idx"]]
+    n = A["n_rows"]
+    xt = syn.vector(n, 30)
+    b = orc.spmv_csr(A, xt)
+    xo, st_o, outer_o, inner_o, res_o = orc.cg_mixed(A, b, prec, tol=1e-10, inner_tol=1e-2, precond="jacobi")
+    assert st_o == 0
+    M = gko.Matrix(A)
+    x = _t(np.zeros(n), dev)
+    info = M.cg_mixed(_t(b, dev), x, inner=prec, tol=1e-10, inner_tol=1e-2, precond="jacobi")
+    assert info.status == 0 and info.rel_residual <= 1e-10
+    assert orc.true_rel_residual(A, b, x.cpu().numpy()) <= 1e-10
+    assert abs(info.outer_iterations - outer_o) <= 2, (info.outer_iterations, outer_o)
+    assert info.iterations <= 1.5 * inner_o + 20, (info.iterations, inner_o)
+
+
 def test_lowprec_copy_matches_oracle_rounding(gko, dev, orc):
     """The mixed solver's rounded matrix is observable through its result on
     a system where one inner solve is exact: A_lo = A when every value is
