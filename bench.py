@@ -214,6 +214,20 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
+def aggregate_replicas(bytes_per_rank, seconds, world, device):
+    """Whole-job throughput of `world` replicas that each moved
+    bytes_per_rank in `seconds`: all ranks' bytes over the slowest rank's
+    time (max over ranks through the initialised process group when
+    world > 1).  Returns (GB/s, max seconds)."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([seconds], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        seconds = float(t.item())
+    return bytes_per_rank * world / seconds / 1e9, seconds
+
+
 def run_gpu(args):
     import torch
     rank, world, local = dist_env()
@@ -297,11 +311,7 @@ def run_gpu(args):
         per_case.setdefault(k, []).append(e0.elapsed_time(e1) * 1e-3)
     kern_s = sum(sum(v) for v in per_case.values())
     bytes_tot = sum(c["bytes"] for c in cases) * args.steps
-    if world > 1:
-        t = torch.tensor([kern_s], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        kern_s = float(t.item())
-    value = bytes_tot * world / kern_s / 1e9
+    value, kern_s = aggregate_replicas(bytes_tot, kern_s, world, dev)
     peak, peak_kind = measured_peaks()
     detail = {}
     for c in cases:

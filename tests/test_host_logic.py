@@ -1,0 +1,90 @@
+"""Host-side logic on the CPU: the replica aggregation of the benchmark
+across two gloo ranks, the benchmark's byte model, and the selector's
+targets, default-kernel rule and regret."""
+import os
+import socket
+
+import numpy as np
+import pytest
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def _rank_main(rank, world, port, seconds, q):
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    sys.path.insert(0, root)
+    import torch.distributed as dist
+    import bench
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        q.put((rank,) + bench.aggregate_replicas(1e9, seconds[rank], world, "cpu"))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_replica_aggregation_two_gloo_ranks():
+    """Two ranks, 1 GB each in 0.5 s and 0.25 s: both report 2 GB over the
+    slower rank's 0.5 s = 4 GB/s."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank_main, args=(r, 2, port, (0.5, 0.25), q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    out = sorted(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for rank, gbs, secs in out:
+        assert secs == 0.5 and abs(gbs - 4.0) < 1e-12, (rank, gbs, secs)
+
+
+def test_single_rank_aggregation():
+    import bench
+    assert bench.aggregate_replicas(3e9, 1.5, 1, "cpu") == (2.0, 1.5)
+
+
+def test_spmv_byte_model():
+    """values + indices + x + y, padding included (β = 0)."""
+    import bench
+    n, m, nnz = 1000, 900, 5000
+    assert bench.spmv_bytes("csr", None, n, m, nnz) == 12 * nnz + 4 * (n + 1) + 8 * m + 8 * n
+    assert bench.spmv_bytes("coo", None, n, m, nnz) == 16 * nnz + 8 * m + 8 * n
+    ell = [1, n, m, nnz, 7, 1024, 7 * 1024, 0]
+    assert bench.spmv_bytes("ell", ell, n, m, nnz) == 12 * 7 * 1024 + 8 * m + 8 * n
+    sellp = [1, n, m, nnz, 64, 16, 6000, 1]
+    assert bench.spmv_bytes("sellp", sellp, n, m, nnz) == 12 * 6000 + 4 * (2 * 16 + 1) + 8 * m + 8 * n
+    hyb = [1, n, m, nnz, 4, 1024, 900, 0]
+    assert bench.spmv_bytes("hybrid", hyb, n, m, nnz) == 12 * 4 * 1024 + 16 * 900 + 8 * m + 8 * n
+
+
+def test_selector_targets_regret_and_default_rule(gko):
+    from paper_2011_08879_gb300 import selector as sel
+    from paper_2011_08879_gb300 import binding as B
+    T = np.array([2e-4, 1e-4, np.nan, 1e-1] + [np.nan] * (len(sel.CANDIDATES) - 4))
+    y, m = sel.targets(T)
+    assert m[:4].tolist() == [1, 1, 0, 1] and m[4:].sum() == 0
+    assert abs(y[0] - np.log10(2.0)) < 1e-6 and y[1] == 0.0
+    assert y[3] == sel.TARGET_CAP  # 1000x slower, capped
+    TT = np.array([[1.0, 2.0, np.nan], [4.0, 1.0, 3.0]])
+    r = sel.regret(TT, np.array([1, 2]))
+    assert np.allclose(r, [1.0, 2.0])
+    r = sel.regret(TT, np.array([2, 1]))  # an unmeasured choice counts as the worst measured time
+    assert np.allclose(r, [1.0, 0.0])
+    names = sel.CLASS_NAMES
+    F = np.zeros((4, 12))
+    F[:, 2] = [7.0, 16.0, 27.0, 20.0]   # mean row length
+    F[:, 4] = [7.0, 16.0, 27.0, 20000]  # max row length
+    got = [names[c] for c in sel.default_csr_class(F)]
+    want = ["csr/%d" % c for c in (B.CFG_CSR_SUBWARP_1, B.CFG_CSR_ROWBLOCK, B.CFG_CSR_SUBWARP_4, B.CFG_CSR_BINNED)]
+    assert got == want
