@@ -102,15 +102,21 @@ def measured_peaks():
 
 
 def kernel_source_hash():
-    """Hash of the CUDA sources (the counters of a capture are valid only for
-    the kernels they were taken on)."""
+    """Hash of the CUDA sources with comments and whitespace removed (the
+    counters of a capture are valid only for the code they were taken on;
+    editing a comment does not change that code)."""
     import glob
     import hashlib
+    import re
     h = hashlib.sha256()
     for p in sorted(glob.glob(os.path.join(ROOT, "paper_2011_08879_gb300", "csrc", "*"))):
         if p.endswith((".cu", ".cuh", ".h")):
-            with open(p, "rb") as f:
-                h.update(f.read())
+            with open(p, encoding="utf-8") as f:
+                src = f.read()
+            src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+            src = re.sub(r"//[^\n]*", " ", src)
+            h.update(os.path.basename(p).encode())
+            h.update(" ".join(src.split()).encode())
     return h.hexdigest()[:16]
 
 

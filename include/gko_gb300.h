@@ -78,7 +78,11 @@ enum { GKO_F64 = 0, GKO_F32 = 1, GKO_BF16 = 2 };
 enum { GKO_PRECOND_NONE = 0, GKO_PRECOND_JACOBI = 1 };
 
 /* Kernel configurations accepted by gko_spmv_config (the candidates of the
- * exhaustive sweep / selector).  GKO_CFG_DEFAULT lets the library choose. */
+ * exhaustive sweep / selector).  GKO_CFG_DEFAULT lets the library choose;
+ * for CSR it picks, from the row-length statistics of the handle: rows of
+ * close length (max <= 2 mean + 16 and max <= 128) one lane per row when at
+ * most 8 long, the staged row blocks up to 20, four lanes per row beyond;
+ * skewed rows the binned kernel. */
 enum {
     GKO_CFG_DEFAULT = 0,
     GKO_CFG_CSR_SUBWARP_1 = 1,  /* CSR, classical: subwarp of 1,2,4,8,16,32 lanes per row */
