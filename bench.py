@@ -85,11 +85,61 @@ def csr_default_launches(A):
     return 1
 
 
-def kernel_launches(fmt, nnz_or_coo, tile=3840, csr_launches=1):
+def kernel_launches(fmt, nnz_or_coo, tile=2816, csr_launches=1):
     """Launches of this library per SpMV (load-balanced kernels add a fix-up
     launch when they span more than one tile)."""
     seg = 1 + (1 if nnz_or_coo > tile else 0)
     return {"csr": csr_launches, "coo": seg, "ell": 1, "sellp": 1, "hybrid": 1 + (seg if nnz_or_coo else 0)}[fmt]
+
+
+def kernel_family(fmt, matrix, coo_part):
+    """Kernel that carries a (matrix, format) SpMV: COO, ELL and SELL-P have
+    one kernel each; a hybrid without COO part runs the ELL kernel alone;
+    the default CSR kernel follows the row lengths (one per sweep matrix)."""
+    if fmt == "hybrid" and not coo_part:
+        return "ell"
+    if fmt == "csr":
+        return "csr:" + matrix
+    return fmt
+
+
+FAMILY_LABEL = {
+    "coo": "seg_spmv_kernel<11> (COO, equal-nnz tiles) + fix-up",
+    "ell": "ell_kernel",
+    "sellp": "sellp_kernel",
+    "hybrid": "ell_kernel + seg_spmv_kernel<11> (COO part, accumulate) + fix-up",
+}
+
+
+def dominant_roofline(cases, seconds, traffic, peak, peak_kind):
+    """Roofline of the kernel with the largest share of the step's device
+    time.  cases: dicts with matrix, fmt, bytes, family; seconds: per case,
+    the list of its timed launches; traffic: DRAM bytes per launch by
+    'matrix/fmt' (ncu).  achieved = algorithmic bytes per launch / mean
+    launch time over all launches of that kernel in the step."""
+    fam_time, fam_cases = {}, {}
+    for c in cases:
+        fam_time[c["family"]] = fam_time.get(c["family"], 0.0) + sum(seconds[(c["matrix"], c["fmt"])])
+        fam_cases.setdefault(c["family"], []).append(c)
+    total = sum(fam_time.values())
+    fam = max(fam_time, key=fam_time.get)
+    cs = fam_cases[fam]
+    n_launch = sum(len(seconds[(c["matrix"], c["fmt"])]) for c in cs)
+    bytes_per_launch = sum(c["bytes"] * len(seconds[(c["matrix"], c["fmt"])]) for c in cs) / n_launch
+    achieved = bytes_per_launch / (fam_time[fam] / n_launch) / 1e9
+    tr = [traffic.get("%s/%s" % (c["matrix"], c["fmt"])) for c in cs]
+    tr_launch = (sum(t * len(seconds[(c["matrix"], c["fmt"])]) for t, c in zip(tr, cs)) / n_launch
+                 if tr and all(t is not None for t in tr) else None)
+    slow = max(cases, key=lambda c: statistics.mean(seconds[(c["matrix"], c["fmt"])]))
+    slow_t = statistics.mean(seconds[(slow["matrix"], slow["fmt"])])
+    return {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "traffic": None if tr_launch is None else round(tr_launch),
+            "kernel": FAMILY_LABEL.get(fam, "default CSR kernel on " + fam[4:]), "peak_kind": peak_kind,
+            "cases": ["%s/%s" % (c["matrix"], c["fmt"]) for c in cs], "bytes_per_launch": round(bytes_per_launch),
+            "share_of_step": round(fam_time[fam] / total, 4),
+            "slowest_case": {"case": "%s/%s" % (slow["matrix"], slow["fmt"]),
+                             "GBs": round(slow["bytes"] / slow_t / 1e9, 1),
+                             "frac": round(slow["bytes"] / slow_t / 1e9 / peak, 4)}}
 
 
 def measured_peaks():
@@ -276,7 +326,7 @@ def run_gpu(args):
             info = M.info(f)
             nb = spmv_bytes(f, info, n, m, nnz)
             coo_part = nnz if f in ("csr", "coo") else (info[6] if f == "hybrid" else 0)
-            cases.append(dict(matrix=name, fmt=f, bytes=nb, flops=2 * nnz,
+            cases.append(dict(matrix=name, fmt=f, bytes=nb, flops=2 * nnz, family=kernel_family(f, name, coo_part),
                               launches=kernel_launches(f, coo_part, csr_launches=csr_default_launches(A))))
     xs = {name: torch.from_numpy(syn.vector(mats[name]["n_cols"], 7)).to(dev) for name in sweep}
     ys = {name: torch.empty(mats[name]["n_rows"], dtype=torch.float64, device=dev) for name in sweep}
@@ -326,14 +376,7 @@ def run_gpu(args):
         detail["%s/%s" % (c["matrix"], c["fmt"])] = {
             "GBs": round(c["bytes"] / med / 1e9, 1), "pct_hbm": round(100 * c["bytes"] / med / 1e9 / peak, 1),
             "GFLOPs": round(c["flops"] / med / 1e9, 1), "us": round(med * 1e6, 1)}
-    dom = max(cases, key=lambda c: sum(per_case[(c["matrix"], c["fmt"])]))
-    dts = per_case[(dom["matrix"], dom["fmt"])]
-    achieved = dom["bytes"] / (sum(dts) / len(dts)) / 1e9
-    traffic = profile_traffic().get("%s/%s" % (dom["matrix"], dom["fmt"]))
-    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": traffic,
-                "kernel": "%s SpMV on %s" % (dom["fmt"], dom["matrix"]), "peak_kind": peak_kind,
-                "bytes_per_launch": dom["bytes"]}
+    roofline = dominant_roofline(cases, per_case, profile_traffic(), peak, peak_kind)
 
     # end to end through gko_spmv_host with pinned host buffers
     e2e = None

@@ -68,6 +68,51 @@ def test_spmv_byte_model():
     assert bench.spmv_bytes("hybrid", hyb, n, m, nnz) == 12 * 4 * 1024 + 16 * 900 + 8 * m + 8 * n
 
 
+def test_dominant_kernel_roofline():
+    """The roofline names the kernel with the largest share of the step:
+    launches of one kernel on different matrices are pooled, a hybrid
+    without COO part counts as the ELL kernel, and achieved is bytes per
+    launch over the mean launch time."""
+    import bench
+    fam = bench.kernel_family
+    assert fam("hybrid", "a", 0) == "ell" and fam("hybrid", "a", 5) == "hybrid"
+    assert fam("csr", "a", 9) == "csr:a" and fam("coo", "a", 9) == "coo"
+    cases = [dict(matrix="a", fmt="coo", bytes=4e8), dict(matrix="b", fmt="coo", bytes=2e8),
+             dict(matrix="b", fmt="hybrid", bytes=3e8), dict(matrix="a", fmt="ell", bytes=3e8),
+             dict(matrix="a", fmt="hybrid", bytes=3e8)]
+    coo_part = {("b", "hybrid"): 7, ("a", "hybrid"): 0}
+    for c in cases:
+        c["family"] = fam(c["fmt"], c["matrix"], coo_part.get((c["matrix"], c["fmt"]), 1))
+    # the single slowest case is the hybrid (0.5 ms), the busiest kernel is COO (0.4 + 0.3 ms)
+    sec = {("a", "coo"): [4e-4, 4e-4], ("b", "coo"): [3e-4, 3e-4], ("b", "hybrid"): [5e-4, 5e-4],
+           ("a", "ell"): [1e-4, 1e-4], ("a", "hybrid"): [1e-4, 1e-4]}
+    traffic = {"a/coo": 4.4e8, "b/coo": 2.2e8}
+    r = bench.dominant_roofline(cases, sec, traffic, 6000.0, "measured")
+    assert r["cases"] == ["a/coo", "b/coo"]
+    assert r["bytes_per_launch"] == 3e8
+    assert r["achieved"] == pytest.approx(3e8 / 3.5e-4 / 1e9, rel=1e-3)
+    assert r["frac"] == pytest.approx(r["achieved"] / 6000.0, rel=1e-3)
+    assert r["traffic"] == pytest.approx(3.3e8)
+    assert r["share_of_step"] == pytest.approx(14e-4 / 28e-4)
+    assert r["slowest_case"]["case"] == "b/hybrid"
+    # a kernel whose launches were not all captured has no traffic
+    r = bench.dominant_roofline(cases, sec, {"a/coo": 4.4e8}, 6000.0, "measured")
+    assert r["traffic"] is None
+    # the ELL kernel (plain ELL and the hybrid without COO part) takes over when it dominates
+    sec[("a", "ell")] = [9e-4, 9e-4]
+    r = bench.dominant_roofline(cases, sec, traffic, 6000.0, "measured")
+    assert r["cases"] == ["a/ell", "a/hybrid"] and r["kernel"] == "ell_kernel"
+
+
+def test_launch_count_model():
+    """One launch per SpMV, plus the fix-up of the equal-nnz kernel once the
+    entries span more than one tile of 256 x 11."""
+    import bench
+    assert bench.kernel_launches("coo", 2816) == 1 and bench.kernel_launches("coo", 2817) == 2
+    assert bench.kernel_launches("hybrid", 0) == 1 and bench.kernel_launches("hybrid", 10 ** 6) == 3
+    assert bench.kernel_launches("csr", 10 ** 6) == 1 and bench.kernel_launches("ell", 10 ** 6) == 1
+
+
 def test_selector_targets_regret_and_default_rule(gko):
     from paper_2011_08879_gb300 import selector as sel
     from paper_2011_08879_gb300 import binding as B
