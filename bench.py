@@ -85,7 +85,7 @@ def csr_default_launches(A):
     return 1
 
 
-def kernel_launches(fmt, nnz_or_coo, tile=704, csr_launches=1):
+def kernel_launches(fmt, nnz_or_coo, tile=2816, csr_launches=1):
     """Launches of this library per SpMV (load-balanced kernels add a fix-up
     launch when they span more than one tile)."""
     seg = 1 + (1 if nnz_or_coo > tile else 0)

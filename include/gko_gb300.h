@@ -222,8 +222,7 @@ int gko_spmm(const gko_matrix* A, int64_t k, const double* x, int64_t ldx, doubl
  * arrays row[nnz], col[nnz], val[nnz] (COO sorted by (row, col), indices in
  * range; not validated), x[n_cols], y[n_rows].  row, col and val must be
  * 16-byte aligned; they are not read past nnz.  beta == 0: y is not read.
- * Same load-balanced kernel and accuracy as gko_spmv(GKO_FMT_COO, ...), run
- * with tiles of 256 threads x 11 entries (gko_spmv: 64 x 11).
+ * Same kernel and accuracy as gko_spmv(GKO_FMT_COO, ...).
  *
  * Scratch: the carries of rows that cross tiles live in a fixed device
  * array inside the library (GKO_NOALLOC_MAX_TILES tiles of 2816 entries,

@@ -58,7 +58,6 @@ inline int64_t padded_len(int64_t n) { return (n + 15) / 16 * 16 + 16; }
 
 constexpr int kSegP = 15;     // entries per thread of the load-balanced CSR kernel (and thr_row)
 constexpr int kSegPCoo = 11;  // entries per thread of the load-balanced COO kernel
-constexpr int kSegThreadsCoo = 64;  // threads per CTA (and per tile) of the load-balanced COO kernel
 
 // ------------------------------------------------------------ the handle
 
@@ -171,7 +170,7 @@ namespace gko {
 // Launchers exported by the kernel translation units.  All asynchronous on
 // the given stream; they validate nothing (the C-ABI layer does).
 int csr_analyse(gko_matrix* A, cudaStream_t st);
-int seg_alloc(SegArrays* s, int64_t nnz, int P, int threads);
+int seg_alloc(SegArrays* s, int64_t nnz, int P);
 void seg_free(SegArrays* s);
 int spmv_csr(const gko_matrix* A, int config, const double* x, double* y, double alpha, double beta,
              cudaStream_t st);

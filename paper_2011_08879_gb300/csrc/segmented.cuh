@@ -6,10 +6,9 @@
 // this kernel is built to issue close to one FP64 instruction per stored
 // entry whatever the row lengths are:
 //
-//  * the stored entries are cut into tiles of TILE = NT * P consecutive
-//    entries; a persistent grid of CTAs of NT threads (512 threads per SM:
-//    2 CTAs of 256 for CSR, 8 CTAs of 64 for COO) walks the tiles round
-//    robin with two shared-memory stages: while one tile is
+//  * the stored entries are cut into tiles of TILE = 256 * P consecutive
+//    entries; a persistent grid (2 CTAs of 256 threads per SM) walks the
+//    tiles round robin with two shared-memory stages: while one tile is
 //    summed, the next one's values, column indices and row pointers (COO:
 //    row indices) stream in through 1-D bulk copies (TMA) completing on an
 //    mbarrier;
@@ -34,9 +33,8 @@
 
 namespace gko {
 
-constexpr int kSegThreads = 256;        // threads per CTA (= per tile) unless a launch picks NT
-constexpr int kSegThreadsPerSm = 512;   // resident threads per SM (registers, shared memory)
-constexpr int kSegCtasPerSm = kSegThreadsPerSm / kSegThreads;
+constexpr int kSegThreads = 256;
+constexpr int kSegCtasPerSm = 2;
 
 // Per-tile carries of rows that cross tile boundaries.
 template <typename T>
@@ -49,27 +47,27 @@ struct SegScratchT {
 };
 using SegScratch = SegScratchT<double>;
 
-template <int P, int NT = kSegThreads>
+template <int P>
 struct SegShape {
-    static constexpr int kTile = NT * P;  // a multiple of 8 entries for the P and NT used here
+    static constexpr int kTile = kSegThreads * P;  // a multiple of 8 entries for the P used here
     static constexpr int kBuf = kTile + 8;         // bulk copies move whole 16-byte groups
     static constexpr int kRowStage = 2048;         // CSR row_ptr entries staged per tile
 };
 
 // one pipeline stage: values | column indices | (COO rows or CSR row_ptr)
-template <int P, typename V, bool kCoo, int NT = kSegThreads>
+template <int P, typename V, bool kCoo>
 struct SegStage {
-    static constexpr size_t kVal = SegShape<P, NT>::kBuf * sizeof(V);
-    static constexpr size_t kCol = SegShape<P, NT>::kBuf * sizeof(int32_t);
-    static constexpr size_t kAux = (kCoo ? SegShape<P, NT>::kBuf : SegShape<P, NT>::kRowStage) * sizeof(int32_t);
+    static constexpr size_t kVal = SegShape<P>::kBuf * sizeof(V);
+    static constexpr size_t kCol = SegShape<P>::kBuf * sizeof(int32_t);
+    static constexpr size_t kAux = (kCoo ? SegShape<P>::kBuf : SegShape<P>::kRowStage) * sizeof(int32_t);
     static constexpr size_t kBytes = kVal + kCol + kAux;
     static_assert(kVal % 16 == 0 && kCol % 16 == 0 && kAux % 16 == 0, "16-byte aligned stage parts");
 };
 
-template <int P, typename V, typename T, bool kCoo, int NT = kSegThreads>
+template <int P, typename V, typename T, bool kCoo>
 constexpr size_t seg_smem_bytes()
 {
-    return 2 * SegStage<P, V, kCoo, NT>::kBytes + NT * (sizeof(T) + sizeof(int32_t)) +
+    return 2 * SegStage<P, V, kCoo>::kBytes + kSegThreads * (sizeof(T) + sizeof(int32_t)) +
            8 * (sizeof(T) + sizeof(int32_t)) + 16;
 }
 
@@ -318,24 +316,21 @@ __device__ __forceinline__ SegThreadOut<T> seg_thread(int ls, int le, int t0, in
 // kExactTail (COO only): the arrays end exactly at nnz (caller-owned, not
 // padded), so the last tile bulk-copies only whole 16-byte groups and the
 // threads load the remaining few entries themselves.
-// NT: threads per CTA and per tile (a multiple of 32, at most 256).
-template <int P, typename V, typename T, bool kAlpha, bool kBeta, bool kCoo, bool kSkipEmpty, bool kExactTail = false,
-          int NT = kSegThreads>
-__global__ void __launch_bounds__(NT, kSegThreadsPerSm / NT)
+template <int P, typename V, typename T, bool kAlpha, bool kBeta, bool kCoo, bool kSkipEmpty, bool kExactTail = false>
+__global__ void __launch_bounds__(kSegThreads, kSegCtasPerSm)
     seg_spmv_kernel(int64_t n_rows64, int64_t nnz64, const int32_t* __restrict__ row_ptr,
                     const int32_t* __restrict__ rows, const int32_t* __restrict__ col,
                     const V* __restrict__ val, const int32_t* __restrict__ thr_row, const T* __restrict__ x,
                     T* __restrict__ y, T alpha, T beta, SegScratchT<T> sc, uint32_t* err)
 {
-    using S = SegShape<P, NT>;
-    using G = SegStage<P, V, kCoo, NT>;
+    using S = SegShape<P>;
+    using G = SegStage<P, V, kCoo>;
     static_assert(!kExactTail || kCoo, "exact tails are implemented for COO");
-    static_assert(NT % 32 == 0 && NT <= 256, "whole warps, at most 8 (s_wsum)");
     constexpr int kAlign = 16 / sizeof(V) > 4 ? 16 / sizeof(V) : 4;  // entries per 16-byte group
     extern __shared__ __align__(16) unsigned char smem[];
     T* s_part = reinterpret_cast<T*>(smem + 2 * G::kBytes);
-    int32_t* s_prow = reinterpret_cast<int32_t*>(s_part + NT);
-    T* s_wsum = reinterpret_cast<T*>(s_prow + NT);
+    int32_t* s_prow = reinterpret_cast<int32_t*>(s_part + kSegThreads);
+    T* s_wsum = reinterpret_cast<T*>(s_prow + kSegThreads);
     int32_t* s_wrow = reinterpret_cast<int32_t*>(s_wsum + 8);
     __shared__ uint64_t bar[2];
     __shared__ SegTileInfo info[2];
@@ -393,11 +388,11 @@ __global__ void __launch_bounds__(NT, kSegThreadsPerSm / NT)
     // metadata loads needed to issue `tile` (read early, used later)
     auto meta_a = [&](int tile) -> int32_t {
         if (kCoo) return tile > 0 ? rows[tile * S::kTile - 1] : -1;
-        return thr_row[tile * NT];
+        return thr_row[tile * kSegThreads];
     };
     auto meta_b = [&](int tile) -> int32_t {
         if (kCoo) return rows[tile * S::kTile];
-        return (tile + 1) * S::kTile < nnz ? thr_row[(tile + 1) * NT] : n_rows;
+        return (tile + 1) * S::kTile < nnz ? thr_row[(tile + 1) * kSegThreads] : n_rows;
     };
     auto meta_c = [&](int tile) -> int32_t {
         if (!kCoo) return 0;
@@ -406,7 +401,7 @@ __global__ void __launch_bounds__(NT, kSegThreadsPerSm / NT)
     // start row of this thread's entries in a tile (threads whose first
     // entry exists only: thr_row has ceil(nnz / P) entries)
     auto start_row = [&](int tile) -> int32_t {
-        const int g = tile * NT + tid;
+        const int g = tile * kSegThreads + tid;
         return (!kCoo && tile < n_tiles && static_cast<int64_t>(g) * P < nnz) ? thr_row[g] : 0;
     };
 
@@ -436,7 +431,7 @@ __global__ void __launch_bounds__(NT, kSegThreadsPerSm / NT)
         if (kExactTail) {  // entries past the last whole 16-byte group (last tile only)
             const int tx0 = info[st].t0;
             const int cx = min(tx0 + S::kTile, nnz) - tx0;
-            for (int i = cx / kAlign * kAlign + tid; i < cx; i += NT) {
+            for (int i = cx / kAlign * kAlign + tid; i < cx; i += kSegThreads) {
                 stage_val(st)[i] = val[tx0 + i];
                 stage_col(st)[i] = col[tx0 + i];
                 stage_aux(st)[i] = rows[tx0 + i];
@@ -565,7 +560,7 @@ __global__ void seg_fixup_kernel(int64_t n_tiles, SegScratchT<T> sc, T* __restri
     seg_store<kAlpha, kBeta>(y, r, total, alpha, beta);
 }
 
-inline int seg_sm_count()
+inline int seg_grid_ctas()
 {
     static int sms = 0;
     if (!sms) {
@@ -574,35 +569,30 @@ inline int seg_sm_count()
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (sms <= 0) sms = 1;
     }
-    return sms;
+    return sms * kSegCtasPerSm;
 }
 
-// 2 CTAs per SM (the row-block CSR kernel's grid uses the same count)
-inline int seg_grid_ctas() { return seg_sm_count() * kSegCtasPerSm; }
-
 // Host-side launcher of the load-balanced kernel + fix-up for one
-// (V, T) pair.  sc must hold ceil(nnz / (NT * P)) tiles.  Sets the dynamic
+// (V, T) pair.  sc must hold ceil(nnz / TILE) tiles.  Sets the dynamic
 // shared-memory attribute on first use (per instantiation).
-template <int P, typename V, typename T, bool kAlpha, bool kBeta, bool kCoo, bool kSkip, bool kExact = false,
-          int NT = kSegThreads>
+template <int P, typename V, typename T, bool kAlpha, bool kBeta, bool kCoo, bool kSkip, bool kExact = false>
 inline cudaError_t seg_launch(int64_t n_rows, int64_t nnz, const int32_t* row_ptr, const int32_t* rows,
                               const int32_t* col, const V* val, const int32_t* thr_row, SegScratchT<T> sc,
                               const T* x, T* y, T alpha, T beta, uint32_t* err, cudaStream_t st)
 {
-    constexpr size_t smem = seg_smem_bytes<P, V, T, kCoo, NT>();
+    constexpr size_t smem = seg_smem_bytes<P, V, T, kCoo>();
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(seg_spmv_kernel<P, V, T, kAlpha, kBeta, kCoo, kSkip, kExact, NT>,
+        cudaError_t e = cudaFuncSetAttribute(seg_spmv_kernel<P, V, T, kAlpha, kBeta, kCoo, kSkip, kExact>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    const int64_t tiles = (nnz + SegShape<P, NT>::kTile - 1) / SegShape<P, NT>::kTile;
-    const int64_t ctas = static_cast<int64_t>(seg_sm_count()) * (kSegThreadsPerSm / NT);
-    const int64_t grid = tiles < ctas ? tiles : ctas;
-    seg_spmv_kernel<P, V, T, kAlpha, kBeta, kCoo, kSkip, kExact, NT>
-        <<<static_cast<unsigned>(grid), NT, smem, st>>>(n_rows, nnz, row_ptr, rows, col, val, thr_row, x, y, alpha,
-                                                        beta, sc, err);
+    const int64_t tiles = (nnz + SegShape<P>::kTile - 1) / SegShape<P>::kTile;
+    const int64_t grid = tiles < seg_grid_ctas() ? tiles : seg_grid_ctas();
+    seg_spmv_kernel<P, V, T, kAlpha, kBeta, kCoo, kSkip, kExact>
+        <<<static_cast<unsigned>(grid), kSegThreads, smem, st>>>(n_rows, nnz, row_ptr, rows, col, val, thr_row, x, y,
+                                                                 alpha, beta, sc, err);
     if (tiles > 1)
         seg_fixup_kernel<kAlpha, kBeta, T>
             <<<static_cast<unsigned>((tiles + 255) / 256), 256, 0, st>>>(tiles, sc, y, alpha, beta);
