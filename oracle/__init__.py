@@ -1,7 +1,8 @@
 """Plain FP64 CPU oracle (test infrastructure only).
 
 Only the tests, the package's smoke check and the benchmark's CPU-baseline
-leg may import this package.  The product path (the CUDA library and its
+and reference legs (the oracle timed on the host cores) may import this
+package.  The product path (the CUDA library and its
 Python binding) never does, and the oracle shares no code with it.
 
 The arithmetic lives in ``oracle.c`` (plain C loops, compiled without fused

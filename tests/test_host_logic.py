@@ -68,6 +68,22 @@ def test_spmv_byte_model():
     assert bench.spmv_bytes("hybrid", hyb, n, m, nnz) == 12 * 4 * 1024 + 16 * 900 + 8 * m + 8 * n
 
 
+def test_byte_model_matches_the_papers_bound():
+    """The marginal bytes of one more stored entry in the benchmark's byte
+    model are the per-entry bytes the paper prints for COO and CSR (Sec. 6.1,
+    fixture tests/golden/spmv_byte_bound.txt), so its flops per byte are the
+    paper's bandwidth / 8 and bandwidth / 6."""
+    import bench
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "spmv_byte_bound.txt")
+    rows = [l.split() for l in open(path) if l.strip() and not l.startswith("#")]
+    assert {r[0] for r in rows} == {"coo", "csr"}
+    n, m, nnz = 5000, 5000, 10 ** 6
+    for fmt, per_entry, flops_per_byte in rows:
+        step = bench.spmv_bytes(fmt, None, n, m, nnz + 1) - bench.spmv_bytes(fmt, None, n, m, nnz)
+        assert step == int(per_entry)
+        assert 2.0 / step == pytest.approx(float(flops_per_byte), rel=1e-15)
+
+
 def test_dominant_kernel_roofline():
     """The roofline names the kernel with the largest share of the step:
     launches of one kernel on different matrices are pooled, a hybrid
