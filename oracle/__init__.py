@@ -25,14 +25,19 @@ LIB_PATH = os.path.join(HERE, "liboracle.so")
 OK, NOT_CONVERGED, BREAKDOWN = 0, 6, 7
 
 
+OMP_LIB_PATH = os.path.join(HERE, "liboracle_omp.so")
+
+
 def build(force: bool = False) -> str:
-    """Compile oracle.c into liboracle.so with gcc (no FMA contraction)."""
-    src = os.path.join(HERE, "oracle.c")
-    if force or not os.path.exists(LIB_PATH) or os.path.getmtime(LIB_PATH) < os.path.getmtime(src):
-        tmp = LIB_PATH + ".tmp%d" % os.getpid()
-        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
-                               "-shared", "-o", tmp, src, "-lm"])
-        os.replace(tmp, LIB_PATH)
+    """Compile oracle.c into liboracle.so with gcc (no FMA contraction), and
+    the all-cores row loop oracle_omp.c into liboracle_omp.so (OpenMP)."""
+    for src, out, extra in ((os.path.join(HERE, "oracle.c"), LIB_PATH, []),
+                            (os.path.join(HERE, "oracle_omp.c"), OMP_LIB_PATH, ["-fopenmp"])):
+        if force or not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(src):
+            tmp = out + ".tmp%d" % os.getpid()
+            subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", *extra,
+                                   "-shared", "-o", tmp, src, "-lm"])
+            os.replace(tmp, out)
     return LIB_PATH
 
 
@@ -120,6 +125,25 @@ def spmv_csr(A, x, alpha=1.0, beta=0.0, y=None):
     x = _c(x, np.float64)
     out = np.zeros(n) if y is None else np.array(y, dtype=np.float64, copy=True)
     lib().orc_spmv_csr(n, _p(rp), _p(ci), _p(v), _p(x), alpha, beta, _p(out))
+    return out
+
+
+_omp = None
+
+
+def spmv_csr_omp(A, x, threads, alpha=1.0, beta=0.0, y=None):
+    """spmv_csr with the row loop shared among `threads` host threads
+    (OpenMP, static blocks of rows); bit-identical to spmv_csr."""
+    global _omp
+    if _omp is None:
+        build()
+        _omp = C.CDLL(OMP_LIB_PATH)
+        _omp.orc_spmv_csr_omp.restype = None
+        _omp.orc_spmv_csr_omp.argtypes = [_I64, _P, _P, _P, _P, _D, _D, _P, _INT]
+    n, rp, ci, v = _csr(A)
+    x = _c(x, np.float64)
+    out = np.zeros(n) if y is None else np.array(y, dtype=np.float64, copy=True)
+    _omp.orc_spmv_csr_omp(n, _p(rp), _p(ci), _p(v), _p(x), alpha, beta, _p(out), int(threads))
     return out
 
 

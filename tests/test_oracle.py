@@ -720,6 +720,49 @@ def test_features_brute_force(orc):
         assert np.allclose(f, exp, rtol=1e-12, atol=0), (f, exp)
 
 
+def test_features_closed_form_laplacian_16():
+    """5-point Laplacian on a 16 x 16 grid, every statistic worked out by hand:
+    4 corner rows of 3 entries, 56 edge rows of 4, 196 interior rows of 5
+    (nnz 1216); 480 entries with |i-j| = 1, 480 with |i-j| = 16, 256 on the
+    diagonal; every 32-row SELL-P slice holds an interior row (width 5).
+    Catches a sample (n-1) instead of population std, |i-j| averaged over
+    rows instead of entries, and a SELL-P width taken from the mean."""
+    f = orc_features_of(syn.laplace2d(16))
+    exp = [math.log10(256), math.log10(1216), 4.75, math.sqrt(56 / 256), 5, 3, 5 / 4.75, 0.0,
+           16 / 256, 8160 / 1216 / 256, 1.0, 1280 / 1216]
+    assert np.allclose(f, exp, rtol=1e-13, atol=0), (f, exp)
+
+
+def test_features_closed_form_block_diagonal():
+    """Five dense 8 x 8 blocks (n = 40): rows of 8, bandwidth 7, sum of
+    |i-j| over one block 2 (7 + 12 + 15 + 16 + 15 + 12 + 7) = 168, i.e. 2.625
+    per entry; the last SELL-P slice (8 rows) still counts 32 rows of
+    width 8, so the slots are 512 for 320 entries."""
+    f = orc_features_of(syn.block_diagonal(40, 8, seed=5))
+    exp = [math.log10(40), math.log10(320), 8.0, 0.0, 8, 8, 1.0, 0.0, 7 / 40, 2.625 / 40, 1.0, 512 / 320]
+    assert np.allclose(f, exp, rtol=1e-13, atol=1e-300), (f, exp)
+
+
+def test_features_closed_form_half_empty_diagonal():
+    """Diagonal entries in the even rows of a 64 x 64 matrix, odd rows empty:
+    mean 1/2, population std 1/2, min 0, max/mean 2, half the rows empty and
+    half holding their diagonal, two SELL-P slices of width 1 (64 slots for
+    32 entries)."""
+    n = 64
+    rp = np.zeros(n + 1, np.int32)
+    rp[1:] = np.cumsum(np.arange(n) % 2 == 0)
+    A = dict(n_rows=n, n_cols=n, row_ptr=rp, col_idx=np.arange(0, n, 2, dtype=np.int32), val=np.ones(n // 2))
+    f = orc_features_of(A)
+    exp = [math.log10(64), math.log10(32), 0.5, 0.5, 1, 0, 2.0, 0.5, 0.0, 0.0, 0.5, 2.0]
+    assert np.allclose(f, exp, rtol=1e-13, atol=1e-300), (f, exp)
+
+
+def orc_features_of(A):
+    import oracle
+    oracle.build()
+    return oracle.features(A)
+
+
 # ---------------------------------------------------------------------- MLP
 
 def test_mlp_gradient_central_differences():
@@ -753,3 +796,71 @@ def test_adam_first_step_moves_by_lr():
     g["b3"][:] = -2.0
     P = mlp.adam_step(P, g, {}, 1, lr=0.01)
     assert np.allclose(P["W1"], -0.01, rtol=1e-6) and np.allclose(P["b3"], 0.01, rtol=1e-6)
+
+
+def test_mlp_forward_hand_computed():
+    """A sparse network whose output is worked out by hand: h1 = relu(W1 x + b1)
+    = (2, relu(-3) = 0, 0.5); h2 = relu(W2 h1 + b2) = (2 + 10 * 0, 4 * 0.5,
+    relu(-2) = 0, relu(-1) = 0); out = W3 h2 + b3 = (0.5 * 2 + 0.25 * 2 + 0.1,
+    7 * 0 - 0.2).  A dropped ReLU, a dropped bias or a transposed W2/W3 each
+    changes the result."""
+    from oracle import mlp
+    P = {k: np.zeros(s) for k, s in mlp.shapes(12, 64, 2).items()}
+    P["W1"][0, 0], P["W1"][1, 1], P["b1"][2] = 1.0, -1.0, 0.5
+    P["W2"][0, 0], P["W2"][0, 1], P["W2"][1, 2], P["W2"][2, 0], P["b2"][3] = 1.0, 10.0, 4.0, -1.0, -1.0
+    P["W3"][0, 0], P["W3"][0, 1], P["W3"][1, 2], P["b3"][:] = 0.5, 0.25, 7.0, (0.1, -0.2)
+    X = np.zeros((2, 12))
+    X[0, :2] = (2.0, 3.0)
+    X[1, :2] = (-1.0, 0.0)  # second sample: h1 = (0, 0, 0.5), h2 = (0, 2, 0, 0)
+    out, _ = mlp.forward(P, X)
+    assert np.allclose(out, [[1.6, -0.2], [0.25 * 2 + 0.1, -0.2]], rtol=0, atol=1e-15), out
+    # masked MSE of that output: only (0, 0) and (1, 1) count
+    Y = np.array([[1.0, 5.0], [0.0, 0.3]])
+    M = np.array([[1.0, 0.0], [0.0, 1.0]])
+    assert abs(mlp.loss(P, X, Y, M) - (0.6 ** 2 + 0.5 ** 2) / 2) <= 1e-15
+
+
+def test_adam_bias_correction_after_three_steps():
+    """With a constant gradient g the bias-corrected moments are exactly g and
+    g^2 at every step, so each of steps 1, 2, 3 moves a parameter by
+    lr * sign(g) (up to eps): after three steps it sits at -3 lr sign(g).
+    Without the 1 - beta^t corrections the second step would move by
+    lr * 0.19 / sqrt(0.001999) = 4.25 lr."""
+    from oracle import mlp
+    sh = mlp.shapes(12, 64, 3)
+    P = {k: np.zeros(s) for k, s in sh.items()}
+    g = {k: np.full(s, 0.5) for k, s in sh.items()}
+    g["b3"][:] = -2.0
+    st = {}
+    for t in (1, 2, 3):
+        P = mlp.adam_step(P, g, st, t, lr=0.01)
+        assert np.allclose(P["W1"], -0.01 * t, rtol=1e-6) and np.allclose(P["b3"], 0.01 * t, rtol=1e-6), t
+
+
+def test_adam_two_steps_worked_example():
+    """Gradients 1 then -2 with the default betas (0.9, 0.999), worked out by
+    hand: m1 = 0.1, v1 = 0.001 -> step 1 = lr; m2 = 0.09 - 0.2 = -0.11,
+    v2 = 0.000999 + 0.004 = 0.004999, m2^ = -0.11 / 0.19, v2^ = 0.004999 /
+    0.001999, step 2 = lr m2^ / sqrt(v2^) = -0.366100... lr."""
+    from oracle import mlp
+    sh = {k: (1,) for k in mlp.NAMES}
+    P = {k: np.zeros(1) for k in mlp.NAMES}
+    st = {}
+    P = mlp.adam_step(P, {k: np.ones(1) for k in sh}, st, 1, lr=1.0, eps=0.0)
+    assert abs(P["W1"][0] + 1.0) <= 1e-12
+    P = mlp.adam_step(P, {k: np.full(1, -2.0) for k in sh}, st, 2, lr=1.0, eps=0.0)
+    step2 = (-0.11 / 0.19) / math.sqrt(0.004999 / 0.001999)
+    assert abs(step2 + 0.3661) < 1e-4
+    assert abs(P["W1"][0] - (-1.0 - step2)) <= 1e-12, P["W1"][0]
+
+
+@pytest.mark.parametrize("threads", [1, 3, 8])
+def test_all_cores_row_loop_equals_the_oracle(orc, threads):
+    """The OpenMP row loop of the CPU baseline computes each row exactly as
+    the sequential oracle does: bit-identical results for any thread count."""
+    for A in small_mats() + [syn.powerlaw(3000, 12.0, 1.5, 900, seed=42)]:
+        x = syn.vector(A["n_cols"], 5)
+        y0 = syn.vector(A["n_rows"], 6)
+        a = orc.spmv_csr(A, x, 1.5, -0.5, y0)
+        b = orc.spmv_csr_omp(A, x, threads, 1.5, -0.5, y0)
+        assert np.array_equal(a, b)
