@@ -85,7 +85,7 @@ def csr_default_launches(A):
     return 1
 
 
-def kernel_launches(fmt, nnz_or_coo, tile=2816, csr_launches=1):
+def kernel_launches(fmt, nnz_or_coo, tile=704, csr_launches=1):
     """Launches of this library per SpMV (load-balanced kernels add a fix-up
     launch when they span more than one tile)."""
     seg = 1 + (1 if nnz_or_coo > tile else 0)
@@ -243,25 +243,56 @@ class ClockSampler:
 
 # ------------------------------------------------------------ CPU baseline
 
+def cpu_model():
+    """Host CPU model name (lscpu, else /proc/cpuinfo), for the baseline record."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
 def cpu_baseline(mats, budget_s=20.0):
-    """The oracle's plain CSR SpMV (one host thread) on the sweep matrices,
-    as many passes as fit in the budget (at least one per matrix)."""
+    """The oracle's plain CSR SpMV on the sweep matrices, timed twice on the
+    host: its row loop on every core of the affinity mask (OpenMP, `value`)
+    and the sequential oracle on one thread; each leg as many passes as fit
+    in half the budget (at least one per matrix)."""
     import oracle
     oracle.build()
-    total_b, total_t, passes = 0.0, 0.0, 0
-    start = time.perf_counter()
-    while True:
-        for name, A in mats.items():
-            x = syn.vector(A["n_cols"], 99)
-            t0 = time.perf_counter()
-            oracle.spmv_csr(A, x)
-            total_t += time.perf_counter() - t0
-            total_b += spmv_bytes("csr", None, A["n_rows"], A["n_cols"], len(A["val"]))
-        passes += 1
-        if time.perf_counter() - start > budget_s:
-            break
-    return {"value": total_b / total_t / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
-            "sample": "%d pass(es) of the oracle's single-thread CSR SpMV over the 4 sweep matrices" % passes}
+    cores = len(os.sched_getaffinity(0))
+
+    def leg(fn, budget):
+        total_b, total_t, passes = 0.0, 0.0, 0
+        start = time.perf_counter()
+        while True:
+            for name, A in mats.items():
+                x = syn.vector(A["n_cols"], 99)
+                t0 = time.perf_counter()
+                fn(A, x)
+                total_t += time.perf_counter() - t0
+                total_b += spmv_bytes("csr", None, A["n_rows"], A["n_cols"], len(A["val"]))
+            passes += 1
+            if time.perf_counter() - start > budget:
+                break
+        return total_b / total_t / 1e9, passes
+
+    v_all, p_all = leg(lambda A, x: oracle.spmv_csr_omp(A, x, cores), budget_s / 2)
+    v_one, p_one = leg(oracle.spmv_csr, budget_s / 2)
+    return {"value": v_all, "unit": "GB/s", "cores": cores, "kind": "oracle",
+            "sample": "%d pass(es) of the oracle's CSR SpMV row loop on %d threads (OpenMP) over the 4 sweep "
+                      "matrices" % (p_all, cores),
+            "cpu_model": cpu_model(),
+            "single_thread": {"value": v_one, "unit": "GB/s", "cores": 1,
+                              "sample": "%d pass(es) of the sequential oracle over the 4 sweep matrices" % p_one}}
 
 
 # -------------------------------------------------------------------- GPU
@@ -299,7 +330,8 @@ def run_gpu(args):
     stream = torch.cuda.current_stream()
     st = stream.cuda_stream
     mats, handles = {}, {}
-    sweep = [m for m in SWEEP if not args.only or any(c.split("/")[0] == m for c in args.only.split(","))]
+    base = syn.SPMV_SWEEP_SMALL if args.sweep == "small" else SWEEP
+    sweep = [m for m in base if not args.only or any(c.split("/")[0] == m for c in args.only.split(","))]
     for name in sweep:
         A = load_workload(name)
         mats[name] = A
@@ -400,7 +432,8 @@ def run_gpu(args):
 
     extra = {}
     if not args.no_extras and rank == 0:
-        extra = run_extras(gko, torch, dev, st)
+        extra = run_extras(gko, torch, dev, st, selector=not args.no_selector,
+                           selector_matrices=args.selector_matrices)
     launches = sum(c["launches"] for c in cases) * args.steps
     line = {
         "metric": "FP64 SpMV GB/s (algorithmic bytes: values + indices + x + y), all formats x 4 sweep matrices",
@@ -433,10 +466,59 @@ def _time_call(torch, fn):
     return time.perf_counter() - t0, r
 
 
-def run_extras(gko, torch, dev, st):
-    """CG time to 1e-10 (FP64 and mixed) and batched CG; outside the timed
-    SpMV region.  Each solve runs once untimed first."""
+def run_selector_extra(gko, torch, n_test=200, workers=None):
+    """Held-out evaluation of the committed selector on this GPU: the 200
+    held-out sweep matrices (seeds 3000..3199) are generated again, every
+    candidate is re-timed exactly as the training sweep times it (round
+    robin, L2 flushed, median of 5), and the committed network's choice is
+    scored against the exhaustive best, the library's default CSR kernel and
+    the best fixed candidate of the training set.  Latency: the first
+    gko_select_format call on a fresh handle (features + forward)."""
+    from paper_2011_08879_gb300 import selector as sel
+    w = sel.load()
+    params = np.asarray(w["params"], dtype=np.float32)
+    mean, scale = np.asarray(w["feat_mean"]), np.asarray(w["feat_scale"])
+    seeds = list(range(3000, 3000 + n_test))
+    if workers is None:
+        workers = max(1, min(14, len(os.sched_getaffinity(0)) - 2))
+    t0 = time.perf_counter()
+    lat = []
+
+    def on_handle(M):
+        if len(lat) < 40:
+            torch.cuda.synchronize()
+            a = time.perf_counter()
+            M.select_format()
+            lat.append(time.perf_counter() - a)
+
+    F, T, N, S, worst = sel.sweep(seeds, workers=workers, on_handle=on_handle)
+    rep = sel.evaluate(params, mean, scale, F, T)
+    fixed_name = w["report"]["test"].get("fixed_best_class")
+    fixed = sel.CLASS_NAMES.index(fixed_name) if fixed_name in sel.CLASS_NAMES else None
+    exhaustive_s = float(np.nansum(T))  # one timing of every candidate of every matrix
+    out = {"matrices": len(seeds), "seeds": "3000..%d" % (3000 + n_test - 1),
+           "regret_mean": round(rep["mean"], 4), "regret_median": round(rep["median"], 4),
+           "regret_p90": round(rep["p90"], 4), "regret_max": round(rep["max"], 4),
+           "default_csr_regret_mean": round(rep["csr_default_mean"], 4),
+           "choices": rep["choices"], "structures": {k: S.count(k) for k in sorted(set(S))},
+           "max_candidate_disagreement": worst,
+           "selector_latency_us_median": round(1e6 * statistics.median(lat), 1) if lat else None,
+           "exhaustive_one_timing_per_candidate_ms": round(1e3 * exhaustive_s / len(seeds), 3),
+           "wall_s": round(time.perf_counter() - t0, 1),
+           "weights_trained_on": "%d matrices" % w["report"].get("n_train", 0)}
+    if fixed is not None:
+        out["fixed_best_class"] = fixed_name
+        out["fixed_best_regret_mean"] = round(float(sel.regret(T, np.full(len(T), fixed)).mean()), 4)
+    return out
+
+
+def run_extras(gko, torch, dev, st, selector=True, selector_matrices=200):
+    """CG time to 1e-10 (FP64 and mixed), batched CG, hardware ceilings and
+    the selector's held-out regret; outside the timed SpMV region.  Each
+    solve runs once untimed first."""
     out = {}
+    if selector:
+        out["selector"] = run_selector_extra(gko, torch, n_test=selector_matrices)
     L = load_workload("laplace2d_128")
     n = L["n_rows"]
     M = gko.Matrix(L, stream=st)
@@ -542,9 +624,29 @@ def run_extras(gko, torch, dev, st):
         x = torch.zeros_like(rhs)
         t, (s, infos) = _time_call(torch, lambda: G.cg(rhs, x, tol=1e-10, maxit=1000, stream=st))
     its = [i.iterations for i in infos]
+    # roofline of the batched solve: every iteration re-streams the system's
+    # CSR (values + indices + row pointers); vectors live in shared memory.
+    # FP64 work per iteration and row: the product's FMAs plus five vector
+    # FMAs (p.q, x, r, r.r, p)
+    ro, rp = B["row_off"], B["row_ptr"].astype(np.int64)
+    n_s = np.diff(ro)
+    nnz_s = rp[ro[1:]] - rp[ro[:-1]]
+    its_a = np.array(its, dtype=np.float64)
+    mat_bytes = float(np.sum(its_a * (12.0 * nnz_s + 4.0 * (n_s + 1))))
+    fmas = float(np.sum(its_a * (nnz_s + 5.0 * n_s)))
     out["batched_cg_4096"] = {"s": round(t, 5), "status": s, "block_size": best,
                               "max_rel_residual": max(i.rel_residual for i in infos),
-                              "iterations_mean": round(float(np.mean(its)), 2)}
+                              "iterations_mean": round(float(np.mean(its)), 2),
+                              "matrix_GBs": round(mat_bytes / t / 1e9, 1),
+                              "fp64_tfma_s": round(fmas / t / 1e12, 4)}
+    # hardware ceilings of this GPU (FP64 / FP32 FMA rate, random gathers)
+    f64, f32, g16 = gko.binding.gko_measure_ceilings(1 << 21, st)
+    g64 = gko.binding.gko_measure_ceilings(1 << 23, st)[2]
+    out["ceilings"] = {"fp64_tfma_s": round(f64, 4), "fp32_tfma_s": round(f32, 3),
+                       "random_gathers_G_s_x_16MB": round(g16, 1), "random_gathers_G_s_x_64MB": round(g64, 1),
+                       "how": "gko_measure_ceilings: 8 FMA chains per thread, 8 blocks of 256 per SM; random 8-byte "
+                              "loads from a 16 MB / 64 MB array; best of 5 after a warm-up"}
+    out["batched_cg_4096"]["fp64_pipe_frac"] = round(fmas / t / 1e12 / f64, 4)
     return out
 
 
@@ -626,6 +728,11 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--only", default="", help="comma list of matrix/format cases to time (profiling runs)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-selector", action="store_true", help="skip the selector's held-out re-timing")
+    ap.add_argument("--selector-matrices", type=int, default=200,
+                    help="held-out matrices re-timed for the selector's regret (seeds 3000 onwards)")
+    ap.add_argument("--sweep", default="full", choices=["full", "small"],
+                    help="small: quarter-size matrices of the same four kinds (profiling captures)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "gko":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)

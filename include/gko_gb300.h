@@ -52,7 +52,7 @@ enum {
     GKO_FMT_HYBRID = 4, /* ELL part of width K_h (row i's first min(len_i, K_h) entries) + COO part
                            (the remaining entries, sorted by (row, col)).  K_h minimises
                            n_pad*K*(s_v+4) + overflow(K)*(s_v+8) bytes, s_v = 8, ties to smaller K */
-    GKO_FMT_AUTO = 5    /* learned selector's choice (gko_spmv only) */
+    GKO_FMT_AUTO = 5    /* learned selector's choice, else the exhaustive autotuner's (gko_spmv only) */
 };
 
 /* Status codes. */
@@ -120,6 +120,31 @@ const char* gko_status_string(int status);
 /* Library version string. */
 const char* gko_version(void);
 
+/* Ceilings of the running GPU that the sparse kernels are judged against,
+ * measured the way Sec. 6 characterises each platform before its SpMV
+ * results (a stream benchmark for bandwidth, mixbench for arithmetic):
+ * *fp64_tfma and *fp32_tfma receive the FMA rates (10^12 FMA/s; eight
+ * independent chains per thread, 8 blocks of 256 threads per SM) and
+ * *gathers_g the rate of random 8-byte loads (10^9/s) from a zeroed array
+ * of gather_span doubles (a power of two >= 1024; indices from a counter
+ * hash, so no index array is read).  Best of five timed runs after a
+ * warm-up (CUDA events on stream).  Allocates and frees its scratch
+ * stream-ordered; synchronises the stream. */
+int gko_measure_ceilings(double* fp64_tfma, double* fp32_tfma, double* gathers_g, int64_t gather_span,
+                         void* stream);
+
+/* Failure-injection hook for tests of the timeout path (the paper has no
+ * counterpart).  The staged kernels (load-balanced CSR/COO SpMV, the CSR
+ * row-block kernel, the mixed-precision inner product) wait for each tile's
+ * bulk copy with a bounded poll loop; polls sets the limit of that wait for
+ * launches made after the call (default 2^22 polls, restored by UINT32_MAX;
+ * CUDA graphs keep the value they were captured with).  polls = 0 makes
+ * every such wait give up at once: the kernel ORs bit 0 into the handle's
+ * error word (gko_matrix_errors), waits with the default limit for the copies
+ * it has in flight, and its CTAs exit, leaving y undefined; solvers return
+ * GKO_ERR_TIMEOUT.  Process-wide; not for concurrent use with other calls. */
+int gko_set_wait_limit(uint32_t polls);
+
 /* ----------------------------------------------------------- matrices */
 
 /* Create a handle from a CSR matrix (Sec. 6.1).  row_ptr[n_rows+1],
@@ -173,7 +198,8 @@ int gko_matrix_export(const gko_matrix* A, int fmt, int array, void* dst, int64_
 
 /* Sticky device error bits of the handle's kernels (bit 0 bounded wait
  * timed out, bit 1 bad index, bit 2 int32 overflow); clears them when
- * clear != 0.  Synchronises the stream. */
+ * clear != 0.  A call during which bit 0 was set left its output undefined
+ * (not merely incomplete).  Synchronises the stream. */
 int gko_matrix_errors(gko_matrix* A, uint32_t* bits, int clear, void* stream);
 
 /* ---------------------------------------------------------------- SpMV */
@@ -182,8 +208,13 @@ int gko_matrix_errors(gko_matrix* A, uint32_t* bits, int clear, void* stream);
  * n_cols entries, y n_rows (device pointers, caller-owned, not aliased).
  * beta == 0 means y is not read (NaN/Inf in y are overwritten).  FP64
  * arithmetic throughout; each y_i is within 1e-12 * (|alpha||A||x| +
- * |beta||y|)_i of the exact result.  GKO_FMT_AUTO uses the selector loaded
- * with gko_selector_load (CSR when none is loaded).  Asynchronous. */
+ * |beta||y|)_i of the exact result.  GKO_FMT_AUTO runs the candidate (see
+ * GKO_N_CANDIDATES) that the selector loaded with gko_selector_load predicts
+ * fastest, or, with no selector loaded, the one gko_autotune_format measures
+ * fastest; the choice is made on the first AUTO call (which then
+ * synchronises the stream) and cached in the handle until another selector
+ * is loaded or a format is materialised or released.  Asynchronous
+ * otherwise.  AUTO calls on one handle must not run concurrently. */
 int gko_spmv(int fmt, const gko_matrix* A, const double* x, double* y, double alpha, double beta,
              void* stream);
 
@@ -222,7 +253,8 @@ int gko_spmm(const gko_matrix* A, int64_t k, const double* x, int64_t ldx, doubl
  * arrays row[nnz], col[nnz], val[nnz] (COO sorted by (row, col), indices in
  * range; not validated), x[n_cols], y[n_rows].  row, col and val must be
  * 16-byte aligned; they are not read past nnz.  beta == 0: y is not read.
- * Same kernel and accuracy as gko_spmv(GKO_FMT_COO, ...).
+ * Same load-balanced kernel and accuracy as gko_spmv(GKO_FMT_COO, ...), run
+ * with tiles of 256 threads x 11 entries (gko_spmv: 64 x 11).
  *
  * Scratch: the carries of rows that cross tiles live in a fixed device
  * array inside the library (GKO_NOALLOC_MAX_TILES tiles of 2816 entries,
@@ -238,7 +270,9 @@ int gko_spmm(const gko_matrix* A, int64_t k, const double* x, int64_t ldx, doubl
  * before capturing a stream.  Later calls only launch kernels.
  *
  * err_flags: optional caller-owned device word; bit 0 is ORed in if a
- * bounded wait for a bulk copy gave up (y is then incomplete).  NULL: not
+ * bounded wait for a bulk copy gave up (y is then undefined), bit 1 in the
+ * bounds-checked build (libgkogb_checked.so) if an index was out of range
+ * (that entry is skipped; a bad row index leaves y undefined).  NULL: not
  * reported.  Asynchronous on stream. */
 #define GKO_NOALLOC_MAX_TILES 32768
 int gko_spmv_coo_noalloc(int64_t n_rows, int64_t n_cols, int64_t nnz, const int32_t* row, const int32_t* col,
@@ -253,8 +287,11 @@ int gko_spmv_coo_noalloc(int64_t n_rows, int64_t n_cols, int64_t nnz, const int3
  * on exit.  Stops when the recursive residual satisfies ||r|| <= tol ||b||
  * and the FP64 true residual confirms it (up to four confirmations), at
  * maxit (GKO_ERR_NOT_CONVERGED) or on breakdown (GKO_ERR_BREAKDOWN).
- * ||b|| = 0 returns x = 0.  Work vectors are allocated stream-ordered for
- * the call.  Synchronises the stream; info (host) may be NULL. */
+ * ||b|| = 0 returns x = 0.  A product whose bounded wait for a bulk copy
+ * gave up (bit 0 of the handle's error word, see gko_matrix_errors; the bit
+ * is sticky until cleared) stops the solve with GKO_ERR_TIMEOUT.  Work
+ * vectors are allocated stream-ordered for the call.  Synchronises the
+ * stream; info (host) may be NULL. */
 int gko_cg(const gko_matrix* A, int fmt, const double* b, double* x, double tol, int maxit,
            void* stream, gko_solve_info* info);
 
@@ -364,7 +401,9 @@ int gko_batch_destroy(gko_batch* B);
 
 /* Solve all systems of the batch by CG, one thread block per system taken
  * from a device work queue (largest systems first), vectors in shared
- * memory, launched as one persistent kernel inside a CUDA graph.
+ * memory, launched as one persistent kernel inside a CUDA graph (the
+ * instantiated graph is kept in the batch and relaunched by later calls
+ * with the same block size, b, x, tol and maxit).
  * block_size 0 = autotuned choice.  b, x device vectors of row_off[count]
  * entries (x: initial guess in, solution out).  infos: host array of count
  * entries or NULL.  Returns the worst status.  Synchronises the stream. */
@@ -408,12 +447,33 @@ int gko_mlp_grad(const float* params, int n_out, const float* X, const float* Y,
 int gko_mlp_adam(float* params, const float* grad, float* m, float* v, int64_t count, int t,
                  float lr, float beta1, float beta2, float eps, void* stream);
 
+/* Exhaustive autotuning, the selector's fallback and the judge of its
+ * regret (Sec. 6.1 observes that no SpMV kernel wins on every matrix).  The
+ * candidates, in this order, are the kernels the selector chooses among:
+ *   0 CSR row blocks (GKO_CFG_CSR_ROWBLOCK), 1 CSR equal-nnz split,
+ *   2 CSR 4 lanes per row, 3 CSR 32 lanes per row, 4 COO, 5 ELL, 6 SELL-P,
+ *   7 hybrid, 8 CSR binned by row length, 9 CSR one lane per row.
+ * gko_autotune_format times every candidate the handle can run (its format
+ * materialised and its configuration applicable): one warm-up and five timed
+ * products each (CUDA events on stream, alpha = 1, beta = 0, on staging
+ * vectors the handle owns), and returns the one with the smallest median in
+ * *fmt, *config.  times_us (host, GKO_N_CANDIDATES doubles, may be NULL)
+ * receives each candidate's median in microseconds, NaN where it does not
+ * apply.  With no selector loaded the choice becomes the handle's
+ * GKO_FMT_AUTO choice.  Synchronises the stream. */
+#define GKO_N_CANDIDATES 10
+int gko_autotune_format(gko_matrix* A, int* fmt, int* config, double* times_us, void* stream);
+
 /* Install a trained selector used by GKO_FMT_AUTO: packed FP32 params
  * (host), feature normalisation mean[12], scale[12] (host doubles), and
  * the n_out (format, config) pairs the outputs stand for (host ints,
  * fmts[i], cfgs[i]).  The prediction is argmin of the outputs. */
 int gko_selector_load(const float* params_host, int n_out, const double* feat_mean,
                       const double* feat_scale, const int* fmts, const int* cfgs);
+
+/* Remove the installed selector: GKO_FMT_AUTO falls back to exhaustive
+ * autotuning. */
+int gko_selector_clear(void);
 
 /* The selector's choice for A (features computed on the device, cached in
  * the handle).  Synchronises the stream. */

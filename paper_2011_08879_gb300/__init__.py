@@ -200,6 +200,12 @@ class Matrix:
     def select_format(self, stream=None):
         return binding.gko_select_format(self.handle, _stream(stream))
 
+    def autotune(self, stream=None):
+        """(fmt, config, times_us) of the exhaustive autotuner over the
+        candidates this handle can run (times in the order of
+        binding.N_CANDIDATES; NaN: not applicable)."""
+        return binding.gko_autotune_format(self.handle, _stream(stream))
+
 
 class Batch:
     """Owning wrapper of a gko_batch (see synthetic.batched_spd for the layout)."""

@@ -14,6 +14,7 @@ import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libgkogb.so")
+LIB_CHECKED_PATH = os.path.join(HERE, "libgkogb_checked.so")
 
 # formats
 FMT_CSR, FMT_COO, FMT_ELL, FMT_SELLP, FMT_HYBRID, FMT_AUTO = range(6)
@@ -46,6 +47,8 @@ _SIGS = {
     "gko_last_error": (C.c_char_p, []),
     "gko_status_string": (C.c_char_p, [_INT]),
     "gko_version": (C.c_char_p, []),
+    "gko_set_wait_limit": (_INT, [C.c_uint32]),
+    "gko_measure_ceilings": (_INT, [_P, _P, _P, _I64, _P]),
     "gko_matrix_create_csr": (_INT, [_I64, _I64, _I64, _P, _P, _P, _INT, _P, C.POINTER(_P)]),
     "gko_matrix_destroy": (_INT, [_P]),
     "gko_matrix_set_params": (_INT, [_P, _INT, _INT, _D]),
@@ -77,13 +80,15 @@ _SIGS = {
     "gko_mlp_adam": (_INT, [_P, _P, _P, _P, _I64, _INT, _F, _F, _F, _F, _P]),
     "gko_selector_load": (_INT, [_P, _INT, _P, _P, _P, _P]),
     "gko_select_format": (_INT, [_P, C.POINTER(_INT), C.POINTER(_INT), _P]),
+    "gko_selector_clear": (_INT, []),
+    "gko_autotune_format": (_INT, [_P, C.POINTER(_INT), C.POINTER(_INT), _P, _P]),
 }
 
 
-def _load() -> C.CDLL:
-    if not os.path.exists(LIB_PATH):
-        raise ImportError("libgkogb.so is not built (%s); run paper_2011_08879_gb300.build.build()" % LIB_PATH)
-    lib = C.CDLL(LIB_PATH)
+def _load(path=LIB_PATH) -> C.CDLL:
+    if not os.path.exists(path):
+        raise ImportError("%s is not built; run paper_2011_08879_gb300.build.build()" % path)
+    lib = C.CDLL(path)
     for name, (res, args) in _SIGS.items():
         f = getattr(lib, name)
         f.restype = res
@@ -92,6 +97,17 @@ def _load() -> C.CDLL:
 
 
 lib = _load()
+_checked = None
+
+
+def checked_lib() -> C.CDLL:
+    """The bounds-checked copy of the library (built with GKO_CHECK_BOUNDS:
+    unvalidated indices are clamped and reported as error bit 1), loaded on
+    first use; same entry points and signatures as ``lib``."""
+    global _checked
+    if _checked is None:
+        _checked = _load(LIB_CHECKED_PATH)
+    return _checked
 
 
 def status_name(s: int) -> str:
@@ -110,6 +126,12 @@ def _check(status: int, where: str, allow=()) -> int:
 
 def gko_version() -> str:
     return lib.gko_version().decode()
+
+
+def gko_set_wait_limit(polls) -> None:
+    """Poll limit of the staged kernels' first bounded wait (tests of the
+    timeout path); 0xFFFFFFFF restores the default."""
+    _check(lib.gko_set_wait_limit(polls), "gko_set_wait_limit")
 
 
 def gko_matrix_create_csr(n_rows, n_cols, nnz, row_ptr, col, val, on_device, stream=0) -> int:
@@ -300,3 +322,27 @@ def gko_select_format(A, stream=0):
     f, c = C.c_int(0), C.c_int(0)
     _check(lib.gko_select_format(A, C.byref(f), C.byref(c), stream), "gko_select_format")
     return f.value, c.value
+
+
+def gko_selector_clear() -> None:
+    """Uninstall the selector (GKO_FMT_AUTO then autotunes exhaustively)."""
+    _check(lib.gko_selector_clear(), "gko_selector_clear")
+
+
+N_CANDIDATES = 10
+
+
+def gko_autotune_format(A, stream=0):
+    """(fmt, config, times_us) of the exhaustive autotuner (see the header)."""
+    f, c = _INT(), _INT()
+    times = (C.c_double * N_CANDIDATES)()
+    _check(lib.gko_autotune_format(A, C.byref(f), C.byref(c), times, stream), "gko_autotune_format")
+    return f.value, c.value, list(times)
+
+
+def gko_measure_ceilings(gather_span=1 << 21, stream=0):
+    """(FP64 TFMA/s, FP32 TFMA/s, random gathers G/s) of the running GPU."""
+    a, b, c = C.c_double(), C.c_double(), C.c_double()
+    _check(lib.gko_measure_ceilings(C.byref(a), C.byref(b), C.byref(c), int(gather_span), stream),
+           "gko_measure_ceilings")
+    return a.value, b.value, c.value

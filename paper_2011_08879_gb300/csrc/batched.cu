@@ -185,11 +185,9 @@ template <int BS>
 static int launch_batched(gko_batch* B, const double* b, double* x, double tol, int maxit, cudaStream_t st)
 {
     const size_t smem = 4 * static_cast<size_t>(B->max_rows) * sizeof(double);
-    GKO_CUDA(cudaFuncSetAttribute(batched_cg_kernel<BS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  static_cast<int>(smem)));
-    int per_sm = 0, sms = 0, dev = 0;
-    GKO_CUDA(cudaGetDevice(&dev));
-    GKO_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    GKO_CUDA(smem_limit_once(reinterpret_cast<const void*>(batched_cg_kernel<BS>), static_cast<int>(smem)));
+    int per_sm = 0;
+    const int sms = device_sm_count();
     GKO_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_cg_kernel<BS>, BS, smem));
     if (per_sm < 1) return fail(GKO_ERR_INVALID_ARG, "batched CG: block does not fit on an SM");
     const int64_t grid = std::min<int64_t>(static_cast<int64_t>(per_sm) * sms, B->count);
@@ -213,9 +211,20 @@ static int launch_any(gko_batch* B, int bs, const double* b, double* x, double t
     return fail(GKO_ERR_INVALID_ARG, "block_size must be 0, 64, 128, 256, 512 or 1024");
 }
 
-// run [queue reset + kernel] as a captured CUDA graph
+// run [queue reset + kernel] as a captured CUDA graph; the instantiated
+// graph is kept in the batch and relaunched while block size, vectors,
+// tolerance and iteration limit are those it was captured with
 static int run_graph(gko_batch* B, int bs, const double* b, double* x, double tol, int maxit, cudaStream_t st)
 {
+    if (B->graph && B->graph_bs == bs && B->graph_b == b && B->graph_x == x && B->graph_tol == tol &&
+        B->graph_maxit == maxit) {
+        GKO_CUDA(cudaGraphLaunch(B->graph, st));
+        return GKO_OK;
+    }
+    if (B->graph) {
+        cudaGraphExecDestroy(B->graph);
+        B->graph = nullptr;
+    }
     cudaStream_t cap;
     GKO_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
     cudaGraph_t g = nullptr;
@@ -228,11 +237,19 @@ static int run_graph(gko_batch* B, int bs, const double* b, double* x, double to
     }
     if (e == cudaSuccess && s == GKO_OK) e = cudaGraphInstantiate(&ge, g, 0);
     if (e == cudaSuccess && s == GKO_OK) e = cudaGraphLaunch(ge, st);
-    if (ge) cudaGraphExecDestroy(ge);
     if (g) cudaGraphDestroy(g);
     cudaStreamDestroy(cap);
-    if (s != GKO_OK) return s;
-    if (e != cudaSuccess) return cuda_fail(e, "batched CG graph");
+    if (s != GKO_OK || e != cudaSuccess) {
+        if (ge) cudaGraphExecDestroy(ge);
+        if (s != GKO_OK) return s;
+        return cuda_fail(e, "batched CG graph");
+    }
+    B->graph = ge;
+    B->graph_bs = bs;
+    B->graph_b = b;
+    B->graph_x = x;
+    B->graph_tol = tol;
+    B->graph_maxit = maxit;
     return GKO_OK;
 }
 
@@ -312,6 +329,7 @@ int gko_batch_destroy(gko_batch* B)
     dev_free(B->iters);
     dev_free(B->status);
     dev_free(B->d_err);
+    if (B->graph) cudaGraphExecDestroy(B->graph);
     delete B;
     return GKO_OK;
 }

@@ -1,9 +1,15 @@
 // The C ABI (include/gko_gb300.h): argument checking, the matrix handle's
 // lifetime, format dispatch.  Every entry point returns a status and
 // records a message; none aborts.
+#include <algorithm>
+#include <array>
+#include <atomic>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
+#include <unordered_map>
 
 #include "common.cuh"
 #include "internal.h"
@@ -27,6 +33,55 @@ int cuda_fail(cudaError_t e, const char* what)
     return e == cudaErrorMemoryAllocation ? GKO_ERR_OUT_OF_MEMORY : GKO_ERR_CUDA;
 }
 
+// ------------------------------------------------------ per-device state
+
+namespace {
+constexpr int kDevCache = 64;  // devices with cached state (others query every time)
+std::mutex g_dev_mu;
+int g_sm_count[kDevCache] = {0};
+std::unordered_map<const void*, std::array<int, kDevCache>> g_smem_set;  // limit set per kernel and device
+std::atomic<uint32_t> g_first_wait_polls{1u << 22};
+}  // namespace
+
+int device_sm_count()
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+    if (dev >= 0 && dev < kDevCache) {
+        std::lock_guard<std::mutex> lk(g_dev_mu);
+        if (g_sm_count[dev] > 0) return g_sm_count[dev];
+    }
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+    if (dev >= 0 && dev < kDevCache) {
+        std::lock_guard<std::mutex> lk(g_dev_mu);
+        g_sm_count[dev] = sms;
+    }
+    return sms;
+}
+
+cudaError_t smem_limit_once(const void* kernel, int bytes)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kDevCache)
+        return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    std::lock_guard<std::mutex> lk(g_dev_mu);
+    auto it = g_smem_set.find(kernel);
+    if (it == g_smem_set.end()) {
+        std::array<int, kDevCache> z{};
+        it = g_smem_set.emplace(kernel, z).first;
+    }
+    if (it->second[dev] >= bytes) return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) it->second[dev] = bytes;
+    return e;
+}
+
+uint32_t first_wait_polls() { return g_first_wait_polls.load(std::memory_order_relaxed); }
+
 static bool valid_fmt(int f) { return f >= GKO_FMT_CSR && f <= GKO_FMT_HYBRID; }
 
 static int check_device(const gko_matrix* A)
@@ -46,6 +101,12 @@ extern "C" {
 const char* gko_last_error(void) { return g_last_error.c_str(); }
 
 const char* gko_version(void) { return "gko-gb300 1.0 (sm_103a)"; }
+
+int gko_set_wait_limit(uint32_t polls)
+{
+    g_first_wait_polls.store(polls == UINT32_MAX ? (1u << 22) : polls, std::memory_order_relaxed);
+    return GKO_OK;
+}
 
 const char* gko_status_string(int s)
 {
@@ -274,14 +335,101 @@ int gko_matrix_errors(gko_matrix* A, uint32_t* bits, int clear, void* stream)
 
 int gko_select_format(gko_matrix* A, int* fmt, int* config, void* stream);
 
+}  // extern "C"
+
+namespace gko {
+
+const int kCandFmt[GKO_N_CANDIDATES] = {GKO_FMT_CSR, GKO_FMT_CSR, GKO_FMT_CSR,   GKO_FMT_CSR,    GKO_FMT_COO,
+                                        GKO_FMT_ELL, GKO_FMT_SELLP, GKO_FMT_HYBRID, GKO_FMT_CSR, GKO_FMT_CSR};
+const int kCandCfg[GKO_N_CANDIDATES] = {GKO_CFG_CSR_ROWBLOCK,  GKO_CFG_CSR_NNZSPLIT, GKO_CFG_CSR_SUBWARP_4,
+                                        GKO_CFG_CSR_SUBWARP_32, 0, 0, 0, 0, GKO_CFG_CSR_BINNED,
+                                        GKO_CFG_CSR_SUBWARP_1};
+
+static int spmv_dispatch(int fmt, int config, const gko_matrix* A, const double* x, double* y, double alpha,
+                         double beta, cudaStream_t st);
+
+// Key of the AUTO choice: the selector generation and the materialised
+// formats (a new selector or a converted/released format invalidates it).
+static uint64_t auto_key(const gko_matrix* A)
+{
+    uint64_t mask = 0;
+    for (int f = 0; f < 5; ++f) mask |= static_cast<uint64_t>(A->has[f]) << f;
+    return (selector_generation() << 8) | (1u << 7) | mask;
+}
+
+// Exhaustive autotuning: every candidate the handle can run, one warm-up
+// and five timed launches each (CUDA events on the stream, on the handle's
+// staging vectors, alpha = 1, beta = 0), median per candidate, fastest wins.
+static int autotune(gko_matrix* A, int* fmt, int* cfg, double* times_us, cudaStream_t st)
+{
+    constexpr int kReps = 5;
+    if (!A->stage_x) {
+        GKO_TRY(dev_alloc(&A->stage_x, std::max<int64_t>(A->n_cols, 1)));
+        GKO_TRY(dev_alloc(&A->stage_y, std::max<int64_t>(A->n_rows, 1)));
+    }
+    GKO_CUDA(cudaMemsetAsync(A->stage_x, 0, std::max<int64_t>(A->n_cols, 1) * sizeof(double), st));
+    cudaEvent_t ev[GKO_N_CANDIDATES][kReps + 1] = {};
+    bool live[GKO_N_CANDIDATES] = {};
+    int status = GKO_OK;
+    for (int c = 0; c < GKO_N_CANDIDATES && status == GKO_OK; ++c) {
+        if (!A->has[kCandFmt[c]]) continue;
+        const std::string keep = gko_last_error();
+        if (spmv_dispatch(kCandFmt[c], kCandCfg[c], A, A->stage_x, A->stage_y, 1.0, 0.0, st) != GKO_OK) {
+            set_error(keep);  // configuration does not apply to this matrix
+            continue;
+        }
+        live[c] = true;
+        for (int k = 0; k <= kReps && status == GKO_OK; ++k) {
+            cudaError_t e = cudaEventCreate(&ev[c][k]);
+            if (e == cudaSuccess) e = cudaEventRecord(ev[c][k], st);
+            if (e != cudaSuccess) status = cuda_fail(e, "autotuner events");
+            if (status == GKO_OK && k < kReps)
+                status = spmv_dispatch(kCandFmt[c], kCandCfg[c], A, A->stage_x, A->stage_y, 1.0, 0.0, st);
+        }
+    }
+    if (status == GKO_OK) {
+        const cudaError_t e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) status = cuda_fail(e, "autotuner timing");
+    }
+    int best = -1;
+    double best_t = 0.0;
+    for (int c = 0; c < GKO_N_CANDIDATES; ++c) {
+        double med = NAN;
+        if (live[c] && status == GKO_OK) {
+            float ms[kReps];
+            for (int k = 0; k < kReps; ++k) cudaEventElapsedTime(&ms[k], ev[c][k], ev[c][k + 1]);
+            std::sort(ms, ms + kReps);
+            med = 1e3 * ms[kReps / 2];
+            if (best < 0 || med < best_t) best = c, best_t = med;
+        }
+        if (times_us) times_us[c] = med;
+        for (int k = 0; k <= kReps; ++k)
+            if (ev[c][k]) cudaEventDestroy(ev[c][k]);
+    }
+    if (status != GKO_OK) return status;
+    *fmt = best >= 0 ? kCandFmt[best] : GKO_FMT_CSR;
+    *cfg = best >= 0 ? kCandCfg[best] : GKO_CFG_DEFAULT;
+    return GKO_OK;
+}
+
 static int spmv_dispatch(int fmt, int config, const gko_matrix* A, const double* x, double* y, double alpha,
                          double beta, cudaStream_t st)
 {
     if (fmt == GKO_FMT_AUTO) {
-        int f = GKO_FMT_CSR, c = GKO_CFG_DEFAULT;
-        GKO_TRY(gko_select_format(const_cast<gko_matrix*>(A), &f, &c, st));
-        if (!A->has[f]) f = GKO_FMT_CSR, c = GKO_CFG_DEFAULT;
-        return spmv_dispatch(f, c, A, x, y, alpha, beta, st);
+        gko_matrix* M = const_cast<gko_matrix*>(A);
+        const uint64_t key = auto_key(M);
+        if (M->auto_fmt < 0 || M->auto_key != key) {
+            int f = GKO_FMT_CSR, c = GKO_CFG_DEFAULT;
+            if (selector_generation() != 0)
+                GKO_TRY(gko_select_format(M, &f, &c, st));
+            else
+                GKO_TRY(autotune(M, &f, &c, nullptr, st));
+            if (!M->has[f]) f = GKO_FMT_CSR, c = GKO_CFG_DEFAULT;
+            M->auto_fmt = f;
+            M->auto_cfg = c;
+            M->auto_key = key;
+        }
+        return spmv_dispatch(M->auto_fmt, M->auto_cfg, A, x, y, alpha, beta, st);
     }
     if (!A->has[fmt]) return fail(GKO_ERR_FORMAT_UNAVAILABLE, "format not materialised (call gko_convert first)");
     if (fmt != GKO_FMT_CSR && config != GKO_CFG_DEFAULT)
@@ -294,6 +442,30 @@ static int spmv_dispatch(int fmt, int config, const gko_matrix* A, const double*
         case GKO_FMT_HYBRID: return spmv_hybrid(A, x, y, alpha, beta, st);
     }
     return fail(GKO_ERR_INVALID_ARG, "unknown format");
+}
+
+}  // namespace gko
+
+extern "C" {
+
+int gko_autotune_format(gko_matrix* A, int* fmt, int* config, double* times_us, void* stream)
+{
+    if (!A || !fmt || !config) return fail(GKO_ERR_INVALID_ARG, "NULL argument");
+    GKO_TRY(check_device(A));
+    *fmt = GKO_FMT_CSR;
+    *config = GKO_CFG_DEFAULT;
+    if (A->n_rows == 0) {
+        if (times_us)
+            for (int c = 0; c < GKO_N_CANDIDATES; ++c) times_us[c] = NAN;
+        return GKO_OK;
+    }
+    GKO_TRY(autotune(A, fmt, config, times_us, static_cast<cudaStream_t>(stream)));
+    if (selector_generation() == 0) {  // the choice GKO_FMT_AUTO uses without a selector
+        A->auto_fmt = *fmt;
+        A->auto_cfg = *config;
+        A->auto_key = auto_key(A);
+    }
+    return GKO_OK;
 }
 
 static int spmv_checks(int fmt, const gko_matrix* A, const double* x, const double* y)

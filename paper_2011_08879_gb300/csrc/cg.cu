@@ -27,7 +27,7 @@
 
 namespace gko {
 
-int launch_seg(int64_t n_rows, int64_t nnz, const int32_t* row_ptr, const int32_t* rows, const int32_t* col,
+int launch_seg(int64_t n_rows, int64_t n_cols, int64_t nnz, const int32_t* row_ptr, const int32_t* rows, const int32_t* col,
                const double* val, const int32_t* thr_row, const SegArrays& sa, const double* x, double* y,
                double alpha, double beta, uint32_t* err, bool coo, cudaStream_t st, bool accumulate);
 
@@ -37,7 +37,7 @@ enum { kDotStore = 0, kDotRhoInit = 1, kDotPQ = 2 };
 template <typename T, int kMode>
 __global__ void __launch_bounds__(kRedThreads)
     dot_kernel(int64_t n, const T* __restrict__ a, const T* __restrict__ b, SolverState* s, double* part,
-               cudaGraphConditionalHandle h)
+               cudaGraphConditionalHandle h, const uint32_t* err = nullptr)
 {
     T acc = T(0);
     for (int64_t i = blockIdx.x * static_cast<int64_t>(kRedThreads) + threadIdx.x; i < n;
@@ -64,7 +64,12 @@ __global__ void __launch_bounds__(kRedThreads)
             }
             s->pq = tot;
             s->iter += 1;
-            if (!(tot > 0.0)) {
+            // a product whose bulk copies did not land leaves q undefined and
+            // sets the timeout bit of the handle's error word
+            if (err && (*reinterpret_cast<const volatile uint32_t*>(err) & 1u)) {
+                s->status = GKO_ERR_TIMEOUT;
+                stop_loop(s, h);
+            } else if (!(tot > 0.0)) {
                 s->status = GKO_ERR_BREAKDOWN;
                 stop_loop(s, h);
             } else {
@@ -567,7 +572,7 @@ static int cg_solve_impl(const gko_matrix* A, int fmt, const double* b, double* 
     GraphHolder gh;
     GKO_TRY(build_while_graph(&gh, [&](cudaGraphConditionalHandle h, cudaStream_t cs) -> int {
         GKO_TRY(spmv_fmt(A, fmt, p, q, 1.0, 0.0, cs));
-        dot_kernel<double, kDotPQ><<<grid, kRedThreads, 0, cs>>>(n, p, q, ds, part, h);
+        dot_kernel<double, kDotPQ><<<grid, kRedThreads, 0, cs>>>(n, p, q, ds, part, h, A->d_err);
         if (jacobi) {
             pcg_update_kernel<<<grid, kRedThreads, 0, cs>>>(n, x, r, p, q, dinv, ds, part, h);
             pcg_pupdate_kernel<<<grid, kRedThreads, 0, cs>>>(n, p, r, dinv, ds, 0, 0);
@@ -584,8 +589,8 @@ static int cg_solve_impl(const gko_matrix* A, int fmt, const double* b, double* 
     while (true) {
         GKO_CUDA(cudaGraphLaunch(gh.exec, st));
         GKO_TRY(read_state(&hs, ds, st));
-        if (hs.status == GKO_ERR_BREAKDOWN) {
-            status = GKO_ERR_BREAKDOWN;
+        if (hs.status == GKO_ERR_BREAKDOWN || hs.status == GKO_ERR_TIMEOUT) {
+            status = hs.status;
             break;
         }
         if (hs.conv) {
@@ -617,7 +622,9 @@ static int cg_solve_impl(const gko_matrix* A, int fmt, const double* b, double* 
     if (res < 0.0) GKO_TRY(true_residual(A, fmt, b, x, q, ds, part, bnorm, st, &res));
     fill_info(info, hs.iter, 0, res, status);
     if (status != GKO_OK)
-        set_error(status == GKO_ERR_BREAKDOWN ? "CG breakdown (p.q <= 0 or NaN)" : "CG reached maxit");
+        set_error(status == GKO_ERR_BREAKDOWN ? "CG breakdown (p.q <= 0 or NaN)"
+                  : status == GKO_ERR_TIMEOUT  ? "CG product: a bounded wait for a bulk copy gave up"
+                                               : "CG reached maxit");
     return status;
 }
 
@@ -1076,67 +1083,209 @@ int bicgstab_solve(const gko_matrix* A, int fmt, const double* b, double* x, dou
 
 // --------------------------------------------------------------- GMRES
 
-constexpr int kGmChunk = 8;  // basis vectors per multi-dot / combination launch
+constexpr int kGmChunk = 8;  // basis vectors per pass of the multi-dot loops
 
-// part[blk * ldp + c0 + c] = the block's share of V_{c0+c} . w (c < cnt)
-__global__ void __launch_bounds__(kRedThreads)
-    gm_multidot_kernel(int64_t n, const double* __restrict__ V, int64_t ldv, int c0, int cnt,
-                       const double* __restrict__ w, double* __restrict__ part, int ldp)
+// Device-resident state of one GMRES(m) cycle.  H is (m + 1) x m row-major;
+// g the rotated right-hand side of the least-squares problem.
+struct GmState {
+    double bnorm, tol;  // stop when |g[j]| <= tol * bnorm
+    double hn;          // norm of the vector just orthogonalised
+    int32_t j;          // Arnoldi steps done in this cycle (columns of H)
+    int32_t m, total, maxit;
+    int32_t stop, broke;
+    uint32_t ticket;
+};
+
+// part[blk * ldp + c] = the block's share of V_c . w for every c < ncols
+// (ncols = j + 1 read from the state), in chunks of kGmChunk columns.
+__device__ __forceinline__ void gm_partial_dots(int64_t n, const double* __restrict__ V, int ncols,
+                                                const double* __restrict__ w, double* __restrict__ part, int ldp)
 {
     __shared__ double sh[kGmChunk][kRedThreads / 32];
-    double acc[kGmChunk];
-#pragma unroll
-    for (int c = 0; c < kGmChunk; ++c) acc[c] = 0.0;
-    for (int64_t i = blockIdx.x * static_cast<int64_t>(kRedThreads) + threadIdx.x; i < n;
-         i += static_cast<int64_t>(gridDim.x) * kRedThreads) {
-        const double wi = w[i];
-#pragma unroll
-        for (int c = 0; c < kGmChunk; ++c)
-            if (c < cnt) acc[c] = fma(V[(c0 + c) * ldv + i], wi, acc[c]);
-    }
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    for (int c0 = 0; c0 < ncols; c0 += kGmChunk) {
+        const int cnt = min(kGmChunk, ncols - c0);
+        double acc[kGmChunk];
 #pragma unroll
-    for (int c = 0; c < kGmChunk; ++c) {
-        double v = acc[c];
-        for (int o = 16; o; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-        if (lane == 0) sh[c][wp] = v;
-    }
-    __syncthreads();
-    if (threadIdx.x < cnt) {
-        double t = 0.0;
-        for (int k = 0; k < kRedThreads / 32; ++k) t += sh[threadIdx.x][k];
-        part[blockIdx.x * static_cast<int64_t>(ldp) + c0 + threadIdx.x] = t;
+        for (int c = 0; c < kGmChunk; ++c) acc[c] = 0.0;
+        for (int64_t i = blockIdx.x * static_cast<int64_t>(kRedThreads) + threadIdx.x; i < n;
+             i += static_cast<int64_t>(gridDim.x) * kRedThreads) {
+            const double wi = w[i];
+#pragma unroll
+            for (int c = 0; c < kGmChunk; ++c)
+                if (c < cnt) acc[c] = fma(V[(c0 + c) * n + i], wi, acc[c]);
+        }
+#pragma unroll
+        for (int c = 0; c < kGmChunk; ++c) {
+            double v = acc[c];
+            for (int o = 16; o; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+            if (lane == 0) sh[c][wp] = v;
+        }
+        __syncthreads();
+        if (threadIdx.x < cnt) {
+            double t = 0.0;
+            for (int k = 0; k < kRedThreads / 32; ++k) t += sh[threadIdx.x][k];
+            part[blockIdx.x * static_cast<int64_t>(ldp) + c0 + threadIdx.x] = t;
+        }
+        __syncthreads();
     }
 }
 
-// h[c] = sum over blocks (in block order) of part[b * ldp + c], c < ncols
-__global__ void gm_reduce_kernel(int nblocks, int ncols, const double* __restrict__ part, int ldp,
-                                 double* __restrict__ h)
+// First Gram-Schmidt pass: partial dots of V_0..V_j with w = A v_j.
+__global__ void __launch_bounds__(kRedThreads)
+    gm_dots_kernel(int64_t n, const double* __restrict__ V, const double* __restrict__ w, double* __restrict__ part,
+                   int ldp, const GmState* s)
 {
+    gm_partial_dots(n, V, s->j + 1, w, part, ldp);
+}
+
+// coef[c] = sum over blocks (in block order) of part[b * ldp + c] for
+// c <= j; hh[c] = coef[c] on the first pass, hh[c] += coef[c] on the second.
+__global__ void gm_coef_kernel(int nblocks, const double* __restrict__ part, int ldp, double* __restrict__ coef,
+                               double* __restrict__ hh, int second, const GmState* s)
+{
+    const int ncols = s->j + 1;
     for (int c = threadIdx.x; c < ncols; c += blockDim.x) {
         double t = 0.0;
         for (int b = 0; b < nblocks; ++b) t += part[b * static_cast<int64_t>(ldp) + c];
-        h[c] = t;
+        coef[c] = t;
+        hh[c] = second ? hh[c] + t : t;
     }
 }
 
-// w -= sum_{c < ncols} h[c] V_c  (sgn = -1) or x += sum y[c] V_c (sgn = +1)
+// w -= sum_{c <= j} coef[c] V_c, then the partial dots of V_0..V_j with the
+// updated w (the second Gram-Schmidt pass reads V once for both).
 __global__ void __launch_bounds__(kRedThreads)
-    gm_combine_kernel(int64_t n, double* __restrict__ w, const double* __restrict__ V, int64_t ldv, int ncols,
-                      const double* __restrict__ h, double sgn)
+    gm_combine_dots_kernel(int64_t n, const double* __restrict__ V, double* __restrict__ w,
+                           const double* __restrict__ coef, double* __restrict__ part, int ldp, const GmState* s)
 {
     __shared__ double hs[128];
-    for (int c = threadIdx.x; c < ncols; c += blockDim.x) hs[c] = sgn * h[c];
+    const int ncols = s->j + 1;
+    for (int c = threadIdx.x; c < ncols; c += blockDim.x) hs[c] = coef[c];
     __syncthreads();
     for (int64_t i = blockIdx.x * static_cast<int64_t>(kRedThreads) + threadIdx.x; i < n;
          i += static_cast<int64_t>(gridDim.x) * kRedThreads) {
         double t = w[i];
-        for (int c = 0; c < ncols; ++c) t = fma(hs[c], V[c * ldv + i], t);
+        for (int c = 0; c < ncols; ++c) t = fma(-hs[c], V[c * n + i], t);
         w[i] = t;
+    }
+    // each thread reads back only the w entries it wrote: no grid barrier needed
+    gm_partial_dots(n, V, ncols, w, part, ldp);
+}
+
+// w -= sum_{c <= j} coef[c] V_c and hn = ||w|| (grid reduction; the last
+// block stores it in the state).
+__global__ void __launch_bounds__(kRedThreads)
+    gm_combine_norm_kernel(int64_t n, const double* __restrict__ V, double* __restrict__ w,
+                           const double* __restrict__ coef, double* __restrict__ part, GmState* s)
+{
+    __shared__ double hs[128];
+    const int ncols = s->j + 1;
+    for (int c = threadIdx.x; c < ncols; c += blockDim.x) hs[c] = coef[c];
+    __syncthreads();
+    double acc = 0.0;
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(kRedThreads) + threadIdx.x; i < n;
+         i += static_cast<int64_t>(gridDim.x) * kRedThreads) {
+        double t = w[i];
+        for (int c = 0; c < ncols; ++c) t = fma(-hs[c], V[c * n + i], t);
+        w[i] = t;
+        acc = fma(t, t, acc);
+    }
+    grid_sum(acc, part, &s->ticket, [&](double tot) { s->hn = sqrt(tot); });
+}
+
+// v_{j+1} = w / hn into the basis and into vcur (the next product's input);
+// nothing when hn is zero or not finite (the cycle stops there).
+__global__ void gm_next_vector_kernel(int64_t n, double* __restrict__ V, double* __restrict__ vcur,
+                                      const double* __restrict__ w, const GmState* s)
+{
+    const double hn = s->hn;
+    if (!(hn > 0.0) || !(hn < INFINITY)) return;
+    double* dst = V + (s->j + 1) * n;
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const double v = w[i] / hn;
+        dst[i] = v;
+        vcur[i] = v;
     }
 }
 
-// out = w / s (s on the device)
+// Column j of the Hessenberg matrix: hh[0..j] and hn; the earlier Givens
+// rotations applied to it, a new rotation zeroing its subdiagonal, the
+// least-squares right-hand side g rotated, the cycle's stop decided (residual
+// estimate |g[j+1]| <= tol ||b||, m columns, maxit steps in all, a zero hn,
+// or a breakdown: NaN or a zero rotation).  One thread.
+__global__ void gm_givens_kernel(double* __restrict__ H, double* __restrict__ cs, double* __restrict__ sn,
+                                 double* __restrict__ g, const double* __restrict__ hh, GmState* s,
+                                 cudaGraphConditionalHandle h)
+{
+    const int j = s->j, m = s->m;
+    const double hn = s->hn;
+    s->total += 1;
+    if (!(hn == hn)) {
+        s->broke = 1;
+        s->stop = 1;
+        cudaGraphSetConditional(h, 0);
+        return;
+    }
+    for (int i = 0; i <= j; ++i) H[i * m + j] = hh[i];
+    H[(j + 1) * m + j] = hn;
+    for (int i = 0; i < j; ++i) {  // earlier rotations on the new column
+        const double a = H[i * m + j], c = H[(i + 1) * m + j];
+        H[i * m + j] = cs[i] * a + sn[i] * c;
+        H[(i + 1) * m + j] = -sn[i] * a + cs[i] * c;
+    }
+    const double a = H[j * m + j], c = H[(j + 1) * m + j];
+    const double d = sqrt(a * a + c * c);
+    if (!(d > 0.0)) {
+        s->broke = 1;
+        s->stop = 1;
+        cudaGraphSetConditional(h, 0);
+        return;
+    }
+    cs[j] = a / d;
+    sn[j] = c / d;
+    H[j * m + j] = d;
+    H[(j + 1) * m + j] = 0.0;
+    g[j + 1] = -sn[j] * g[j];
+    g[j] = cs[j] * g[j];
+    s->j = j + 1;
+    if (fabs(g[j + 1]) <= s->tol * s->bnorm || !(hn > 0.0) || j + 1 >= m || s->total >= s->maxit) {
+        s->stop = 1;
+        cudaGraphSetConditional(h, 0);
+    }
+}
+
+// y = H(0:j, 0:j)^-1 g(0:j) by back substitution (one thread).
+__global__ void gm_backsub_kernel(const double* __restrict__ H, const double* __restrict__ g, double* __restrict__ y,
+                                  const GmState* s)
+{
+    const int j = s->j, m = s->m;
+    for (int i = j - 1; i >= 0; --i) {
+        double acc = g[i];
+        for (int k = i + 1; k < j; ++k) acc -= H[i * m + k] * y[k];
+        y[i] = acc / H[i * m + i];
+    }
+}
+
+// x += sum_{c < j} y[c] V_c
+__global__ void __launch_bounds__(kRedThreads)
+    gm_update_x_kernel(int64_t n, double* __restrict__ x, const double* __restrict__ V, const double* __restrict__ y,
+                       const GmState* s)
+{
+    __shared__ double ys[128];
+    const int ncols = s->j;
+    for (int c = threadIdx.x; c < ncols; c += blockDim.x) ys[c] = y[c];
+    __syncthreads();
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(kRedThreads) + threadIdx.x; i < n;
+         i += static_cast<int64_t>(gridDim.x) * kRedThreads) {
+        double t = x[i];
+        for (int c = 0; c < ncols; ++c) t = fma(ys[c], V[c * n + i], t);
+        x[i] = t;
+    }
+}
+
+// out = w / s (s on the host)
 __global__ void gm_scale_kernel(int64_t n, double* __restrict__ out, const double* __restrict__ w, double s)
 {
     for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
@@ -1145,14 +1294,16 @@ __global__ void gm_scale_kernel(int64_t n, double* __restrict__ out, const doubl
 }
 
 // Restarted GMRES(m) (Saad and Schultz 1986) for general square A.  The
-// Arnoldi basis V (m + 1 vectors of n) lives in device memory; A v_j is
-// orthogonalised by classical Gram-Schmidt applied twice (each pass: one
-// multi-dot launch per 8 basis vectors with fixed-order partial sums, one
-// combination launch), its norm taken by one grid reduction; the (j + 2)
-// Hessenberg entries go to the host, which applies the Givens rotations and
-// reads the residual estimate (one synchronisation per step).  A cycle
-// ends at m steps or when the estimate is <= tol ||b||; x += V y, and the
-// next cycle starts from the FP64 true residual, which decides convergence.
+// Arnoldi basis V (m + 1 vectors of n) lives in device memory.  One cycle is
+// a CUDA graph whose WHILE node runs the Arnoldi steps: the product
+// w = A v_j, classical Gram-Schmidt applied twice (partial dots of the basis
+// with w, their fixed-order sum, the combination fused with the second
+// pass's dots, the second combination fused with ||w||), the next basis
+// vector, and the Givens step on the new Hessenberg column, all on the
+// device; the Givens kernel ends the loop when the residual estimate is
+// <= tol ||b||, at m steps or at maxit.  The host synchronises once per
+// cycle: x += V y (back substitution on the device), and the next cycle
+// starts from the FP64 true residual, which decides convergence.
 int gmres_solve(const gko_matrix* A, int fmt, const double* b, double* x, double tol, int m, int maxit,
                 cudaStream_t st, gko_solve_info* info)
 {
@@ -1162,15 +1313,24 @@ int gmres_solve(const gko_matrix* A, int fmt, const double* b, double* x, double
         return GKO_OK;
     }
     Workspace ws(st);
-    double *V, *w, *part, *h, *hsum;
+    double *V, *w, *vcur, *part, *H, *cs, *sn, *g, *hh, *coef, *yv;
     SolverState* ds;
+    GmState* gs;
     const int grid = red_grid(n);
+    const int ldp = m + 1;
     GKO_TRY(ws.get(&V, n * (m + 1)));
     GKO_TRY(ws.get(&w, n));
-    GKO_TRY(ws.get(&part, static_cast<int64_t>(kRedBlocks) * (m + 1) + 2 * kRedBlocks));
-    GKO_TRY(ws.get(&h, m + 1));
-    GKO_TRY(ws.get(&hsum, m + 1));
+    GKO_TRY(ws.get(&vcur, n));
+    GKO_TRY(ws.get(&part, static_cast<int64_t>(kRedBlocks) * ldp + 2 * kRedBlocks));
+    GKO_TRY(ws.get(&H, static_cast<int64_t>(m + 1) * m));
+    GKO_TRY(ws.get(&cs, m));
+    GKO_TRY(ws.get(&sn, m));
+    GKO_TRY(ws.get(&g, m + 1));
+    GKO_TRY(ws.get(&hh, m + 1));
+    GKO_TRY(ws.get(&coef, m + 1));
+    GKO_TRY(ws.get(&yv, m));
     GKO_TRY(ws.get(&ds, 1));
+    GKO_TRY(ws.get(&gs, 1));
     SolverState hs = {};
     GKO_TRY(write_state(ds, &hs, st));
     auto norm = [&](const double* v, double* out) -> int {
@@ -1187,16 +1347,27 @@ int gmres_solve(const gko_matrix* A, int fmt, const double* b, double* x, double
         fill_info(info, 0, 0, 0.0, GKO_OK);
         return GKO_OK;
     }
-    // V_c . w for c < ncols into h (device)
-    auto multidot = [&](int ncols, const double* vec) -> int {
-        for (int c0 = 0; c0 < ncols; c0 += kGmChunk)
-            gm_multidot_kernel<<<grid, kRedThreads, 0, st>>>(n, V, n, c0, std::min(kGmChunk, ncols - c0), vec, part,
-                                                              m + 1);
-        gm_reduce_kernel<<<1, 128, 0, st>>>(grid, ncols, part, m + 1, h);
+    GmState hg = {};
+    hg.bnorm = bnorm;
+    hg.tol = tol;
+    hg.m = m;
+    hg.maxit = maxit;
+    GKO_CUDA(cudaMemsetAsync(part, 0, (static_cast<int64_t>(kRedBlocks) * ldp + 2 * kRedBlocks) * sizeof(double), st));
+
+    GraphHolder gh;
+    GKO_TRY(build_while_graph(&gh, [&](cudaGraphConditionalHandle h, cudaStream_t cs_) -> int {
+        GKO_TRY(spmv_fmt(A, fmt, vcur, w, 1.0, 0.0, cs_));
+        gm_dots_kernel<<<grid, kRedThreads, 0, cs_>>>(n, V, w, part, ldp, gs);
+        gm_coef_kernel<<<1, 128, 0, cs_>>>(grid, part, ldp, coef, hh, 0, gs);
+        gm_combine_dots_kernel<<<grid, kRedThreads, 0, cs_>>>(n, V, w, coef, part, ldp, gs);
+        gm_coef_kernel<<<1, 128, 0, cs_>>>(grid, part, ldp, coef, hh, 1, gs);
+        gm_combine_norm_kernel<<<grid, kRedThreads, 0, cs_>>>(n, V, w, coef, part + static_cast<int64_t>(kRedBlocks) * ldp, gs);
+        gm_next_vector_kernel<<<grid, kRedThreads, 0, cs_>>>(n, V, vcur, w, gs);
+        gm_givens_kernel<<<1, 1, 0, cs_>>>(H, cs, sn, g, hh, gs, h);
         GKO_CUDA(cudaGetLastError());
         return GKO_OK;
-    };
-    std::vector<double> H(static_cast<size_t>(m + 1) * m, 0.0), cs(m), sn(m), g(m + 1), yv(m), hh(m + 2);
+    }));
+
     int status = GKO_ERR_NOT_CONVERGED, total = 0;
     double res = -1.0;
     while (true) {
@@ -1216,67 +1387,27 @@ int gmres_solve(const gko_matrix* A, int fmt, const double* b, double* x, double
         }
         if (total >= maxit) break;
         gm_scale_kernel<<<grid, kRedThreads, 0, st>>>(n, V, V, beta);
-        std::fill(g.begin(), g.end(), 0.0);
-        g[0] = beta;
-        int j = 0;
-        bool broke = false;
-        for (; j < m && total < maxit; ++j) {
-            double* vj1 = V + (j + 1) * n;
-            GKO_TRY(spmv_fmt(A, fmt, V + j * n, w, 1.0, 0.0, st));
-            total += 1;
-            // classical Gram-Schmidt, twice
-            std::fill(hh.begin(), hh.end(), 0.0);
-            for (int pass = 0; pass < 2; ++pass) {
-                GKO_TRY(multidot(j + 1, w));
-                gm_combine_kernel<<<grid, kRedThreads, 0, st>>>(n, w, V, n, j + 1, h, -1.0);
-                std::vector<double> hp(j + 1);
-                GKO_CUDA(cudaMemcpyAsync(hp.data(), h, (j + 1) * sizeof(double), cudaMemcpyDeviceToHost, st));
-                GKO_CUDA(cudaStreamSynchronize(st));
-                for (int i = 0; i <= j; ++i) hh[i] += hp[i];
-            }
-            double hn;
-            GKO_TRY(norm(w, &hn));
-            if (!(hn == hn)) {
-                broke = true;
-                break;
-            }
-            if (hn > 0.0) gm_scale_kernel<<<grid, kRedThreads, 0, st>>>(n, vj1, w, hn);
-            for (int i = 0; i <= j; ++i) H[static_cast<size_t>(i) * m + j] = hh[i];
-            H[static_cast<size_t>(j + 1) * m + j] = hn;
-            for (int i = 0; i < j; ++i) {  // earlier rotations on the new column
-                const double a = H[static_cast<size_t>(i) * m + j], c = H[static_cast<size_t>(i + 1) * m + j];
-                H[static_cast<size_t>(i) * m + j] = cs[i] * a + sn[i] * c;
-                H[static_cast<size_t>(i + 1) * m + j] = -sn[i] * a + cs[i] * c;
-            }
-            const double a = H[static_cast<size_t>(j) * m + j], c = H[static_cast<size_t>(j + 1) * m + j];
-            const double d = std::sqrt(a * a + c * c);
-            if (!(d > 0.0)) {
-                broke = true;
-                break;
-            }
-            cs[j] = a / d;
-            sn[j] = c / d;
-            H[static_cast<size_t>(j) * m + j] = d;
-            H[static_cast<size_t>(j + 1) * m + j] = 0.0;
-            g[j + 1] = -sn[j] * g[j];
-            g[j] = cs[j] * g[j];
-            if (std::fabs(g[j + 1]) <= tol * bnorm || !(hn > 0.0)) {
-                j += 1;
-                break;
-            }
-        }
-        if (broke) {
+        GKO_CUDA(cudaMemcpyAsync(vcur, V, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        GKO_CUDA(cudaMemsetAsync(g, 0, (m + 1) * sizeof(double), st));
+        GKO_CUDA(cudaMemcpyAsync(g, &beta, sizeof(double), cudaMemcpyHostToDevice, st));
+        hg.j = 0;
+        hg.total = total;
+        hg.stop = 0;
+        hg.broke = 0;
+        hg.hn = 0.0;
+        hg.ticket = 0;
+        GKO_CUDA(cudaMemcpyAsync(gs, &hg, sizeof(GmState), cudaMemcpyHostToDevice, st));
+        GKO_CUDA(cudaGraphLaunch(gh.exec, st));
+        GKO_CUDA(cudaMemcpyAsync(&hg, gs, sizeof(GmState), cudaMemcpyDeviceToHost, st));
+        GKO_CUDA(cudaStreamSynchronize(st));
+        total = hg.total;
+        if (hg.broke) {
             status = GKO_ERR_BREAKDOWN;
             break;
         }
-        for (int i = j - 1; i >= 0; --i) {  // back substitution
-            double sacc = g[i];
-            for (int k = i + 1; k < j; ++k) sacc -= H[static_cast<size_t>(i) * m + k] * yv[k];
-            yv[i] = sacc / H[static_cast<size_t>(i) * m + i];
-        }
-        if (j > 0) {
-            GKO_CUDA(cudaMemcpyAsync(hsum, yv.data(), j * sizeof(double), cudaMemcpyHostToDevice, st));
-            gm_combine_kernel<<<grid, kRedThreads, 0, st>>>(n, x, V, n, j, hsum, 1.0);
+        if (hg.j > 0) {
+            gm_backsub_kernel<<<1, 1, 0, st>>>(H, g, yv, gs);
+            gm_update_x_kernel<<<grid, kRedThreads, 0, st>>>(n, x, V, yv, gs);
             GKO_CUDA(cudaGetLastError());
         }
     }
@@ -1393,7 +1524,7 @@ static cudaError_t inner_spmv(const gko_matrix* A, const V* val, SegScratchT<flo
         else
             return rowblock_lowprec_f32(A, val, p, q, st);
     }
-    return seg_launch<kSegP, V, float, false, false, false, false>(A->n_rows, A->nnz, A->csr.row_ptr, nullptr,
+    return seg_launch<kSegP, V, float, false, false, false, false>(A->n_rows, A->n_cols, A->nnz, A->csr.row_ptr, nullptr,
                                                                    A->csr.col, val, A->csr.thr_row, sc, p, q, 1.0f,
                                                                    0.0f, A->d_err, st);
 }

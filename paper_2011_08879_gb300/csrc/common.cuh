@@ -163,8 +163,38 @@ __device__ __forceinline__ T ldg(const T* p)
     return __ldg(p);
 }
 
+// ldg as a volatile load: issued where it stands in the source (the
+// compiler neither removes it nor moves it into the branches that use it).
+template <typename T>
+__device__ __forceinline__ T ldg_early(const T* p)
+{
+    if constexpr (sizeof(T) == 8) {
+        double v;
+        asm volatile("ld.global.nc.f64 %0, [%1];" : "=d"(v) : "l"(p));
+        return static_cast<T>(v);
+    } else {
+        float v;
+        asm volatile("ld.global.nc.f32 %0, [%1];" : "=f"(v) : "l"(p));
+        return static_cast<T>(v);
+    }
+}
+
 // ----------------------------------------------------------- host helpers
 
 inline int ceil_div(int64_t a, int64_t b) { return static_cast<int>((a + b - 1) / b); }
+
+// SM count of the current device, looked up once per device (thread-safe).
+int device_sm_count();
+
+// Raise a kernel's dynamic shared-memory limit to at least `bytes` on the
+// current device.  cudaFuncSetAttribute acts on the current device only, so
+// the library remembers the limit per (kernel, device) and calls it again
+// for each new device or larger size (thread-safe).
+cudaError_t smem_limit_once(const void* kernel, int bytes);
+
+// Poll limit of the first bounded wait for a bulk copy in the staged
+// kernels (default 2^22 polls; gko_set_wait_limit changes it, for tests of
+// the timeout path).  Read by the launchers and passed to the kernels.
+uint32_t first_wait_polls();
 
 }  // namespace gko

@@ -58,6 +58,7 @@ inline int64_t padded_len(int64_t n) { return (n + 15) / 16 * 16 + 16; }
 
 constexpr int kSegP = 15;     // entries per thread of the load-balanced CSR kernel (and thr_row)
 constexpr int kSegPCoo = 11;  // entries per thread of the load-balanced COO kernel
+constexpr int kSegThreadsCoo = 64;  // threads per CTA (and per tile) of the load-balanced COO kernel
 
 // ------------------------------------------------------------ the handle
 
@@ -146,6 +147,8 @@ struct gko_matrix {
     gko::LowPrecEll lp_ell;          // ELL layout of those copies (when padding is small)
     bool feats_valid = false;
     double feats[12] = {0};
+    int auto_fmt = -1, auto_cfg = 0;  // cached GKO_FMT_AUTO choice (-1: not made yet)
+    uint64_t auto_key = 0;            // selector generation and format mask it was made for
 };
 
 struct gko_batch {
@@ -163,6 +166,13 @@ struct gko_batch {
     int32_t max_rows = 0;
     int best_block = 0;           // autotuned block size (0 = not tuned)
     uint32_t* d_err = nullptr;
+    // instantiated graph of the last solve [queue reset + kernel], relaunched
+    // while the launch arguments stay the same
+    cudaGraphExec_t graph = nullptr;
+    int graph_bs = 0, graph_maxit = 0;
+    const double* graph_b = nullptr;
+    double* graph_x = nullptr;
+    double graph_tol = 0.0;
 };
 
 namespace gko {
@@ -170,7 +180,7 @@ namespace gko {
 // Launchers exported by the kernel translation units.  All asynchronous on
 // the given stream; they validate nothing (the C-ABI layer does).
 int csr_analyse(gko_matrix* A, cudaStream_t st);
-int seg_alloc(SegArrays* s, int64_t nnz, int P);
+int seg_alloc(SegArrays* s, int64_t nnz, int P, int threads);
 void seg_free(SegArrays* s);
 int spmv_csr(const gko_matrix* A, int config, const double* x, double* y, double alpha, double beta,
              cudaStream_t st);
@@ -238,5 +248,11 @@ int cg_mixed_solve(gko_matrix* A, int inner, const double* b, double* x, double 
 
 // selector (selector.cu)
 int features_compute(const gko_matrix* A, double* out_host, cudaStream_t st);
+uint64_t selector_generation();  // 0: no selector installed; changes with every gko_selector_load/clear
+
+// the (format, configuration) candidates of the exhaustive autotuner, in the
+// order of the public table (GKO_N_CANDIDATES)
+extern const int kCandFmt[GKO_N_CANDIDATES];
+extern const int kCandCfg[GKO_N_CANDIDATES];
 
 }  // namespace gko

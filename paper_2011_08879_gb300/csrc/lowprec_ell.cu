@@ -314,7 +314,7 @@ template <typename V, typename I, int KC>
 __global__ void __launch_bounds__(kLpThreads, 2)
     lp_ell_tma_cg1_kernel(int64_t n, int64_t n_pad, int K, int R, const I* __restrict__ col,
                           const V* __restrict__ val, const float* __restrict__ r, const float* __restrict__ rd,
-                          float* __restrict__ w, uint32_t* err, Cg1Reduce red)
+                          float* __restrict__ w, uint32_t* err, Cg1Reduce red, uint32_t polls)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ uint64_t bar[2];
@@ -354,9 +354,15 @@ __global__ void __launch_bounds__(kLpThreads, 2)
         if (b >= n_stages) break;
         const int st = it & 1;
         const uint32_t parity = (it >> 1) & 1;
-        bool landed = mbar_wait_bounded(&bar[st], parity, err);
-        if (!landed) landed = mbar_wait_bounded(&bar[st], parity, err);
+        const bool landed = mbar_wait_bounded(&bar[st], parity, err, polls);
         if (!__syncthreads_and(landed)) {  // CTA-uniform: give up on the rest
+            // wait (default limit) for the copies still in flight into this
+            // stage and the next one, so none lands after the CTA has exited
+            if (tid == 0) {
+                mbar_wait_bounded(&bar[st], parity, err);
+                if (b + stride < n_stages) mbar_wait_bounded(&bar[st ^ 1], ((it + 1) >> 1) & 1, err);
+            }
+            __syncthreads();
             failed = true;
             break;
         }
@@ -438,15 +444,12 @@ static cudaError_t launch_lp_tma_k(const gko_matrix* A, const V* val, const floa
                                    Cg1Reduce red, int R, int grid, cudaStream_t st)
 {
     const LowPrecEll& E = A->lp_ell;
-    static bool attr = false;
-    if (!attr) {
-        const cudaError_t e = cudaFuncSetAttribute(lp_ell_tma_cg1_kernel<V, I, KC>,
-                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * kLpStageBytes);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    const cudaError_t e =
+        smem_limit_once(reinterpret_cast<const void*>(lp_ell_tma_cg1_kernel<V, I, KC>), 2 * kLpStageBytes);
+    if (e != cudaSuccess) return e;
     lp_ell_tma_cg1_kernel<V, I, KC><<<grid, kLpThreads, 2 * kLpStageBytes, st>>>(
-        A->n_rows, E.n_pad, static_cast<int>(E.K), R, static_cast<const I*>(E.col), val, r, rd, w, A->d_err, red);
+        A->n_rows, E.n_pad, static_cast<int>(E.K), R, static_cast<const I*>(E.col), val, r, rd, w, A->d_err, red,
+        first_wait_polls());
     return cudaGetLastError();
 }
 
@@ -458,10 +461,7 @@ static cudaError_t launch_lp_tma(const gko_matrix* A, const V* val, const float*
     const int K = static_cast<int>(E.K);
     const int R = lp_stage_rows<V, I>(K);
     const int64_t n_stages = (E.n_pad + R - 1) / R;
-    int sms = 0, dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int grid = static_cast<int>(std::min<int64_t>(n_stages, 2 * std::max(sms, 1)));
+    const int grid = static_cast<int>(std::min<int64_t>(n_stages, 2 * device_sm_count()));
     switch (K) {
         case 5: return launch_lp_tma_k<V, I, 5>(A, val, r, rd, w, red, R, grid, st);
         case 7: return launch_lp_tma_k<V, I, 7>(A, val, r, rd, w, red, R, grid, st);

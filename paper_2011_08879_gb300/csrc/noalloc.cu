@@ -85,8 +85,8 @@ extern "C" int gko_spmv_coo_noalloc(int64_t n_rows, int64_t n_cols, int64_t nnz,
     const bool a = alpha != 1.0, b = beta != 0.0;
     cudaError_t e;
 #define GKO_NA(KA, KB)                                                                                        \
-    e = seg_launch<kSegPCoo, double, double, KA, KB, true, false, true>(n_rows, nnz, nullptr, row, col, val, \
-                                                                        nullptr, sc, x, y, alpha, beta,      \
+    e = seg_launch<kSegPCoo, double, double, KA, KB, true, false, true>(n_rows, n_cols, nnz, nullptr, row, col, \
+                                                                        val, nullptr, sc, x, y, alpha, beta, \
                                                                         err_flags, st)
     if (a && b)
         GKO_NA(true, true);

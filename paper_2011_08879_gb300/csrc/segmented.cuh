@@ -6,9 +6,10 @@
 // this kernel is built to issue close to one FP64 instruction per stored
 // entry whatever the row lengths are:
 //
-//  * the stored entries are cut into tiles of TILE = 256 * P consecutive
-//    entries; a persistent grid (2 CTAs of 256 threads per SM) walks the
-//    tiles round robin with two shared-memory stages: while one tile is
+//  * the stored entries are cut into tiles of TILE = NT * P consecutive
+//    entries; a persistent grid of CTAs of NT threads (512 threads per SM:
+//    2 CTAs of 256 for CSR, 8 CTAs of 64 for COO) walks the tiles round
+//    robin with two shared-memory stages: while one tile is
 //    summed, the next one's values, column indices and row pointers (COO:
 //    row indices) stream in through 1-D bulk copies (TMA) completing on an
 //    mbarrier;
@@ -33,8 +34,9 @@
 
 namespace gko {
 
-constexpr int kSegThreads = 256;
-constexpr int kSegCtasPerSm = 2;
+constexpr int kSegThreads = 256;        // threads per CTA (= per tile) unless a launch picks NT
+constexpr int kSegThreadsPerSm = 512;   // resident threads per SM (registers, shared memory)
+constexpr int kSegCtasPerSm = kSegThreadsPerSm / kSegThreads;
 
 // Per-tile carries of rows that cross tile boundaries.
 template <typename T>
@@ -47,27 +49,27 @@ struct SegScratchT {
 };
 using SegScratch = SegScratchT<double>;
 
-template <int P>
+template <int P, int NT = kSegThreads>
 struct SegShape {
-    static constexpr int kTile = kSegThreads * P;  // a multiple of 8 entries for the P used here
+    static constexpr int kTile = NT * P;  // a multiple of 8 entries for the P and NT used here
     static constexpr int kBuf = kTile + 8;         // bulk copies move whole 16-byte groups
     static constexpr int kRowStage = 2048;         // CSR row_ptr entries staged per tile
 };
 
 // one pipeline stage: values | column indices | (COO rows or CSR row_ptr)
-template <int P, typename V, bool kCoo>
+template <int P, typename V, bool kCoo, int NT = kSegThreads>
 struct SegStage {
-    static constexpr size_t kVal = SegShape<P>::kBuf * sizeof(V);
-    static constexpr size_t kCol = SegShape<P>::kBuf * sizeof(int32_t);
-    static constexpr size_t kAux = (kCoo ? SegShape<P>::kBuf : SegShape<P>::kRowStage) * sizeof(int32_t);
+    static constexpr size_t kVal = SegShape<P, NT>::kBuf * sizeof(V);
+    static constexpr size_t kCol = SegShape<P, NT>::kBuf * sizeof(int32_t);
+    static constexpr size_t kAux = (kCoo ? SegShape<P, NT>::kBuf : SegShape<P, NT>::kRowStage) * sizeof(int32_t);
     static constexpr size_t kBytes = kVal + kCol + kAux;
     static_assert(kVal % 16 == 0 && kCol % 16 == 0 && kAux % 16 == 0, "16-byte aligned stage parts");
 };
 
-template <int P, typename V, typename T, bool kCoo>
+template <int P, typename V, typename T, bool kCoo, int NT = kSegThreads>
 constexpr size_t seg_smem_bytes()
 {
-    return 2 * SegStage<P, V, kCoo>::kBytes + kSegThreads * (sizeof(T) + sizeof(int32_t)) +
+    return 2 * SegStage<P, V, kCoo, NT>::kBytes + NT * (sizeof(T) + sizeof(int32_t)) +
            8 * (sizeof(T) + sizeof(int32_t)) + 16;
 }
 
@@ -309,6 +311,123 @@ __device__ __forceinline__ SegThreadOut<T> seg_thread(int ls, int le, int t0, in
     return o;
 }
 
+// Phase 1 of one tile for one thread, COO.  The thread's entries
+// [ls, ls + rem) are loaded with their rows; a bit mask marks the entries
+// after which a row ends (the row of the next entry differs; rows are
+// sorted), so the row structure costs one compare per entry.  Fast path
+// (at most three row ends, no row without entries in between): one FMA per
+// entry into a single running sum that is stored and reset at each end;
+// the first finished row goes to fin when it began before the thread.
+// kFull: every thread of the tile holds P entries (all tiles but the last),
+// so no per-entry bounds predicates are needed.
+template <int P, typename V, typename T, bool kAlpha, bool kBeta, bool kSkipEmpty, bool kFull>
+__device__ __forceinline__ SegThreadOut<T> seg_thread_coo(int ls, int rem, int t0, int cnt, const V* s_val,
+                                                          const int32_t* s_col, const int32_t* s_row,
+                                                          bool first_carried, int next_r_tile,
+                                                          const T* __restrict__ x, T* __restrict__ y, T alpha, T beta)
+{
+    SegThreadOut<T> o{-1, T(0), -1, T(0)};
+    T vv[P], xv[P];
+    int rr[P];
+    // the gathers of x are issued first, as volatile loads, so that they are
+    // all in flight before the row logic and are not moved to their uses
+    // behind the warp vote (random columns miss in L1 and L2)
+#pragma unroll
+    for (int j = 0; j < P; ++j) {
+        const bool ok = kFull || j < rem;
+        const int c = ok ? s_col[ls + j] : 0;
+        vv[j] = ok ? to_t<V, T>(s_val[ls + j]) : T(0);
+        xv[j] = ldg_early(x + c);
+    }
+#pragma unroll
+    for (int j = 0; j < P; ++j) rr[j] = (kFull || j < rem) ? s_row[ls + j] : 0;
+    // NOTE: lanes without entries must not return before the warp vote below.
+    const bool has = rem > 0;
+    const int n_mine = kFull ? P : max(0, min(rem, P));
+    const int after = ls + n_mine;  // position after the thread's last entry
+    const int r_next = has ? (after < cnt ? s_row[after] : next_r_tile) : 0;
+    const int r_first = rr[0];
+    const bool ob = has && ((ls == 0) ? first_carried : (s_row[ls - 1] == r_first));
+    uint32_t mask = 0;  // bit j: a row ends after entry j
+#pragma unroll
+    for (int j = 0; j < P; ++j) {
+        if (kFull || j < n_mine) {
+            const int nx = (j + 1 < P && (kFull || j + 1 < n_mine)) ? rr[j + 1] : r_next;
+            mask |= static_cast<uint32_t>(nx != rr[j]) << j;
+        }
+    }
+    const int n_end = __popc(mask);
+    // rows are sorted: a row without entries lies between the thread's first
+    // row and the next one exactly when they are further apart than the
+    // number of row changes
+    const bool gap = has && (r_next - r_first > n_end);
+    if (has && !kSkipEmpty && t0 + ls == 0)  // rows before the first stored entry
+        for (int r = 0; r < r_first; ++r) seg_store<kAlpha, kBeta>(y, r, T(0), alpha, beta);
+    const bool fast = n_end <= 3 && (kSkipEmpty || !gap);
+    const bool warp_fast = __all_sync(0xffffffffu, fast);  // every lane of the warp reaches this
+    if (!has) return o;
+    if (warp_fast) {
+        const int e0 = __ffs(mask);  // 1 + position of the first end (0: none)
+        T acc = T(0), f0 = T(0);
+#pragma unroll
+        for (int j = 0; j < P; ++j) {
+            if (kFull || j < n_mine) {
+                acc = fma(vv[j], xv[j], acc);
+                const bool end = (mask >> j) & 1u;
+                const bool first = j + 1 == e0;
+                if (end && !(first && ob)) seg_store<kAlpha, kBeta>(y, rr[j], acc, alpha, beta);
+                f0 = first ? acc : f0;
+                acc = end ? T(0) : acc;
+            }
+        }
+        if (ob && n_end > 0) {
+            o.fin_row = r_first;
+            o.fin_val = f0;
+        }
+        if (!((mask >> (n_mine - 1)) & 1u)) {  // the last entry's row is still open
+            o.open_row = rr[kFull ? P - 1 : 0];
+            if (!kFull)
+#pragma unroll
+                for (int j = 1; j < P; ++j)
+                    if (j < n_mine) o.open_row = rr[j];
+            o.open_val = acc;
+        }
+        return o;
+    }
+
+    // ---- general path: any number of row ends, empty rows included
+    T acc = T(0);
+    bool pending = false, obb = ob;
+    int row = r_first;
+#pragma unroll
+    for (int j = 0; j < P; ++j) {
+        if (kFull || j < n_mine) {
+            acc = fma(vv[j], xv[j], acc);
+            pending = true;
+            const int nr = (j + 1 < P && (kFull || j + 1 < n_mine)) ? rr[j + 1] : r_next;
+            if (nr != row) {
+                if (obb) {
+                    o.fin_row = row;
+                    o.fin_val = acc;
+                } else {
+                    seg_store<kAlpha, kBeta>(y, row, acc, alpha, beta);
+                }
+                acc = T(0);
+                pending = false;
+                obb = false;
+                if (!kSkipEmpty)
+                    for (int r = row + 1; r < nr; ++r) seg_store<kAlpha, kBeta>(y, r, T(0), alpha, beta);
+                row = nr;
+            }
+        }
+    }
+    if (pending) {
+        o.open_row = row;
+        o.open_val = acc;
+    }
+    return o;
+}
+
 // kCoo = false: CSR with row_ptr and the per-thread start rows thr_row
 // (thr_row[g] = row holding entry g*P).  kCoo = true: COO with row[].
 // kSkipEmpty: rows without entries are left untouched (used to add the COO
@@ -316,21 +435,24 @@ __device__ __forceinline__ SegThreadOut<T> seg_thread(int ls, int le, int t0, in
 // kExactTail (COO only): the arrays end exactly at nnz (caller-owned, not
 // padded), so the last tile bulk-copies only whole 16-byte groups and the
 // threads load the remaining few entries themselves.
-template <int P, typename V, typename T, bool kAlpha, bool kBeta, bool kCoo, bool kSkipEmpty, bool kExactTail = false>
-__global__ void __launch_bounds__(kSegThreads, kSegCtasPerSm)
-    seg_spmv_kernel(int64_t n_rows64, int64_t nnz64, const int32_t* __restrict__ row_ptr,
+// NT: threads per CTA and per tile (a multiple of 32, at most 256).
+template <int P, typename V, typename T, bool kAlpha, bool kBeta, bool kCoo, bool kSkipEmpty, bool kExactTail = false,
+          int NT = kSegThreads>
+__global__ void __launch_bounds__(NT, kSegThreadsPerSm / NT)
+    seg_spmv_kernel(int64_t n_rows64, int64_t n_cols64, int64_t nnz64, const int32_t* __restrict__ row_ptr,
                     const int32_t* __restrict__ rows, const int32_t* __restrict__ col,
                     const V* __restrict__ val, const int32_t* __restrict__ thr_row, const T* __restrict__ x,
-                    T* __restrict__ y, T alpha, T beta, SegScratchT<T> sc, uint32_t* err)
+                    T* __restrict__ y, T alpha, T beta, SegScratchT<T> sc, uint32_t* err, uint32_t polls)
 {
-    using S = SegShape<P>;
-    using G = SegStage<P, V, kCoo>;
+    using S = SegShape<P, NT>;
+    using G = SegStage<P, V, kCoo, NT>;
     static_assert(!kExactTail || kCoo, "exact tails are implemented for COO");
+    static_assert(NT % 32 == 0 && NT <= 256, "whole warps, at most 8 (s_wsum)");
     constexpr int kAlign = 16 / sizeof(V) > 4 ? 16 / sizeof(V) : 4;  // entries per 16-byte group
     extern __shared__ __align__(16) unsigned char smem[];
     T* s_part = reinterpret_cast<T*>(smem + 2 * G::kBytes);
-    int32_t* s_prow = reinterpret_cast<int32_t*>(s_part + kSegThreads);
-    T* s_wsum = reinterpret_cast<T*>(s_prow + kSegThreads);
+    int32_t* s_prow = reinterpret_cast<int32_t*>(s_part + NT);
+    T* s_wsum = reinterpret_cast<T*>(s_prow + NT);
     int32_t* s_wrow = reinterpret_cast<int32_t*>(s_wsum + 8);
     __shared__ uint64_t bar[2];
     __shared__ SegTileInfo info[2];
@@ -388,20 +510,25 @@ __global__ void __launch_bounds__(kSegThreads, kSegCtasPerSm)
     // metadata loads needed to issue `tile` (read early, used later)
     auto meta_a = [&](int tile) -> int32_t {
         if (kCoo) return tile > 0 ? rows[tile * S::kTile - 1] : -1;
-        return thr_row[tile * kSegThreads];
+        return thr_row[tile * NT];
     };
     auto meta_b = [&](int tile) -> int32_t {
         if (kCoo) return rows[tile * S::kTile];
-        return (tile + 1) * S::kTile < nnz ? thr_row[(tile + 1) * kSegThreads] : n_rows;
+        return (tile + 1) * S::kTile < nnz ? thr_row[(tile + 1) * NT] : n_rows;
     };
     auto meta_c = [&](int tile) -> int32_t {
         if (!kCoo) return 0;
-        return (tile + 1) * S::kTile < nnz ? rows[(tile + 1) * S::kTile] : n_rows;
+        const int32_t r = (tile + 1) * S::kTile < nnz ? rows[(tile + 1) * S::kTile] : n_rows;
+#ifdef GKO_CHECK_BOUNDS
+        return min(max(r, 0), n_rows);  // bounds rows of empty-row stores at n_rows
+#else
+        return r;
+#endif
     };
     // start row of this thread's entries in a tile (threads whose first
     // entry exists only: thr_row has ceil(nnz / P) entries)
     auto start_row = [&](int tile) -> int32_t {
-        const int g = tile * kSegThreads + tid;
+        const int g = tile * NT + tid;
         return (!kCoo && tile < n_tiles && static_cast<int64_t>(g) * P < nnz) ? thr_row[g] : 0;
     };
 
@@ -425,19 +552,59 @@ __global__ void __launch_bounds__(kSegThreads, kSegCtasPerSm)
         if (tile >= n_tiles) break;
         const int st = it & 1;
         const uint32_t parity = (it >> 1) & 1;
-        bool landed = mbar_wait_bounded(&bar[st], parity, err);
-        if (!landed) landed = mbar_wait_bounded(&bar[st], parity, err);  // copies still in flight: once more
-        if (!__syncthreads_and(landed)) return;                           // CTA-uniform exit
+        const bool landed = mbar_wait_bounded(&bar[st], parity, err, polls);
+        if (!__syncthreads_and(landed)) {  // CTA-uniform exit (y is left undefined)
+            // first wait for the copies this CTA still has in flight (this
+            // stage and the next tile's, default limit), so that no bulk copy
+            // writes its shared memory after it has exited
+            if (tid == 0) {
+                mbar_wait_bounded(&bar[st], parity, err);
+                if (tile + stride < n_tiles) mbar_wait_bounded(&bar[st ^ 1], ((it + 1) >> 1) & 1, err);
+            }
+            // the tiles left undone carry nothing: the fix-up then reads only
+            // carries written in this launch
+            for (int t = tile + tid * stride; t < n_tiles; t += NT * stride) {
+                sc.head_row[t] = -1;
+                sc.tail_row[t] = -1;
+            }
+            __syncthreads();
+            return;
+        }
         if (kExactTail) {  // entries past the last whole 16-byte group (last tile only)
             const int tx0 = info[st].t0;
             const int cx = min(tx0 + S::kTile, nnz) - tx0;
-            for (int i = cx / kAlign * kAlign + tid; i < cx; i += kSegThreads) {
+            for (int i = cx / kAlign * kAlign + tid; i < cx; i += NT) {
                 stage_val(st)[i] = val[tx0 + i];
                 stage_col(st)[i] = col[tx0 + i];
                 stage_aux(st)[i] = rows[tx0 + i];
             }
             __syncthreads();
         }
+#ifdef GKO_CHECK_BOUNDS
+        // checked build: indices the caller did not validate (the allocation-
+        // free COO entry) are checked in shared memory before use; an entry
+        // with a column or row out of range gets column 0 (row n_rows - 1)
+        // and value 0 and kErrBadIndex is raised: no load or store leaves
+        // the arrays (a bad column then adds nothing; a bad row may leave y
+        // wrong, which the error bit reports)
+        if constexpr (kCoo && sizeof(V) == 8) {
+            const int cx = min(info[st].t0 + S::kTile, nnz) - info[st].t0;
+            int32_t* sc_col = stage_col(st);
+            int32_t* sc_row = stage_aux(st);
+            V* sc_val = stage_val(st);
+            for (int i = tid; i < cx; i += NT) {
+                const bool bad_c = static_cast<uint32_t>(sc_col[i]) >= static_cast<uint32_t>(n_cols64);
+                const bool bad_r = static_cast<uint32_t>(sc_row[i]) >= static_cast<uint32_t>(n_rows);
+                if (bad_c || bad_r) {
+                    raise_error(err, kErrBadIndex);
+                    sc_col[i] = 0;
+                    sc_val[i] = V(0);
+                    if (bad_r) sc_row[i] = n_rows - 1;
+                }
+            }
+            __syncthreads();
+        }
+#endif
 
         // prefetch what the next issue and the next tile need
         const int t_issue = tile + 2 * stride;
@@ -460,11 +627,16 @@ __global__ void __launch_bounds__(kSegThreads, kSegCtasPerSm)
         const int first_row = ti.r_lo;
         bool first_carried;
         SegThreadOut<T> o;
-        if (kCoo) {
+        if constexpr (kCoo) {
             first_carried = ti.began != 0;
-            o = seg_thread<P, V, T, kAlpha, kBeta, kCoo, kSkipEmpty>(ls, le, t0, cnt, n_rows, s_val, s_col, s_aux,
-                                                                     s_aux, first_row, first_carried, ti.next_r,
-                                                                     my_row, x, y, alpha, beta);
+            if (cnt == S::kTile)  // tile-uniform: every thread holds P entries
+                o = seg_thread_coo<P, V, T, kAlpha, kBeta, kSkipEmpty, true>(ls, le - ls, t0, cnt, s_val, s_col,
+                                                                            s_aux, first_carried, ti.next_r, x, y,
+                                                                            alpha, beta);
+            else
+                o = seg_thread_coo<P, V, T, kAlpha, kBeta, kSkipEmpty, false>(ls, le - ls, t0, cnt, s_val, s_col,
+                                                                             s_aux, first_carried, ti.next_r, x, y,
+                                                                             alpha, beta);
         } else if (ti.staged) {
             const int32_t* rps = s_aux - ti.a_lo;  // shared memory, indexed by global row
             first_carried = rps[first_row] < t0;
@@ -560,39 +732,29 @@ __global__ void seg_fixup_kernel(int64_t n_tiles, SegScratchT<T> sc, T* __restri
     seg_store<kAlpha, kBeta>(y, r, total, alpha, beta);
 }
 
-inline int seg_grid_ctas()
-{
-    static int sms = 0;
-    if (!sms) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (sms <= 0) sms = 1;
-    }
-    return sms * kSegCtasPerSm;
-}
+// 2 CTAs per SM (the row-block CSR kernel's grid uses the same count)
+inline int seg_grid_ctas() { return device_sm_count() * kSegCtasPerSm; }
 
 // Host-side launcher of the load-balanced kernel + fix-up for one
-// (V, T) pair.  sc must hold ceil(nnz / TILE) tiles.  Sets the dynamic
-// shared-memory attribute on first use (per instantiation).
-template <int P, typename V, typename T, bool kAlpha, bool kBeta, bool kCoo, bool kSkip, bool kExact = false>
-inline cudaError_t seg_launch(int64_t n_rows, int64_t nnz, const int32_t* row_ptr, const int32_t* rows,
+// (V, T) pair.  sc must hold ceil(nnz / (NT * P)) tiles.  Raises the dynamic
+// shared-memory limit once per instantiation and device.
+template <int P, typename V, typename T, bool kAlpha, bool kBeta, bool kCoo, bool kSkip, bool kExact = false,
+          int NT = kSegThreads>
+inline cudaError_t seg_launch(int64_t n_rows, int64_t n_cols, int64_t nnz, const int32_t* row_ptr, const int32_t* rows,
                               const int32_t* col, const V* val, const int32_t* thr_row, SegScratchT<T> sc,
                               const T* x, T* y, T alpha, T beta, uint32_t* err, cudaStream_t st)
 {
-    constexpr size_t smem = seg_smem_bytes<P, V, T, kCoo>();
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(seg_spmv_kernel<P, V, T, kAlpha, kBeta, kCoo, kSkip, kExact>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
-    const int64_t tiles = (nnz + SegShape<P>::kTile - 1) / SegShape<P>::kTile;
-    const int64_t grid = tiles < seg_grid_ctas() ? tiles : seg_grid_ctas();
-    seg_spmv_kernel<P, V, T, kAlpha, kBeta, kCoo, kSkip, kExact>
-        <<<static_cast<unsigned>(grid), kSegThreads, smem, st>>>(n_rows, nnz, row_ptr, rows, col, val, thr_row, x, y,
-                                                                 alpha, beta, sc, err);
+    constexpr size_t smem = seg_smem_bytes<P, V, T, kCoo, NT>();
+    const cudaError_t e = smem_limit_once(
+        reinterpret_cast<const void*>(seg_spmv_kernel<P, V, T, kAlpha, kBeta, kCoo, kSkip, kExact, NT>),
+        static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    const int64_t tiles = (nnz + SegShape<P, NT>::kTile - 1) / SegShape<P, NT>::kTile;
+    const int64_t ctas = static_cast<int64_t>(device_sm_count()) * (kSegThreadsPerSm / NT);
+    const int64_t grid = tiles < ctas ? tiles : ctas;
+    seg_spmv_kernel<P, V, T, kAlpha, kBeta, kCoo, kSkip, kExact, NT>
+        <<<static_cast<unsigned>(grid), NT, smem, st>>>(n_rows, n_cols, nnz, row_ptr, rows, col, val, thr_row, x, y,
+                                                        alpha, beta, sc, err, first_wait_polls());
     if (tiles > 1)
         seg_fixup_kernel<kAlpha, kBeta, T>
             <<<static_cast<unsigned>((tiles + 255) / 256), 256, 0, st>>>(tiles, sc, y, alpha, beta);

@@ -254,6 +254,13 @@ struct Selector {
 };
 static Selector g_sel;
 static std::mutex g_sel_mu;
+static uint64_t g_sel_gen = 0;  // bumped by every load/clear; 0 until the first load
+
+uint64_t selector_generation()
+{
+    std::lock_guard<std::mutex> lk(g_sel_mu);
+    return g_sel.loaded ? g_sel_gen : 0;
+}
 
 }  // namespace gko
 
@@ -342,6 +349,17 @@ int gko_selector_load(const float* params_host, int n_out, const double* feat_me
     GKO_CUDA(cudaMemcpy(g_sel.d_params, g_sel.params.data(), cnt * sizeof(float), cudaMemcpyHostToDevice));
     GKO_CUDA(cudaGetDevice(&g_sel.device));
     g_sel.loaded = true;
+    ++g_sel_gen;
+    return GKO_OK;
+}
+
+int gko_selector_clear(void)
+{
+    std::lock_guard<std::mutex> lk(g_sel_mu);
+    if (g_sel.d_params) cudaFree(g_sel.d_params);
+    g_sel.d_params = nullptr;
+    g_sel.loaded = false;
+    ++g_sel_gen;
     return GKO_OK;
 }
 

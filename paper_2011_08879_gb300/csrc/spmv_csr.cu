@@ -163,10 +163,10 @@ static int csr_build_bins(gko_matrix* A, cudaStream_t st)
     return s;
 }
 
-int seg_alloc(SegArrays* s, int64_t nnz, int P)
+int seg_alloc(SegArrays* s, int64_t nnz, int P, int threads)
 {
     seg_free(s);
-    const int64_t tile = static_cast<int64_t>(kSegThreads) * P;
+    const int64_t tile = static_cast<int64_t>(threads) * P;
     s->n_tiles = (nnz + tile - 1) / tile;
     const int64_t t = std::max<int64_t>(s->n_tiles, 1);
     GKO_TRY(dev_alloc(&s->tail_val, t));
@@ -203,7 +203,7 @@ int csr_analyse(gko_matrix* A, cudaStream_t st)
     GKO_TRY(dev_alloc(&c.thr_row, std::max<int64_t>(n_thr, 1)));
     if (n_thr > 0)
         thr_row_kernel<<<ceil_div(n_thr, 256), 256, 0, st>>>(A->n_rows, n_thr, kSegP, c.row_ptr, c.thr_row);
-    GKO_TRY(seg_alloc(&c.seg, A->nnz, kSegP));
+    GKO_TRY(seg_alloc(&c.seg, A->nnz, kSegP, kSegThreads));
     int32_t* d_stats;
     GKO_TRY(dev_alloc(&d_stats, 2));
     GKO_CUDA(cudaMemsetAsync(d_stats, 0, 2 * sizeof(int32_t), st));
@@ -416,7 +416,7 @@ static SegScratch scratch_of(const SegArrays& sa)
     return SegScratch{sa.tail_val, sa.tail_row, sa.tail_pass, sa.head_val, sa.head_row};
 }
 
-int launch_seg(int64_t n_rows, int64_t nnz, const int32_t* row_ptr, const int32_t* rows, const int32_t* col,
+int launch_seg(int64_t n_rows, int64_t n_cols, int64_t nnz, const int32_t* row_ptr, const int32_t* rows, const int32_t* col,
                const double* val, const int32_t* thr_row, const SegArrays& sa, const double* x, double* y,
                double alpha, double beta, uint32_t* err, bool coo, cudaStream_t st, bool accumulate)
 {
@@ -425,21 +425,21 @@ int launch_seg(int64_t n_rows, int64_t nnz, const int32_t* row_ptr, const int32_
     if (accumulate) {  // y += alpha * A x, rows without entries untouched
         if (nnz == 0) return GKO_OK;
         if (alpha != 1.0)
-            e = seg_launch<kSegPCoo, double, double, true, true, true, true>(n_rows, nnz, row_ptr, rows, col, val,
-                                                                         thr_row, sc, x, y, alpha, 1.0, err, st);
+            e = seg_launch<kSegPCoo, double, double, true, true, true, true, false, kSegThreadsCoo>(
+                n_rows, n_cols, nnz, row_ptr, rows, col, val, thr_row, sc, x, y, alpha, 1.0, err, st);
         else
-            e = seg_launch<kSegPCoo, double, double, false, true, true, true>(n_rows, nnz, row_ptr, rows, col, val,
-                                                                          thr_row, sc, x, y, alpha, 1.0, err, st);
+            e = seg_launch<kSegPCoo, double, double, false, true, true, true, false, kSegThreadsCoo>(
+                n_rows, n_cols, nnz, row_ptr, rows, col, val, thr_row, sc, x, y, alpha, 1.0, err, st);
         if (e != cudaSuccess) return cuda_fail(e, "load-balanced SpMV launch");
         return GKO_OK;
     }
     if (nnz == 0) return scale_vector(n_rows, y, beta, st);
     const bool a = alpha != 1.0, b = beta != 0.0;
 #define GKO_SEG(KA, KB)                                                                                          \
-    e = coo ? seg_launch<kSegPCoo, double, double, KA, KB, true, false>(n_rows, nnz, row_ptr, rows, col, val,       \
-                                                                     thr_row, sc, x, y, alpha, beta, err, st)    \
-            : seg_launch<kSegP, double, double, KA, KB, false, false>(n_rows, nnz, row_ptr, rows, col, val,      \
-                                                                      thr_row, sc, x, y, alpha, beta, err, st)
+    e = coo ? seg_launch<kSegPCoo, double, double, KA, KB, true, false, false, kSegThreadsCoo>(                     \
+                  n_rows, n_cols, nnz, row_ptr, rows, col, val, thr_row, sc, x, y, alpha, beta, err, st)         \
+            : seg_launch<kSegP, double, double, KA, KB, false, false>(n_rows, n_cols, nnz, row_ptr, rows, col,   \
+                                                                      val, thr_row, sc, x, y, alpha, beta, err, st)
     if (a && b)
         GKO_SEG(true, true);
     else if (a)
@@ -495,7 +495,7 @@ int spmv_csr(const gko_matrix* A, int config, const double* x, double* y, double
             }
             break;
         case GKO_CFG_CSR_NNZSPLIT:
-            return launch_seg(A->n_rows, A->nnz, A->csr.row_ptr, nullptr, A->csr.col, A->csr.val, A->csr.thr_row,
+            return launch_seg(A->n_rows, A->n_cols, A->nnz, A->csr.row_ptr, nullptr, A->csr.col, A->csr.val, A->csr.thr_row,
                               A->csr.seg, x, y, alpha, beta, A->d_err, false, st, false);
         default: return fail(GKO_ERR_INVALID_ARG, "configuration does not apply to CSR");
     }
@@ -507,7 +507,7 @@ int spmv_coo(const gko_matrix* A, const CooPart& coo, const double* x, double* y
              cudaStream_t st)
 {
     if (A->n_rows == 0) return GKO_OK;
-    return launch_seg(A->n_rows, coo.nnz, nullptr, coo.row, coo.col, coo.val, nullptr, coo.seg, x, y, alpha, beta,
+    return launch_seg(A->n_rows, A->n_cols, coo.nnz, nullptr, coo.row, coo.col, coo.val, nullptr, coo.seg, x, y, alpha, beta,
                       A->d_err, true, st, false);
 }
 

@@ -91,7 +91,7 @@ template <typename V, typename T, bool kAlpha, bool kBeta, bool kX, int CH, bool
 __global__ void __launch_bounds__(kRbThreads, 2)
     csr_rowblock_kernel(int64_t n_rows, int64_t n_cols, int R, int band, int xbuf, const int32_t* __restrict__ row_ptr,
                         const int32_t* __restrict__ col, const V* __restrict__ val, const T* __restrict__ x,
-                        T* __restrict__ y, T alpha, T beta, uint32_t* err, Cg1Reduce red)
+                        T* __restrict__ y, T alpha, T beta, uint32_t* err, Cg1Reduce red, uint32_t polls)
 {
     using G = RbStage<V>;
     constexpr int kXAl = 16 / static_cast<int>(sizeof(T));
@@ -161,9 +161,15 @@ __global__ void __launch_bounds__(kRbThreads, 2)
         if (b >= n_blocks) break;
         const int st = it & 1;
         const uint32_t parity = (it >> 1) & 1;
-        bool landed = mbar_wait_bounded(&bar[st], parity, err);
-        if (!landed) landed = mbar_wait_bounded(&bar[st], parity, err);
+        const bool landed = mbar_wait_bounded(&bar[st], parity, err, polls);
         if (!__syncthreads_and(landed)) {  // CTA-uniform: give up on the rest
+            // wait (default limit) for the copies still in flight into this
+            // stage and the next one, so none lands after the CTA has exited
+            if (tid == 0) {
+                mbar_wait_bounded(&bar[st], parity, err);
+                if (b + stride < n_blocks) mbar_wait_bounded(&bar[st ^ 1], ((it + 1) >> 1) & 1, err);
+            }
+            __syncthreads();
             failed = true;
             break;
         }
@@ -252,13 +258,15 @@ static cudaError_t launch_rowblock_ch(const gko_matrix* A, const V* val, const T
     cudaError_t e = cudaSuccess;
 #define GKO_RB(KA, KB)                                                                                    \
     do {                                                                                                  \
-        e = cudaFuncSetAttribute(csr_rowblock_kernel<V, T, KA, KB, kX, CH, kDots, kHint>,                 \
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));    \
+        e = smem_limit_once(                                                                              \
+            reinterpret_cast<const void*>(csr_rowblock_kernel<V, T, KA, KB, kX, CH, kDots, kHint>),       \
+            static_cast<int>(smem));                                                                      \
         if (e != cudaSuccess) return e;                                                                   \
         csr_rowblock_kernel<V, T, KA, KB, kX, CH, kDots, kHint>                                           \
             <<<static_cast<unsigned>(grid), kRbThreads, smem, st>>>(A->n_rows, A->n_cols, R, band, xbuf,  \
                                                                     A->csr.row_ptr, A->csr.col, val, x, y, \
-                                                                    alpha, beta, A->d_err, red);          \
+                                                                    alpha, beta, A->d_err, red,           \
+                                                                    first_wait_polls());                  \
     } while (0)
     if (kDots)
         GKO_RB(false, false);

@@ -20,7 +20,7 @@ The sweep checks that every candidate agrees with the others; the
 agreement with the CPU oracle is checked by the GPU tests.
 
 Command line (writes the weights and a JSON report):
-    python -m paper_2011_08879_gb300.selector --train 1000:2000 --test 3000:3200 --out weights.json
+    python -m paper_2011_08879_gb300.selector --train 1000:3000 --test 3000:3200 --out weights.json
 """
 from __future__ import annotations
 
@@ -148,11 +148,11 @@ def _gen(seed):
     return seed, synthetic.sweep_matrix(seed)
 
 
-def sweep(seeds, workers=0, log=None):
+def sweep(seeds, workers=0, log=None, on_handle=None):
     """Features (N x 12), times (N x C), nnz (N), structures for the seeds.
-    Matrices are generated in a spawn-started process pool (started before
-    this process touches CUDA when called first) while the GPU times the
-    previous ones."""
+    Matrices are generated in a spawn-started process pool while the GPU
+    times the previous ones.  on_handle(M), if given, is called with each
+    fresh handle before its features are computed."""
     feats, times, nnzs, structs, worst = [], [], [], [], 0.0
     if workers > 0:
         import multiprocessing as mp
@@ -166,6 +166,8 @@ def sweep(seeds, workers=0, log=None):
     try:
         for k, (seed, A) in enumerate(it):
             M = prepare(A)
+            if on_handle is not None:
+                on_handle(M)
             f = M.features()
             t, w = measure(M)
             worst = max(worst, w)
@@ -337,7 +339,7 @@ def _range(s):
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("--train", default="1000:2000")
+    ap.add_argument("--train", default="1000:3000")
     ap.add_argument("--test", default="3000:3200")
     ap.add_argument("--workers", type=int, default=max(1, min(12, (os.cpu_count() or 2) - 2)))
     ap.add_argument("--epochs", type=int, default=600)

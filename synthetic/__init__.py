@@ -405,12 +405,14 @@ def batched_spd(count: int = 4096, seed: int = 7, n_min: int = 32, n_max: int = 
 SWEEP_STRUCTURES = ("stencil", "banded", "powerlaw", "random")
 
 
-def sweep_params(seed: int, n_min: float = 1e4, n_max: float = 2e6, m_min: float = 4.0, m_max: float = 200.0,
-                 nnz_cap: float = 1.5e7) -> dict:
+def sweep_params(seed: int, n_min: float = 1e4, n_max: float = 4e6, m_min: float = 4.0, m_max: float = 200.0,
+                 nnz_cap: float = 3e7) -> dict:
     """Shape of one selector-sweep matrix: structure equiprobable over
     SWEEP_STRUCTURES, rows log-uniform in [n_min, n_max], mean entries per
     row log-uniform in [m_min, m_max]; rows are reduced so that rows * mean
-    stays below nnz_cap."""
+    stays below nnz_cap (3e7 entries, 480 MB as COO: the full product of the
+    ranges would reach 8e8 entries, beyond what the host generates in the
+    time of one sweep)."""
     u = uniform01(seed, S_STRUCT, np.arange(4, dtype=np.uint64))
     structure = SWEEP_STRUCTURES[min(3, int(u[0] * 4))]
     n = 10 ** (math.log10(n_min) + u[1] * (math.log10(n_max) - math.log10(n_min)))
@@ -461,6 +463,15 @@ def workload(name: str) -> dict:
         return powerlaw(2_000_000, 20.0, 1.5, 20000, seed=4)
     if name == "blockdiag_1M":
         return block_diagonal(1_000_000, 8, seed=5)
+    # quarter-size matrices of the same four kinds (profiling captures)
+    if name == "stencil27_80":
+        return stencil27(80, seed=2)
+    if name == "banded_1M":
+        return banded(1_000_000, 64, 16, seed=3)
+    if name == "powerlaw_500k":
+        return powerlaw(500_000, 20.0, 1.5, 20000, seed=4)
+    if name == "blockdiag_250k":
+        return block_diagonal(250_000, 8, seed=5)
     if name == "diffusion7_160":
         return diffusion7(160, 1.0, seed=6)
     if name == "batched_4096":
@@ -469,3 +480,4 @@ def workload(name: str) -> dict:
 
 
 SPMV_SWEEP = ("stencil27_128", "banded_4M", "powerlaw_2M", "blockdiag_1M")
+SPMV_SWEEP_SMALL = ("stencil27_80", "banded_1M", "powerlaw_500k", "blockdiag_250k")

@@ -147,34 +147,66 @@ def test_sweep_candidates_match_oracle(gko, dev, orc):
     assert len(seen) == 4
 
 
-def test_selector_learns_on_a_small_sweep(gko, dev):
-    """Train on 48 small sweep matrices with the library's kernels and
-    check that the network beats a fixed choice on the training set and
-    that its held-out regret is reported sanely; the full-size training is
-    the module's command line."""
+def test_selector_gains_over_default_csr_on_held_out_matrices(gko, dev):
+    """Train on 96 small sweep matrices with the library's kernels (features,
+    forward, backward and Adam on the GPU), then score the network on 48
+    held-out matrices that the training never saw: its mean time regret
+    against the exhaustive best is below that of the library's default CSR
+    kernel (the method without the selector) and below that of the best
+    single candidate of the training set.  The full-size training is the
+    module's command line."""
     from paper_2011_08879_gb300 import selector as sel
     import synthetic
-    tr = [synthetic.sweep_matrix(s, n_max=3e5, nnz_cap=3e6) for s in range(1000, 1048)]
-    te = [synthetic.sweep_matrix(s, n_max=3e5, nnz_cap=3e6) for s in range(3000, 3012)]
+    tr = [synthetic.sweep_matrix(s, n_max=3e5, nnz_cap=3e6) for s in range(1000, 1096)]
+    te = [synthetic.sweep_matrix(s, n_max=3e5, nnz_cap=3e6) for s in range(3000, 3048)]
 
     def run(mats):
-        F, T, N = [], [], []
+        F, T = [], []
         for A in mats:
             M = sel.prepare(A)
             F.append(M.features())
             t, w = sel.measure(M, reps=3, warmup=1)
             assert w < 1e-9
             T.append(t)
-            N.append(len(A["val"]))
             M.close()
-        return np.array(F), np.array(T), np.array(N)
+        return np.array(F), np.array(T)
 
-    Ftr, Ttr, Ntr = run(tr)
-    Fte, Tte, Nte = run(te)
-    Y, Mk = zip(*[sel.targets(t, n) for t, n in zip(Ttr, Ntr)])
-    params, mean, scale = sel.train(Ftr, np.array(Y), np.array(Mk), epochs=300)
-    rep_tr = sel.evaluate(params, mean, scale, Ftr, Ttr)
-    fixed = [np.mean(sel.regret(Ttr, np.full(len(Ttr), c))) for c in range(len(sel.CANDIDATES))]
-    assert rep_tr["mean"] < min(fixed), (rep_tr, fixed)
+    Ftr, Ttr = run(tr)
+    Fte, Tte = run(te)
+    Y, Mk = zip(*[sel.targets(t) for t in Ttr])
+    params, mean, scale = sel.train(Ftr, np.array(Y), np.array(Mk), epochs=400)
     rep_te = sel.evaluate(params, mean, scale, Fte, Tte)
-    assert 0.0 <= rep_te["mean"] < 10.0
+    fixed = int(np.argmin([np.mean(sel.regret(Ttr, np.full(len(Ttr), c))) for c in range(len(sel.CANDIDATES))]))
+    fixed_te = float(np.mean(sel.regret(Tte, np.full(len(Tte), fixed))))
+    print("held-out regret: selector %.3f, default CSR %.3f, best fixed (%s) %.3f"
+          % (rep_te["mean"], rep_te["csr_default_mean"], sel.CLASS_NAMES[fixed], fixed_te))
+    assert rep_te["mean"] < rep_te["csr_default_mean"], rep_te
+    assert rep_te["mean"] < fixed_te, (rep_te, fixed_te)
+
+
+def test_auto_without_selector_autotunes_and_matches_oracle(gko, dev, orc):
+    """With no selector installed, GKO_FMT_AUTO falls back to the exhaustive
+    autotuner: it times every candidate the handle can run once, caches the
+    fastest in the handle, and its product matches the oracle."""
+    import torch
+    from paper_2011_08879_gb300 import selector as sel
+    gko.binding.gko_selector_clear()
+    A = syn.powerlaw(200000, 12.0, 1.5, 5000, seed=77)
+    M = sel.prepare(A)  # every format that the padding limit admits
+    f, c, times = M.autotune()
+    live = [i for i, t in enumerate(times) if t == t]
+    assert len(live) >= 6
+    best = sel.CANDIDATES[int(np.nanargmin(times))]
+    assert (f, c) == (gko.binding.FORMATS[best[0]], best[1])
+    # candidates whose format is not materialised are reported as NaN
+    for i, (fmt, cfg) in enumerate(sel.CANDIDATES):
+        if not M.has(fmt):
+            assert times[i] != times[i]
+    x = syn.vector(A["n_cols"], 3)
+    y0 = syn.vector(A["n_rows"], 4)
+    xd = torch.from_numpy(x).to(dev)
+    yd = torch.from_numpy(y0).to(dev)
+    M.spmv(xd, yd, 0.5, 2.0, fmt="auto")
+    torch.cuda.synchronize()
+    ref, mag = orc.spmv_dot2(A, x, 0.5, 2.0, y0)
+    assert np.all(np.abs(yd.cpu().numpy() - ref) <= 1e-12 * mag + 1e-300)

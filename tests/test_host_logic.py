@@ -122,9 +122,9 @@ def test_dominant_kernel_roofline():
 
 def test_launch_count_model():
     """One launch per SpMV, plus the fix-up of the equal-nnz kernel once the
-    entries span more than one tile of 256 x 11."""
+    entries span more than one tile of 64 x 11."""
     import bench
-    assert bench.kernel_launches("coo", 2816) == 1 and bench.kernel_launches("coo", 2817) == 2
+    assert bench.kernel_launches("coo", 704) == 1 and bench.kernel_launches("coo", 705) == 2
     assert bench.kernel_launches("hybrid", 0) == 1 and bench.kernel_launches("hybrid", 10 ** 6) == 3
     assert bench.kernel_launches("csr", 10 ** 6) == 1 and bench.kernel_launches("ell", 10 ** 6) == 1
 

@@ -3,9 +3,11 @@
 It serves callers that cannot allocate device memory while they run (graph
 capture with a fixed footprint, real-time loops, memory owned by another
 allocator); its scratch is a fixed array inside the library.  These tests
-call it through the C ABI and compare its output with the handle-based COO
-SpMV (gko_spmv) on two calls in a row, within the tolerance every SpMV test
-uses: |y - y_ref| <= 1e-12 * (|alpha| |A| |x| + |beta| |y|) per entry.
+call it through the C ABI on two calls in a row and compare its output
+element by element with the oracle's compensated (Dot2) product, within the
+tolerance every SpMV test uses: |y - y_ref| <= 1e-12 * (|alpha| |A| |x| +
+|beta| |y|) per entry; the handle-based COO SpMV (gko_spmv) is held to the
+same reference on the same inputs.
 The file is collected last so that a run stopping at the first failure has
 already run every other test."""
 import numpy as np
@@ -51,9 +53,11 @@ def test_no_alloc_matches_handle_spmv_twice(gko, dev, orc, alpha, beta):
         gko.gko_spmv_coo_noalloc(n, m, nnz, row.data_ptr(), col.data_ptr(), val.data_ptr(), x.data_ptr(),
                                  y.data_ptr(), alpha, beta, err.data_ptr(), torch.cuda.current_stream().cuda_stream)
         torch.cuda.synchronize()
-        _, mag = orc.spmv_dot2(A, x_h, alpha, beta, y0_h)
-        d = np.abs(y.cpu().numpy() - y_ref.cpu().numpy())
+        ref, mag = orc.spmv_dot2(A, x_h, alpha, beta, y0_h)
+        d = np.abs(y.cpu().numpy() - ref)
         assert np.all(d <= 1e-12 * mag + 1e-300), (call, float(d.max()))
+        d_handle = np.abs(y_ref.cpu().numpy() - ref)
+        assert np.all(d_handle <= 1e-12 * mag + 1e-300), (call, float(d_handle.max()))
         assert int(err.item()) == 0
 
 
@@ -75,3 +79,56 @@ def test_no_alloc_limits_and_arguments(gko, dev):
     gko.gko_spmv_coo_noalloc(5, 5, 0, 0, 0, 0, 0, y.data_ptr(), 1.0, 0.5)
     torch.cuda.synchronize()
     assert torch.all(y == 1.0)
+
+
+def test_no_alloc_at_the_entry_limit(gko, dev):
+    """nnz exactly GKO_NOALLOC_MAX_TILES * 2816 is accepted and runs in the
+    fixed array (its last tile, index 32767, carries a row into the fix-up).
+    Rows of 3001 entries cross tile boundaries; values 1 and x_c = (c mod 7)
+    - 3 make every row sum an exact integer: y_r = sum_{c < len_r} x_c."""
+    import torch
+    nnz = 32768 * 2816
+    L, m = 3001, 4096
+    n = (nnz + L - 1) // L
+    k = torch.arange(nnz, device=dev, dtype=torch.int64)
+    row = (k // L).to(torch.int32)
+    col = (k % L).to(torch.int32)
+    del k
+    val = torch.ones(nnz, dtype=torch.float64, device=dev)
+    xc = (np.arange(m) % 7 - 3).astype(np.float64)
+    x = torch.from_numpy(xc).to(dev)
+    y = torch.full((n,), float("nan"), dtype=torch.float64, device=dev)
+    err = torch.zeros(1, dtype=torch.int32, device=dev)
+    gko.gko_spmv_coo_noalloc(n, m, nnz, row.data_ptr(), col.data_ptr(), val.data_ptr(), x.data_ptr(), y.data_ptr(),
+                             1.0, 0.0, err.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    assert int(err.item()) == 0
+    exp = np.full(n, xc[:L].sum())
+    exp[-1] = xc[:nnz - (n - 1) * L].sum()
+    assert np.array_equal(y.cpu().numpy(), exp)
+    b = gko.binding
+    assert b.lib.gko_spmv_coo_noalloc(n, m, nnz + 1, row.data_ptr(), col.data_ptr(), val.data_ptr(), x.data_ptr(),
+                                      y.data_ptr(), 1.0, 0.0, None, None) == b.ERR_INVALID_ARG
+
+
+def test_no_alloc_on_a_second_device(gko, dev, orc):
+    """The array's address is looked up per device: a call on device 1 after
+    calls on device 0 matches the oracle too."""
+    import torch
+    if torch.cuda.device_count() < 2:
+        pytest.skip("one device")
+    A = syn.powerlaw(20000, 12.0, 1.5, 900, seed=93)
+    n, m = A["n_rows"], A["n_cols"]
+    rows = np.repeat(np.arange(n, dtype=np.int32), np.diff(A["row_ptr"]))
+    x_h = syn.vector(m, 2)
+    ref, mag = orc.spmv_dot2(A, x_h)
+    for d in (0, 1):
+        with torch.cuda.device(d):
+            dv = torch.device("cuda", d)
+            r, c, v = (torch.from_numpy(np.ascontiguousarray(a)).to(dv) for a in (rows, A["col_idx"], A["val"]))
+            x = torch.from_numpy(x_h).to(dv)
+            y = torch.empty(n, dtype=torch.float64, device=dv)
+            gko.gko_spmv_coo_noalloc(n, m, len(A["val"]), r.data_ptr(), c.data_ptr(), v.data_ptr(), x.data_ptr(),
+                                     y.data_ptr(), 1.0, 0.0, None, torch.cuda.current_stream(dv).cuda_stream)
+            torch.cuda.synchronize(dv)
+            assert np.all(np.abs(y.cpu().numpy() - ref) <= 1e-12 * mag + 1e-300)
