@@ -104,10 +104,10 @@ def kernel_family(fmt, matrix, coo_part):
 
 
 FAMILY_LABEL = {
-    "coo": "seg_spmv_kernel<11> (COO, equal-nnz tiles) + fix-up",
+    "coo": "seg_spmv_kernel<11|13> (COO, equal-nnz tiles of 64 threads) + fix-up",
     "ell": "ell_kernel",
     "sellp": "sellp_kernel",
-    "hybrid": "ell_kernel + seg_spmv_kernel<11> (COO part, accumulate) + fix-up",
+    "hybrid": "ell_kernel + seg_spmv_kernel<11|13> (COO part, accumulate) + fix-up",
 }
 
 
@@ -170,20 +170,31 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def profile_traffic():
-    """DRAM bytes per launch from the committed ncu summary, if present and
-    taken on the current kernel sources: lines 'source <hash>' and
-    'traffic <matrix>/<format> <bytes>'."""
-    out, src = {}, None
+def profile_traffic(cases):
+    """DRAM bytes per launch of each (matrix, format) case, from the committed
+    ncu summary if it was taken on the current kernel sources.  The capture
+    runs the quarter-size sweep (same matrix kinds, `--sweep small`) and the
+    file records, per kind and format, DRAM bytes over algorithmic bytes
+    ('ratio <kind>/<format> <r>'); a streaming kernel's traffic grows in
+    proportion to the entries it moves, so the full-size traffic is that
+    ratio times the full case's algorithmic bytes."""
+    ratios, src = {}, None
     path = os.path.join(ROOT, "profiles", "spmv_dram_traffic.txt")
     if os.path.exists(path):
         for line in open(path):
             parts = line.split()
             if len(parts) == 2 and parts[0] == "source":
                 src = parts[1]
-            if len(parts) == 3 and parts[0] == "traffic":
-                out[parts[1]] = float(parts[2])
-    return out if src == kernel_source_hash() else {}
+            if len(parts) == 3 and parts[0] == "ratio":
+                ratios[parts[1]] = float(parts[2])
+    if src != kernel_source_hash():
+        return {}
+    out = {}
+    for c in cases:
+        key = "%s/%s" % (c["matrix"].split("_")[0], c["fmt"])
+        if key in ratios:
+            out["%s/%s" % (c["matrix"], c["fmt"])] = ratios[key] * c["bytes"]
+    return out
 
 
 # ----------------------------------------------------------------- clocks
@@ -408,7 +419,7 @@ def run_gpu(args):
         detail["%s/%s" % (c["matrix"], c["fmt"])] = {
             "GBs": round(c["bytes"] / med / 1e9, 1), "pct_hbm": round(100 * c["bytes"] / med / 1e9 / peak, 1),
             "GFLOPs": round(c["flops"] / med / 1e9, 1), "us": round(med * 1e6, 1)}
-    roofline = dominant_roofline(cases, per_case, profile_traffic(), peak, peak_kind)
+    roofline = dominant_roofline(cases, per_case, profile_traffic(cases), peak, peak_kind)
 
     # end to end through gko_spmv_host with pinned host buffers
     e2e = None

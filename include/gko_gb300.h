@@ -347,16 +347,18 @@ int gko_bicgstab(const gko_matrix* A, int fmt, const double* b, double* x, doubl
 /* Restarted GMRES(restart) (Saad and Schultz, SIAM J. Sci. Stat. Comput.
  * 7, 1986) on A x = b for a general square A, the minimal-residual Krylov
  * solver of Sec. 6.2's family: each cycle builds an Arnoldi basis from the
- * true residual (orthogonalised by classical Gram-Schmidt applied twice),
- * reduces the Hessenberg matrix by Givens rotations and ends after restart
- * steps (1..127) or when the least-squares residual estimate is
- * <= tol ||b||; x += V y; the next cycle's FP64 true residual decides
- * convergence.  Products with format fmt; the basis ((restart + 1) n
- * doubles) is allocated stream-ordered for the call.  maxit bounds the
- * Arnoldi steps (info->iterations counts them): GKO_ERR_NOT_CONVERGED; a
- * NaN or a zero rotation before convergence: GKO_ERR_BREAKDOWN.  The host
- * applies the rotations (one synchronisation per step).  ||b|| = 0
- * returns x = 0.  Synchronises the stream. */
+ * true residual, orthogonalised by classical Gram-Schmidt applied twice,
+ * reduces the
+ * Hessenberg matrix by Givens rotations and ends after restart steps
+ * (1..127) or when the least-squares residual estimate is <= tol ||b||;
+ * x += V y; the next cycle's FP64 true residual decides convergence.  The
+ * Arnoldi steps, rotations and back substitution run on the device (one
+ * CUDA graph per cycle, one host synchronisation per cycle).  Products with
+ * format fmt; the basis ((restart + 1) n doubles) is allocated
+ * stream-ordered for the call.  maxit bounds the Arnoldi steps
+ * (info->iterations counts them): GKO_ERR_NOT_CONVERGED; a NaN or a zero
+ * rotation before convergence: GKO_ERR_BREAKDOWN.  ||b|| = 0 returns x = 0.
+ * Synchronises the stream. */
 int gko_gmres(const gko_matrix* A, int fmt, const double* b, double* x, double tol, int restart, int maxit,
               void* stream, gko_solve_info* info);
 

@@ -29,7 +29,7 @@ namespace gko {
 
 int launch_seg(int64_t n_rows, int64_t n_cols, int64_t nnz, const int32_t* row_ptr, const int32_t* rows, const int32_t* col,
                const double* val, const int32_t* thr_row, const SegArrays& sa, const double* x, double* y,
-               double alpha, double beta, uint32_t* err, bool coo, cudaStream_t st, bool accumulate);
+               double alpha, double beta, uint32_t* err, bool coo, cudaStream_t st, bool accumulate, int coo_p);
 
 enum { kDotStore = 0, kDotRhoInit = 1, kDotPQ = 2 };
 
@@ -1096,8 +1096,8 @@ struct GmState {
     uint32_t ticket;
 };
 
-// part[blk * ldp + c] = the block's share of V_c . w for every c < ncols
-// (ncols = j + 1 read from the state), in chunks of kGmChunk columns.
+// part[blk * ldp + c] = the block's share of V_c . w for every c < ncols,
+// in chunks of kGmChunk columns.
 __device__ __forceinline__ void gm_partial_dots(int64_t n, const double* __restrict__ V, int ncols,
                                                 const double* __restrict__ w, double* __restrict__ part, int ldp)
 {
@@ -1139,22 +1139,28 @@ __global__ void __launch_bounds__(kRedThreads)
     gm_partial_dots(n, V, s->j + 1, w, part, ldp);
 }
 
-// coef[c] = sum over blocks (in block order) of part[b * ldp + c] for
-// c <= j; hh[c] = coef[c] on the first pass, hh[c] += coef[c] on the second.
-__global__ void gm_coef_kernel(int nblocks, const double* __restrict__ part, int ldp, double* __restrict__ coef,
-                               double* __restrict__ hh, int second, const GmState* s)
+// coef[c] = sum over blocks of part[b * ldp + c] (block c of the grid sums
+// column c in a fixed tree order) for c <= j; hh[c] = coef[c] on the first
+// pass, hh[c] += coef[c] on the second.
+__global__ void __launch_bounds__(kRedThreads)
+    gm_coef_kernel(int nblocks, const double* __restrict__ part, int ldp, double* __restrict__ coef,
+                   double* __restrict__ hh, int second, const GmState* s)
 {
-    const int ncols = s->j + 1;
-    for (int c = threadIdx.x; c < ncols; c += blockDim.x) {
-        double t = 0.0;
-        for (int b = 0; b < nblocks; ++b) t += part[b * static_cast<int64_t>(ldp) + c];
+    __shared__ double sh[32];
+    const int c = blockIdx.x;
+    if (c > s->j) return;  // block-uniform
+    double t = 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += kRedThreads) t += part[b * static_cast<int64_t>(ldp) + c];
+    t = block_sum(t, sh);
+    if (threadIdx.x == 0) {
         coef[c] = t;
         hh[c] = second ? hh[c] + t : t;
     }
 }
 
 // w -= sum_{c <= j} coef[c] V_c, then the partial dots of V_0..V_j with the
-// updated w (the second Gram-Schmidt pass reads V once for both).
+// updated w (the second Gram-Schmidt pass; its dots re-read the V entries
+// this thread has just read, mostly from L2).
 __global__ void __launch_bounds__(kRedThreads)
     gm_combine_dots_kernel(int64_t n, const double* __restrict__ V, double* __restrict__ w,
                            const double* __restrict__ coef, double* __restrict__ part, int ldp, const GmState* s)
@@ -1214,58 +1220,82 @@ __global__ void gm_next_vector_kernel(int64_t n, double* __restrict__ V, double*
 // rotations applied to it, a new rotation zeroing its subdiagonal, the
 // least-squares right-hand side g rotated, the cycle's stop decided (residual
 // estimate |g[j+1]| <= tol ||b||, m columns, maxit steps in all, a zero hn,
-// or a breakdown: NaN or a zero rotation).  One thread.
-__global__ void gm_givens_kernel(double* __restrict__ H, double* __restrict__ cs, double* __restrict__ sn,
-                                 double* __restrict__ g, const double* __restrict__ hh, GmState* s,
-                                 cudaGraphConditionalHandle h)
+// or a breakdown: NaN or a zero rotation).  The block stages the column and
+// the rotations in shared memory; thread 0 applies them.
+__global__ void __launch_bounds__(128)
+    gm_givens_kernel(double* __restrict__ H, double* __restrict__ cs, double* __restrict__ sn,
+                     double* __restrict__ g, const double* __restrict__ hh, GmState* s, cudaGraphConditionalHandle h)
 {
+    __shared__ double col[129], c_s[128], s_s[128];
     const int j = s->j, m = s->m;
-    const double hn = s->hn;
-    s->total += 1;
-    if (!(hn == hn)) {
-        s->broke = 1;
-        s->stop = 1;
-        cudaGraphSetConditional(h, 0);
-        return;
+    for (int i = threadIdx.x; i <= j; i += blockDim.x) {
+        col[i] = hh[i];
+        c_s[i] = cs[i];
+        s_s[i] = sn[i];
     }
-    for (int i = 0; i <= j; ++i) H[i * m + j] = hh[i];
-    H[(j + 1) * m + j] = hn;
-    for (int i = 0; i < j; ++i) {  // earlier rotations on the new column
-        const double a = H[i * m + j], c = H[(i + 1) * m + j];
-        H[i * m + j] = cs[i] * a + sn[i] * c;
-        H[(i + 1) * m + j] = -sn[i] * a + cs[i] * c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const double hn = s->hn;
+        s->total += 1;
+        bool stop = false;
+        if (!(hn == hn)) {
+            s->broke = 1;
+            stop = true;
+        } else {
+            col[j + 1] = hn;
+            for (int i = 0; i < j; ++i) {  // earlier rotations on the new column
+                const double a = col[i], c = col[i + 1];
+                col[i] = c_s[i] * a + s_s[i] * c;
+                col[i + 1] = -s_s[i] * a + c_s[i] * c;
+            }
+            const double a = col[j], c = col[j + 1];
+            const double d = sqrt(a * a + c * c);
+            if (!(d > 0.0)) {
+                s->broke = 1;
+                stop = true;
+            } else {
+                cs[j] = a / d;
+                sn[j] = c / d;
+                col[j] = d;
+                col[j + 1] = 0.0;
+                const double gj = g[j];
+                g[j + 1] = -(c / d) * gj;
+                g[j] = (a / d) * gj;
+                s->j = j + 1;
+                stop = fabs(g[j + 1]) <= s->tol * s->bnorm || !(hn > 0.0) || j + 1 >= m || s->total >= s->maxit;
+            }
+        }
+        if (stop) {
+            s->stop = 1;
+            cudaGraphSetConditional(h, 0);
+        }
     }
-    const double a = H[j * m + j], c = H[(j + 1) * m + j];
-    const double d = sqrt(a * a + c * c);
-    if (!(d > 0.0)) {
-        s->broke = 1;
-        s->stop = 1;
-        cudaGraphSetConditional(h, 0);
-        return;
-    }
-    cs[j] = a / d;
-    sn[j] = c / d;
-    H[j * m + j] = d;
-    H[(j + 1) * m + j] = 0.0;
-    g[j + 1] = -sn[j] * g[j];
-    g[j] = cs[j] * g[j];
-    s->j = j + 1;
-    if (fabs(g[j + 1]) <= s->tol * s->bnorm || !(hn > 0.0) || j + 1 >= m || s->total >= s->maxit) {
-        s->stop = 1;
-        cudaGraphSetConditional(h, 0);
-    }
+    __syncthreads();
+    if (!s->broke)
+        for (int i = threadIdx.x; i <= j + 1; i += blockDim.x) H[i * m + j] = col[i];
 }
 
-// y = H(0:j, 0:j)^-1 g(0:j) by back substitution (one thread).
-__global__ void gm_backsub_kernel(const double* __restrict__ H, const double* __restrict__ g, double* __restrict__ y,
-                                  const GmState* s)
+// y = H(0:j, 0:j)^-1 g(0:j) by back substitution (H and g staged in shared
+// memory by the block, solved by thread 0).
+__global__ void __launch_bounds__(128)
+    gm_backsub_kernel(const double* __restrict__ H, const double* __restrict__ g, double* __restrict__ y,
+                      const GmState* s)
 {
+    extern __shared__ double hs[];
     const int j = s->j, m = s->m;
-    for (int i = j - 1; i >= 0; --i) {
-        double acc = g[i];
-        for (int k = i + 1; k < j; ++k) acc -= H[i * m + k] * y[k];
-        y[i] = acc / H[i * m + i];
+    double* gs = hs + static_cast<size_t>(j) * j;
+    for (int t = threadIdx.x; t < j * j; t += blockDim.x) hs[t] = H[(t / j) * m + t % j];
+    for (int t = threadIdx.x; t < j; t += blockDim.x) gs[t] = g[t];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int i = j - 1; i >= 0; --i) {
+            double acc = gs[i];
+            for (int k = i + 1; k < j; ++k) acc -= hs[i * j + k] * gs[k];
+            gs[i] = acc / hs[i * j + i];
+        }
     }
+    __syncthreads();
+    for (int t = threadIdx.x; t < j; t += blockDim.x) y[t] = gs[t];
 }
 
 // x += sum_{c < j} y[c] V_c
@@ -1296,10 +1326,10 @@ __global__ void gm_scale_kernel(int64_t n, double* __restrict__ out, const doubl
 // Restarted GMRES(m) (Saad and Schultz 1986) for general square A.  The
 // Arnoldi basis V (m + 1 vectors of n) lives in device memory.  One cycle is
 // a CUDA graph whose WHILE node runs the Arnoldi steps: the product
-// w = A v_j, classical Gram-Schmidt applied twice (partial dots of the basis
-// with w, their fixed-order sum, the combination fused with the second
-// pass's dots, the second combination fused with ||w||), the next basis
-// vector, and the Givens step on the new Hessenberg column, all on the
+// w = A v_j, classical Gram-Schmidt applied twice (partial dots of the
+// basis with w, their fixed-order sums, the combination fused with the
+// second pass's dots, the second combination fused with ||w||), the next
+// basis vector, and the Givens step on the new Hessenberg column, all on the
 // device; the Givens kernel ends the loop when the residual estimate is
 // <= tol ||b||, at m steps or at maxit.  The host synchronises once per
 // cycle: x += V y (back substitution on the device), and the next cycle
@@ -1358,12 +1388,13 @@ int gmres_solve(const gko_matrix* A, int fmt, const double* b, double* x, double
     GKO_TRY(build_while_graph(&gh, [&](cudaGraphConditionalHandle h, cudaStream_t cs_) -> int {
         GKO_TRY(spmv_fmt(A, fmt, vcur, w, 1.0, 0.0, cs_));
         gm_dots_kernel<<<grid, kRedThreads, 0, cs_>>>(n, V, w, part, ldp, gs);
-        gm_coef_kernel<<<1, 128, 0, cs_>>>(grid, part, ldp, coef, hh, 0, gs);
+        gm_coef_kernel<<<m + 1, kRedThreads, 0, cs_>>>(grid, part, ldp, coef, hh, 0, gs);
         gm_combine_dots_kernel<<<grid, kRedThreads, 0, cs_>>>(n, V, w, coef, part, ldp, gs);
-        gm_coef_kernel<<<1, 128, 0, cs_>>>(grid, part, ldp, coef, hh, 1, gs);
-        gm_combine_norm_kernel<<<grid, kRedThreads, 0, cs_>>>(n, V, w, coef, part + static_cast<int64_t>(kRedBlocks) * ldp, gs);
+        gm_coef_kernel<<<m + 1, kRedThreads, 0, cs_>>>(grid, part, ldp, coef, hh, 1, gs);
+        gm_combine_norm_kernel<<<grid, kRedThreads, 0, cs_>>>(n, V, w, coef,
+                                                              part + static_cast<int64_t>(kRedBlocks) * ldp, gs);
         gm_next_vector_kernel<<<grid, kRedThreads, 0, cs_>>>(n, V, vcur, w, gs);
-        gm_givens_kernel<<<1, 1, 0, cs_>>>(H, cs, sn, g, hh, gs, h);
+        gm_givens_kernel<<<1, 128, 0, cs_>>>(H, cs, sn, g, hh, gs, h);
         GKO_CUDA(cudaGetLastError());
         return GKO_OK;
     }));
@@ -1406,7 +1437,9 @@ int gmres_solve(const gko_matrix* A, int fmt, const double* b, double* x, double
             break;
         }
         if (hg.j > 0) {
-            gm_backsub_kernel<<<1, 1, 0, st>>>(H, g, yv, gs);
+            const int bs_smem = hg.j * (hg.j + 1) * static_cast<int>(sizeof(double));
+            GKO_CUDA(smem_limit_once(reinterpret_cast<const void*>(gm_backsub_kernel), bs_smem));
+            gm_backsub_kernel<<<1, 128, bs_smem, st>>>(H, g, yv, gs);
             gm_update_x_kernel<<<grid, kRedThreads, 0, st>>>(n, x, V, yv, gs);
             GKO_CUDA(cudaGetLastError());
         }

@@ -158,7 +158,8 @@ int convert_csr_to_coo(gko_matrix* A, cudaStream_t st)
         csr_rows_kernel<<<ceil_div(n_thr, 256), 256, 0, st>>>(A->nnz, A->n_rows, A->csr.row_ptr, A->csr.thr_row,
                                                                c.row);
     c.nnz = A->nnz;
-    GKO_TRY(seg_alloc(&c.seg, c.nnz, kSegPCoo, kSegThreadsCoo));
+    c.P = coo_entries_per_thread(A);
+    GKO_TRY(seg_alloc(&c.seg, c.nnz, c.P, kSegThreadsCoo));
     GKO_CUDA(cudaGetLastError());
     GKO_CUDA(cudaStreamSynchronize(st));
     A->has[GKO_FMT_COO] = true;
@@ -664,7 +665,8 @@ int convert_csr_to_hybrid(gko_matrix* A, cudaStream_t st)
         csr_to_hybrid_coo_kernel<<<ceil_div(n_thr, 256), 256, 0, st>>>(A->nnz, A->n_rows, K, A->csr.row_ptr,
                                                                         A->csr.thr_row, A->csr.col, A->csr.val, off,
                                                                         c.row, c.col, c.val);
-    GKO_TRY(seg_alloc(&c.seg, c.nnz, kSegPCoo, kSegThreadsCoo));
+    c.P = coo_entries_per_thread(A);
+    GKO_TRY(seg_alloc(&c.seg, c.nnz, c.P, kSegThreadsCoo));
     GKO_CUDA(cudaFreeAsync(cnt, st));
     GKO_CUDA(cudaFreeAsync(off, st));
     GKO_CUDA(cudaGetLastError());

@@ -57,7 +57,9 @@ void dev_free(T*& p)
 inline int64_t padded_len(int64_t n) { return (n + 15) / 16 * 16 + 16; }
 
 constexpr int kSegP = 15;     // entries per thread of the load-balanced CSR kernel (and thr_row)
-constexpr int kSegPCoo = 11;  // entries per thread of the load-balanced COO kernel
+constexpr int kSegPCoo = 11;       // entries per thread of the load-balanced COO kernel (scattered columns;
+                                   // also the allocation-free entry's tile)
+constexpr int kSegPCooLocal = 13;  // ... for matrices whose columns stay near the diagonal
 constexpr int kSegThreadsCoo = 64;  // threads per CTA (and per tile) of the load-balanced COO kernel
 
 // ------------------------------------------------------------ the handle
@@ -92,6 +94,7 @@ struct CooPart {
     int32_t* col = nullptr;
     double* val = nullptr;
     int64_t nnz = 0;
+    int P = kSegPCoo;  // entries per thread of its load-balanced kernel (coo_entries_per_thread)
     SegArrays seg;
 };
 
@@ -181,6 +184,11 @@ namespace gko {
 // the given stream; they validate nothing (the C-ABI layer does).
 int csr_analyse(gko_matrix* A, cudaStream_t st);
 int seg_alloc(SegArrays* s, int64_t nnz, int P, int threads);
+// Entries per thread of the COO kernel for this matrix: 13 when its columns
+// stay near the diagonal (max |i - j| <= max(4096, n / 16): the gathers of x
+// hit L1), else 11 (scattered columns: the smaller shared-memory stages
+// leave L1 room for more gathers in flight).  Measured on GB300.
+int coo_entries_per_thread(const gko_matrix* A);
 void seg_free(SegArrays* s);
 int spmv_csr(const gko_matrix* A, int config, const double* x, double* y, double alpha, double beta,
              cudaStream_t st);

@@ -314,12 +314,15 @@ __device__ __forceinline__ SegThreadOut<T> seg_thread(int ls, int le, int t0, in
 // Phase 1 of one tile for one thread, COO.  The thread's entries
 // [ls, ls + rem) are loaded with their rows; a bit mask marks the entries
 // after which a row ends (the row of the next entry differs; rows are
-// sorted), so the row structure costs one compare per entry.  Fast path
-// (at most three row ends, no row without entries in between): one FMA per
-// entry into a single running sum that is stored and reset at each end;
-// the first finished row goes to fin when it began before the thread.
-// kFull: every thread of the tile holds P entries (all tiles but the last),
-// so no per-entry bounds predicates are needed.
+// sorted), so the row structure costs one compare per entry.  Each entry
+// then costs one FMA into a running sum that is reset at each end; the
+// first finished row goes to fin when it began before the thread.  Three
+// paths, chosen per warp: at most three ends (the sums at the ends kept in
+// registers, stored after the loop); any number of ends with no row
+// without entries in between (the sums parked in the thread's own stage
+// slots, stored after the loop); the general path (rows without entries
+// get their zero stores).  kFull: every thread of the tile holds P entries
+// (all tiles but the last), so no per-entry bounds predicates are needed.
 template <int P, typename V, typename T, bool kAlpha, bool kBeta, bool kSkipEmpty, bool kFull>
 __device__ __forceinline__ SegThreadOut<T> seg_thread_coo(int ls, int rem, int t0, int cnt, const V* s_val,
                                                           const int32_t* s_col, const int32_t* s_row,
@@ -365,17 +368,64 @@ __device__ __forceinline__ SegThreadOut<T> seg_thread_coo(int ls, int rem, int t
         for (int r = 0; r < r_first; ++r) seg_store<kAlpha, kBeta>(y, r, T(0), alpha, beta);
     const bool fast = n_end <= 3 && (kSkipEmpty || !gap);
     const bool warp_fast = __all_sync(0xffffffffu, fast);  // every lane of the warp reaches this
+    const bool warp_flat = !warp_fast && __all_sync(0xffffffffu, kSkipEmpty || !gap);
     if (!has) return o;
     if (warp_fast) {
+        // at most three ends: the sums at the ends are captured in registers
+        // and stored after the loop
         const int e0 = __ffs(mask);  // 1 + position of the first end (0: none)
+        const uint32_t m1 = mask & (mask - 1u);
+        const int e1 = __ffs(m1);
+        const int e2 = __ffs(m1 & (m1 - 1u));
+        T acc = T(0), v0 = T(0), v1 = T(0), v2 = T(0);
+#pragma unroll
+        for (int j = 0; j < P; ++j) {
+            if (kFull || j < n_mine) {
+                acc = fma(vv[j], xv[j], acc);
+                v0 = (j + 1 == e0) ? acc : v0;
+                v1 = (j + 1 == e1) ? acc : v1;
+                v2 = (j + 1 == e2) ? acc : v2;
+                acc = ((mask >> j) & 1u) ? T(0) : acc;
+            }
+        }
+        if (n_end > 0) {
+            if (ob) {
+                o.fin_row = r_first;
+                o.fin_val = v0;
+            } else {
+                seg_store<kAlpha, kBeta>(y, r_first, v0, alpha, beta);
+            }
+        }
+        if (n_end > 1) seg_store<kAlpha, kBeta>(y, s_row[ls + e0], v1, alpha, beta);
+        if (n_end > 2) seg_store<kAlpha, kBeta>(y, s_row[ls + e1], v2, alpha, beta);
+        if (!((mask >> (n_mine - 1)) & 1u)) {  // the last entry's row is still open
+            o.open_row = s_row[ls + n_mine - 1];
+            o.open_val = acc;
+        }
+        return o;
+    }
+    if (warp_flat) {
+        // any number of ends (rows without entries are skipped or absent):
+        // the finished rows go to this thread's own slots of the stage (its
+        // values and columns are in registers already) and are written out
+        // after the FMA loop, loads of y first when beta != 0
+        V* sv = const_cast<V*>(s_val) + ls;
+        int32_t* sr = const_cast<int32_t*>(s_col) + ls;
+        const int e0 = __ffs(mask);
         T acc = T(0), f0 = T(0);
+        int k = 0;
 #pragma unroll
         for (int j = 0; j < P; ++j) {
             if (kFull || j < n_mine) {
                 acc = fma(vv[j], xv[j], acc);
                 const bool end = (mask >> j) & 1u;
                 const bool first = j + 1 == e0;
-                if (end && !(first && ob)) seg_store<kAlpha, kBeta>(y, rr[j], acc, alpha, beta);
+                const bool put = end && !(first && ob);
+                if (put) {
+                    sv[k] = static_cast<V>(acc);
+                    sr[k] = rr[j];
+                }
+                k += put ? 1 : 0;
                 f0 = first ? acc : f0;
                 acc = end ? T(0) : acc;
             }
@@ -384,13 +434,24 @@ __device__ __forceinline__ SegThreadOut<T> seg_thread_coo(int ls, int rem, int t
             o.fin_row = r_first;
             o.fin_val = f0;
         }
-        if (!((mask >> (n_mine - 1)) & 1u)) {  // the last entry's row is still open
-            o.open_row = rr[kFull ? P - 1 : 0];
-            if (!kFull)
-#pragma unroll
-                for (int j = 1; j < P; ++j)
-                    if (j < n_mine) o.open_row = rr[j];
+        if (!((mask >> (n_mine - 1)) & 1u)) {
+            o.open_row = s_row[ls + n_mine - 1];
             o.open_val = acc;
+        }
+        if (kBeta) {
+            T yo[P];
+#pragma unroll
+            for (int q = 0; q < P; ++q) yo[q] = q < k ? y[sr[q]] : T(0);
+#pragma unroll
+            for (int q = 0; q < P; ++q)
+                if (q < k) {
+                    const T vq = kAlpha ? alpha * to_t<V, T>(sv[q]) : to_t<V, T>(sv[q]);
+                    y[sr[q]] = fma(beta, yo[q], vq);
+                }
+        } else {
+#pragma unroll
+            for (int q = 0; q < P; ++q)
+                if (q < k) seg_store<kAlpha, kBeta>(y, sr[q], to_t<V, T>(sv[q]), alpha, beta);
         }
         return o;
     }

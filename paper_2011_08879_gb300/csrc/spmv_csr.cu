@@ -416,30 +416,54 @@ static SegScratch scratch_of(const SegArrays& sa)
     return SegScratch{sa.tail_val, sa.tail_row, sa.tail_pass, sa.head_val, sa.head_row};
 }
 
+int coo_entries_per_thread(const gko_matrix* A)
+{
+    const int64_t band = A->csr.band;
+    return (band >= 0 && band <= std::max<int64_t>(4096, A->n_rows / 16)) ? kSegPCooLocal : kSegPCoo;
+}
+
+template <int PC>
+static cudaError_t launch_coo_p(int64_t n_rows, int64_t n_cols, int64_t nnz, const int32_t* rows, const int32_t* col,
+                                const double* val, const SegScratch& sc, const double* x, double* y, double alpha,
+                                double beta, uint32_t* err, cudaStream_t st, bool accumulate)
+{
+    const bool a = alpha != 1.0, b = beta != 0.0;
+    if (accumulate)  // y += alpha * A x, rows without entries untouched
+        return a ? seg_launch<PC, double, double, true, true, true, true, false, kSegThreadsCoo>(
+                       n_rows, n_cols, nnz, nullptr, rows, col, val, nullptr, sc, x, y, alpha, 1.0, err, st)
+                 : seg_launch<PC, double, double, false, true, true, true, false, kSegThreadsCoo>(
+                       n_rows, n_cols, nnz, nullptr, rows, col, val, nullptr, sc, x, y, alpha, 1.0, err, st);
+#define GKO_COO(KA, KB)                                                                                   \
+    return seg_launch<PC, double, double, KA, KB, true, false, false, kSegThreadsCoo>(                    \
+        n_rows, n_cols, nnz, nullptr, rows, col, val, nullptr, sc, x, y, alpha, beta, err, st)
+    if (a && b) GKO_COO(true, true);
+    if (a) GKO_COO(true, false);
+    if (b) GKO_COO(false, true);
+    GKO_COO(false, false);
+#undef GKO_COO
+}
+
 int launch_seg(int64_t n_rows, int64_t n_cols, int64_t nnz, const int32_t* row_ptr, const int32_t* rows, const int32_t* col,
                const double* val, const int32_t* thr_row, const SegArrays& sa, const double* x, double* y,
-               double alpha, double beta, uint32_t* err, bool coo, cudaStream_t st, bool accumulate)
+               double alpha, double beta, uint32_t* err, bool coo, cudaStream_t st, bool accumulate, int coo_p)
 {
     const SegScratch sc = scratch_of(sa);
     cudaError_t e;
-    if (accumulate) {  // y += alpha * A x, rows without entries untouched
-        if (nnz == 0) return GKO_OK;
-        if (alpha != 1.0)
-            e = seg_launch<kSegPCoo, double, double, true, true, true, true, false, kSegThreadsCoo>(
-                n_rows, n_cols, nnz, row_ptr, rows, col, val, thr_row, sc, x, y, alpha, 1.0, err, st);
-        else
-            e = seg_launch<kSegPCoo, double, double, false, true, true, true, false, kSegThreadsCoo>(
-                n_rows, n_cols, nnz, row_ptr, rows, col, val, thr_row, sc, x, y, alpha, 1.0, err, st);
-        if (e != cudaSuccess) return cuda_fail(e, "load-balanced SpMV launch");
+    if (accumulate && nnz == 0) return GKO_OK;
+    if (!accumulate && nnz == 0) return scale_vector(n_rows, y, beta, st);
+    if (coo) {
+        e = coo_p == kSegPCooLocal
+                ? launch_coo_p<kSegPCooLocal>(n_rows, n_cols, nnz, rows, col, val, sc, x, y, alpha, beta, err, st,
+                                              accumulate)
+                : launch_coo_p<kSegPCoo>(n_rows, n_cols, nnz, rows, col, val, sc, x, y, alpha, beta, err, st,
+                                         accumulate);
+        if (e != cudaSuccess) return cuda_fail(e, "load-balanced COO SpMV launch");
         return GKO_OK;
     }
-    if (nnz == 0) return scale_vector(n_rows, y, beta, st);
     const bool a = alpha != 1.0, b = beta != 0.0;
 #define GKO_SEG(KA, KB)                                                                                          \
-    e = coo ? seg_launch<kSegPCoo, double, double, KA, KB, true, false, false, kSegThreadsCoo>(                     \
-                  n_rows, n_cols, nnz, row_ptr, rows, col, val, thr_row, sc, x, y, alpha, beta, err, st)         \
-            : seg_launch<kSegP, double, double, KA, KB, false, false>(n_rows, n_cols, nnz, row_ptr, rows, col,   \
-                                                                      val, thr_row, sc, x, y, alpha, beta, err, st)
+    e = seg_launch<kSegP, double, double, KA, KB, false, false>(n_rows, n_cols, nnz, row_ptr, rows, col, val,    \
+                                                                 thr_row, sc, x, y, alpha, beta, err, st)
     if (a && b)
         GKO_SEG(true, true);
     else if (a)
@@ -496,7 +520,7 @@ int spmv_csr(const gko_matrix* A, int config, const double* x, double* y, double
             break;
         case GKO_CFG_CSR_NNZSPLIT:
             return launch_seg(A->n_rows, A->n_cols, A->nnz, A->csr.row_ptr, nullptr, A->csr.col, A->csr.val, A->csr.thr_row,
-                              A->csr.seg, x, y, alpha, beta, A->d_err, false, st, false);
+                              A->csr.seg, x, y, alpha, beta, A->d_err, false, st, false, 0);
         default: return fail(GKO_ERR_INVALID_ARG, "configuration does not apply to CSR");
     }
     GKO_CUDA(cudaGetLastError());
@@ -508,7 +532,7 @@ int spmv_coo(const gko_matrix* A, const CooPart& coo, const double* x, double* y
 {
     if (A->n_rows == 0) return GKO_OK;
     return launch_seg(A->n_rows, A->n_cols, coo.nnz, nullptr, coo.row, coo.col, coo.val, nullptr, coo.seg, x, y, alpha, beta,
-                      A->d_err, true, st, false);
+                      A->d_err, true, st, false, coo.P);
 }
 
 }  // namespace gko

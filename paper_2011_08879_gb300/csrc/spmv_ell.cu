@@ -17,7 +17,7 @@ namespace gko {
 
 int launch_seg(int64_t n_rows, int64_t n_cols, int64_t nnz, const int32_t* row_ptr, const int32_t* rows, const int32_t* col,
                const double* val, const int32_t* thr_row, const SegArrays& sa, const double* x, double* y,
-               double alpha, double beta, uint32_t* err, bool coo, cudaStream_t st, bool accumulate);
+               double alpha, double beta, uint32_t* err, bool coo, cudaStream_t st, bool accumulate, int coo_p);
 
 template <bool kAlpha, bool kBeta>
 __device__ __forceinline__ void store_pair(double* y, int64_t r, int64_t n, double a0, double a1, double alpha,
@@ -204,7 +204,7 @@ int spmv_hybrid(const gko_matrix* A, const double* x, double* y, double alpha, d
     GKO_TRY(spmv_ell(A, h.ell, x, y, alpha, beta, st));
     if (h.coo.nnz == 0) return GKO_OK;
     return launch_seg(A->n_rows, A->n_cols, h.coo.nnz, nullptr, h.coo.row, h.coo.col, h.coo.val, nullptr, h.coo.seg, x, y,
-                      alpha, 1.0, A->d_err, true, st, true);
+                      alpha, 1.0, A->d_err, true, st, true, h.coo.P);
 }
 
 }  // namespace gko
