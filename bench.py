@@ -170,7 +170,7 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def profile_traffic(cases):
+def profile_traffic(cases, path=None):
     """DRAM bytes per launch of each (matrix, format) case, from the committed
     ncu summary if it was taken on the current kernel sources.  The capture
     runs the quarter-size sweep (same matrix kinds, `--sweep small`) and the
@@ -179,7 +179,7 @@ def profile_traffic(cases):
     proportion to the entries it moves, so the full-size traffic is that
     ratio times the full case's algorithmic bytes."""
     ratios, src = {}, None
-    path = os.path.join(ROOT, "profiles", "spmv_dram_traffic.txt")
+    path = path or os.path.join(ROOT, "profiles", "spmv_dram_traffic.txt")
     if os.path.exists(path):
         for line in open(path):
             parts = line.split()

@@ -111,12 +111,21 @@ __device__ __forceinline__ T seg_walk(int start, int r, const T* s_part, const i
     return sum;
 }
 
-template <bool kAlpha, bool kBeta, typename T>
+// y[r] = alpha v + beta y[r].  kRed (accumulate mode of the hybrid format's
+// COO part, beta = 1): y[r] += alpha v as a fire-and-forget reduction in L2,
+// so no load of y stalls the thread; every row gets exactly one such add per
+// launch (rows crossing tiles only from the fix-up), so the result does not
+// depend on the order of the adds.
+template <bool kAlpha, bool kBeta, bool kRed = false, typename T>
 __device__ __forceinline__ void seg_store(T* y, int64_t r, T v, T alpha, T beta)
 {
-    T out = kAlpha ? alpha * v : v;
-    if (kBeta) out = fma(beta, y[r], out);
-    y[r] = out;
+    if constexpr (kRed) {
+        atomicAdd(y + r, kAlpha ? alpha * v : v);
+    } else {
+        T out = kAlpha ? alpha * v : v;
+        if (kBeta) out = fma(beta, y[r], out);
+        y[r] = out;
+    }
 }
 
 __device__ __forceinline__ void fence_proxy_async_smem()
@@ -393,11 +402,11 @@ __device__ __forceinline__ SegThreadOut<T> seg_thread_coo(int ls, int rem, int t
                 o.fin_row = r_first;
                 o.fin_val = v0;
             } else {
-                seg_store<kAlpha, kBeta>(y, r_first, v0, alpha, beta);
+                seg_store<kAlpha, kBeta, kSkipEmpty>(y, r_first, v0, alpha, beta);
             }
         }
-        if (n_end > 1) seg_store<kAlpha, kBeta>(y, s_row[ls + e0], v1, alpha, beta);
-        if (n_end > 2) seg_store<kAlpha, kBeta>(y, s_row[ls + e1], v2, alpha, beta);
+        if (n_end > 1) seg_store<kAlpha, kBeta, kSkipEmpty>(y, s_row[ls + e0], v1, alpha, beta);
+        if (n_end > 2) seg_store<kAlpha, kBeta, kSkipEmpty>(y, s_row[ls + e1], v2, alpha, beta);
         if (!((mask >> (n_mine - 1)) & 1u)) {  // the last entry's row is still open
             o.open_row = s_row[ls + n_mine - 1];
             o.open_val = acc;
@@ -438,7 +447,11 @@ __device__ __forceinline__ SegThreadOut<T> seg_thread_coo(int ls, int rem, int t
             o.open_row = s_row[ls + n_mine - 1];
             o.open_val = acc;
         }
-        if (kBeta) {
+        if (kSkipEmpty) {  // accumulate mode: reductions, no loads of y
+#pragma unroll
+            for (int q = 0; q < P; ++q)
+                if (q < k) seg_store<kAlpha, kBeta, true>(y, sr[q], to_t<V, T>(sv[q]), alpha, beta);
+        } else if (kBeta) {
             T yo[P];
 #pragma unroll
             for (int q = 0; q < P; ++q) yo[q] = q < k ? y[sr[q]] : T(0);
@@ -471,7 +484,7 @@ __device__ __forceinline__ SegThreadOut<T> seg_thread_coo(int ls, int rem, int t
                     o.fin_row = row;
                     o.fin_val = acc;
                 } else {
-                    seg_store<kAlpha, kBeta>(y, row, acc, alpha, beta);
+                    seg_store<kAlpha, kBeta, kSkipEmpty>(y, row, acc, alpha, beta);
                 }
                 acc = T(0);
                 pending = false;
@@ -491,8 +504,9 @@ __device__ __forceinline__ SegThreadOut<T> seg_thread_coo(int ls, int rem, int t
 
 // kCoo = false: CSR with row_ptr and the per-thread start rows thr_row
 // (thr_row[g] = row holding entry g*P).  kCoo = true: COO with row[].
-// kSkipEmpty: rows without entries are left untouched (used to add the COO
-// part of the hybrid format onto the ELL part's result, with beta = 1).
+// kSkipEmpty: accumulate mode, y[r] += alpha (A x)_r by L2 reductions for
+// the rows with entries, the others left untouched (adds the COO part of the
+// hybrid format onto the ELL part's result; COO only, beta = 1).
 // kExactTail (COO only): the arrays end exactly at nnz (caller-owned, not
 // padded), so the last tile bulk-copies only whole 16-byte groups and the
 // threads load the remaining few entries themselves.
@@ -746,7 +760,7 @@ __global__ void __launch_bounds__(NT, kSegThreadsPerSm / NT)
                 sc.head_row[tile] = o.fin_row;
                 s_head_done = 1;
             } else {
-                seg_store<kAlpha, kBeta>(y, o.fin_row, total, alpha, beta);
+                seg_store<kAlpha, kBeta, kCoo && kSkipEmpty>(y, o.fin_row, total, alpha, beta);
             }
         }
         // the tile's last active thread publishes the carry of a row open at t1
@@ -777,7 +791,7 @@ __global__ void __launch_bounds__(NT, kSegThreadsPerSm / NT)
 
 // Finish rows that cross tile boundaries: for each tile f that deferred a
 // row r, add the carries of the preceding tiles whose open row is r.
-template <bool kAlpha, bool kBeta, typename T>
+template <bool kAlpha, bool kBeta, typename T, bool kRed = false>
 __global__ void seg_fixup_kernel(int64_t n_tiles, SegScratchT<T> sc, T* __restrict__ y, T alpha, T beta)
 {
     const int64_t f = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
@@ -790,7 +804,7 @@ __global__ void seg_fixup_kernel(int64_t n_tiles, SegScratchT<T> sc, T* __restri
         if (!sc.tail_pass[t]) break;
     }
     const T total = acc + sc.head_val[f];
-    seg_store<kAlpha, kBeta>(y, r, total, alpha, beta);
+    seg_store<kAlpha, kBeta, kRed>(y, r, total, alpha, beta);
 }
 
 // 2 CTAs per SM (the row-block CSR kernel's grid uses the same count)
@@ -817,7 +831,7 @@ inline cudaError_t seg_launch(int64_t n_rows, int64_t n_cols, int64_t nnz, const
         <<<static_cast<unsigned>(grid), NT, smem, st>>>(n_rows, n_cols, nnz, row_ptr, rows, col, val, thr_row, x, y,
                                                         alpha, beta, sc, err, first_wait_polls());
     if (tiles > 1)
-        seg_fixup_kernel<kAlpha, kBeta, T>
+        seg_fixup_kernel<kAlpha, kBeta, T, kCoo && kSkip>
             <<<static_cast<unsigned>((tiles + 255) / 256), 256, 0, st>>>(tiles, sc, y, alpha, beta);
     return cudaGetLastError();
 }

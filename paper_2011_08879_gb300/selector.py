@@ -69,14 +69,18 @@ def prepare(A, stream=0):
     return M
 
 
-def measure(M, reps=5, warmup=2, flush_bytes=256 << 20, check=True, seed=7, spin_s=0.005):
+def measure(M, reps=5, warmup=2, flush_bytes=256 << 20, check=True, seed=7, spin_s=0.005, queue_s=0.02):
     """Median time (s) of every candidate on handle M (NaN: not applicable),
     plus the worst relative disagreement between candidates.
 
     The GPU is first kept busy for spin_s (clocks leave their idle state
     after the host-side set-up of the matrix), then the candidates are timed
     round robin, one repetition of each per round with L2 flushed before
-    every run, so that slow drifts of the clock hit every candidate alike."""
+    every run, so that slow drifts of the clock hit every candidate alike.
+    All timed launches are queued behind a device-side sleep of queue_s, so
+    the GPU runs them back to back: a product of a few microseconds would
+    otherwise be timed together with any delay of the host between its start
+    event and its launch (a sweep's host also receives the next matrices)."""
     torch = _torch()
     dev = torch.device("cuda", torch.cuda.current_device())
     st = torch.cuda.current_stream()
@@ -109,6 +113,7 @@ def measure(M, reps=5, warmup=2, flush_bytes=256 << 20, check=True, seed=7, spin
         flush.fill_(1.0)
         torch.cuda.synchronize()
     ev = {ci: [] for ci in live}
+    torch.cuda._sleep(int(queue_s * 2.0e9))  # ~queue_s at GB300 clocks; the queue below is host-bound
     for _ in range(reps):
         for ci in live:
             fmt, cfg = CANDIDATES[ci]

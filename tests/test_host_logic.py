@@ -149,3 +149,18 @@ def test_selector_targets_regret_and_default_rule(gko):
     got = [names[c] for c in sel.default_csr_class(F)]
     want = ["csr/%d" % c for c in (B.CFG_CSR_SUBWARP_1, B.CFG_CSR_ROWBLOCK, B.CFG_CSR_SUBWARP_4, B.CFG_CSR_BINNED)]
     assert got == want
+
+
+def test_traffic_scaled_from_the_small_capture(tmp_path):
+    """DRAM traffic per launch is the captured ratio (DRAM over algorithmic
+    bytes on the quarter-size matrix of the same kind) times the full case's
+    algorithmic bytes, and is withheld when the capture was taken on other
+    kernel sources."""
+    import bench
+    f = tmp_path / "traffic.txt"
+    cases = [dict(matrix="stencil27_128", fmt="coo", bytes=925.4e6), dict(matrix="banded_4M", fmt="ell", bytes=1e9)]
+    f.write_text("source %s\nratio stencil27/coo 1.002\n" % bench.kernel_source_hash())
+    t = bench.profile_traffic(cases, str(f))
+    assert t == {"stencil27_128/coo": 1.002 * 925.4e6}
+    f.write_text("source 0000\nratio stencil27/coo 1.002\n")
+    assert bench.profile_traffic(cases, str(f)) == {}
