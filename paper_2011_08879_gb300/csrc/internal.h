@@ -162,7 +162,6 @@ struct gko_batch {
     int32_t* col = nullptr;       // device, local column indices
     double* val = nullptr;
     int32_t* order = nullptr;     // systems sorted by decreasing size (work queue order)
-    int32_t* rperm = nullptr;     // per system, its rows (local indices) by decreasing length
     int32_t* queue = nullptr;     // device work-queue counter
     double* res = nullptr;        // per system: relative residual
     int32_t* iters = nullptr;     // per system: iterations
