@@ -165,16 +165,24 @@ __device__ __forceinline__ T ldg(const T* p)
 
 // ldg as a volatile load: issued where it stands in the source (the
 // compiler neither removes it nor moves it into the branches that use it).
-template <typename T>
+// kL2: cached in L2 only (ld.global.cg), for gathers at random columns that
+// L1 would not reuse.
+template <typename T, bool kL2 = false>
 __device__ __forceinline__ T ldg_early(const T* p)
 {
     if constexpr (sizeof(T) == 8) {
         double v;
-        asm volatile("ld.global.nc.f64 %0, [%1];" : "=d"(v) : "l"(p));
+        if constexpr (kL2)
+            asm volatile("ld.global.cg.f64 %0, [%1];" : "=d"(v) : "l"(p));
+        else
+            asm volatile("ld.global.nc.f64 %0, [%1];" : "=d"(v) : "l"(p));
         return static_cast<T>(v);
     } else {
         float v;
-        asm volatile("ld.global.nc.f32 %0, [%1];" : "=f"(v) : "l"(p));
+        if constexpr (kL2)
+            asm volatile("ld.global.cg.f32 %0, [%1];" : "=f"(v) : "l"(p));
+        else
+            asm volatile("ld.global.nc.f32 %0, [%1];" : "=f"(v) : "l"(p));
         return static_cast<T>(v);
     }
 }

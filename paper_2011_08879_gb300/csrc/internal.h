@@ -187,7 +187,8 @@ int seg_alloc(SegArrays* s, int64_t nnz, int P, int threads);
 // Entries per thread of the COO kernel for this matrix: 13 when its columns
 // stay near the diagonal (max |i - j| <= max(4096, n / 16): the gathers of x
 // hit L1), else 11 (scattered columns: the smaller shared-memory stages
-// leave L1 room for more gathers in flight).  Measured on GB300.
+// leave L1 room for more gathers in flight, and the gathers bypass L1).
+// Measured on GB300.
 int coo_entries_per_thread(const gko_matrix* A);
 void seg_free(SegArrays* s);
 int spmv_csr(const gko_matrix* A, int config, const double* x, double* y, double alpha, double beta,

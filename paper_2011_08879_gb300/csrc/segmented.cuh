@@ -332,7 +332,7 @@ __device__ __forceinline__ SegThreadOut<T> seg_thread(int ls, int le, int t0, in
 // slots, stored after the loop); the general path (rows without entries
 // get their zero stores).  kFull: every thread of the tile holds P entries
 // (all tiles but the last), so no per-entry bounds predicates are needed.
-template <int P, typename V, typename T, bool kAlpha, bool kBeta, bool kSkipEmpty, bool kFull>
+template <int P, typename V, typename T, bool kAlpha, bool kBeta, bool kSkipEmpty, bool kFull, bool kGatherL2>
 __device__ __forceinline__ SegThreadOut<T> seg_thread_coo(int ls, int rem, int t0, int cnt, const V* s_val,
                                                           const int32_t* s_col, const int32_t* s_row,
                                                           bool first_carried, int next_r_tile,
@@ -349,7 +349,7 @@ __device__ __forceinline__ SegThreadOut<T> seg_thread_coo(int ls, int rem, int t
         const bool ok = kFull || j < rem;
         const int c = ok ? s_col[ls + j] : 0;
         vv[j] = ok ? to_t<V, T>(s_val[ls + j]) : T(0);
-        xv[j] = ldg_early(x + c);
+        xv[j] = ldg_early<T, kGatherL2>(x + c);
     }
 #pragma unroll
     for (int j = 0; j < P; ++j) rr[j] = (kFull || j < rem) ? s_row[ls + j] : 0;
@@ -511,8 +511,11 @@ __device__ __forceinline__ SegThreadOut<T> seg_thread_coo(int ls, int rem, int t
 // padded), so the last tile bulk-copies only whole 16-byte groups and the
 // threads load the remaining few entries themselves.
 // NT: threads per CTA and per tile (a multiple of 32, at most 256).
+// kGatherL2 (COO): gathers of x cached in L2 only (columns scattered at
+// random: L1 would not reuse them and its lines are better left to the
+// gathers in flight).
 template <int P, typename V, typename T, bool kAlpha, bool kBeta, bool kCoo, bool kSkipEmpty, bool kExactTail = false,
-          int NT = kSegThreads>
+          int NT = kSegThreads, bool kGatherL2 = false>
 __global__ void __launch_bounds__(NT, kSegThreadsPerSm / NT)
     seg_spmv_kernel(int64_t n_rows64, int64_t n_cols64, int64_t nnz64, const int32_t* __restrict__ row_ptr,
                     const int32_t* __restrict__ rows, const int32_t* __restrict__ col,
@@ -705,11 +708,11 @@ __global__ void __launch_bounds__(NT, kSegThreadsPerSm / NT)
         if constexpr (kCoo) {
             first_carried = ti.began != 0;
             if (cnt == S::kTile)  // tile-uniform: every thread holds P entries
-                o = seg_thread_coo<P, V, T, kAlpha, kBeta, kSkipEmpty, true>(ls, le - ls, t0, cnt, s_val, s_col,
+                o = seg_thread_coo<P, V, T, kAlpha, kBeta, kSkipEmpty, true, kGatherL2>(ls, le - ls, t0, cnt, s_val, s_col,
                                                                             s_aux, first_carried, ti.next_r, x, y,
                                                                             alpha, beta);
             else
-                o = seg_thread_coo<P, V, T, kAlpha, kBeta, kSkipEmpty, false>(ls, le - ls, t0, cnt, s_val, s_col,
+                o = seg_thread_coo<P, V, T, kAlpha, kBeta, kSkipEmpty, false, kGatherL2>(ls, le - ls, t0, cnt, s_val, s_col,
                                                                              s_aux, first_carried, ti.next_r, x, y,
                                                                              alpha, beta);
         } else if (ti.staged) {
@@ -814,20 +817,20 @@ inline int seg_grid_ctas() { return device_sm_count() * kSegCtasPerSm; }
 // (V, T) pair.  sc must hold ceil(nnz / (NT * P)) tiles.  Raises the dynamic
 // shared-memory limit once per instantiation and device.
 template <int P, typename V, typename T, bool kAlpha, bool kBeta, bool kCoo, bool kSkip, bool kExact = false,
-          int NT = kSegThreads>
+          int NT = kSegThreads, bool kGatherL2 = false>
 inline cudaError_t seg_launch(int64_t n_rows, int64_t n_cols, int64_t nnz, const int32_t* row_ptr, const int32_t* rows,
                               const int32_t* col, const V* val, const int32_t* thr_row, SegScratchT<T> sc,
                               const T* x, T* y, T alpha, T beta, uint32_t* err, cudaStream_t st)
 {
     constexpr size_t smem = seg_smem_bytes<P, V, T, kCoo, NT>();
     const cudaError_t e = smem_limit_once(
-        reinterpret_cast<const void*>(seg_spmv_kernel<P, V, T, kAlpha, kBeta, kCoo, kSkip, kExact, NT>),
+        reinterpret_cast<const void*>(seg_spmv_kernel<P, V, T, kAlpha, kBeta, kCoo, kSkip, kExact, NT, kGatherL2>),
         static_cast<int>(smem));
     if (e != cudaSuccess) return e;
     const int64_t tiles = (nnz + SegShape<P, NT>::kTile - 1) / SegShape<P, NT>::kTile;
     const int64_t ctas = static_cast<int64_t>(device_sm_count()) * (kSegThreadsPerSm / NT);
     const int64_t grid = tiles < ctas ? tiles : ctas;
-    seg_spmv_kernel<P, V, T, kAlpha, kBeta, kCoo, kSkip, kExact, NT>
+    seg_spmv_kernel<P, V, T, kAlpha, kBeta, kCoo, kSkip, kExact, NT, kGatherL2>
         <<<static_cast<unsigned>(grid), NT, smem, st>>>(n_rows, n_cols, nnz, row_ptr, rows, col, val, thr_row, x, y,
                                                         alpha, beta, sc, err, first_wait_polls());
     if (tiles > 1)

@@ -428,13 +428,15 @@ static cudaError_t launch_coo_p(int64_t n_rows, int64_t n_cols, int64_t nnz, con
                                 double beta, uint32_t* err, cudaStream_t st, bool accumulate)
 {
     const bool a = alpha != 1.0, b = beta != 0.0;
+    // matrices with scattered columns (the smaller tiles) gather x through L2 only
+    constexpr bool kL2 = PC == kSegPCoo;
     if (accumulate)  // y += alpha * A x, rows without entries untouched
-        return a ? seg_launch<PC, double, double, true, true, true, true, false, kSegThreadsCoo>(
+        return a ? seg_launch<PC, double, double, true, true, true, true, false, kSegThreadsCoo, kL2>(
                        n_rows, n_cols, nnz, nullptr, rows, col, val, nullptr, sc, x, y, alpha, 1.0, err, st)
-                 : seg_launch<PC, double, double, false, true, true, true, false, kSegThreadsCoo>(
+                 : seg_launch<PC, double, double, false, true, true, true, false, kSegThreadsCoo, kL2>(
                        n_rows, n_cols, nnz, nullptr, rows, col, val, nullptr, sc, x, y, alpha, 1.0, err, st);
 #define GKO_COO(KA, KB)                                                                                   \
-    return seg_launch<PC, double, double, KA, KB, true, false, false, kSegThreadsCoo>(                    \
+    return seg_launch<PC, double, double, KA, KB, true, false, false, kSegThreadsCoo, kL2>(               \
         n_rows, n_cols, nnz, nullptr, rows, col, val, nullptr, sc, x, y, alpha, beta, err, st)
     if (a && b) GKO_COO(true, true);
     if (a) GKO_COO(true, false);
