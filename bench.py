@@ -604,7 +604,7 @@ def run_extras(gko, torch, dev, st, selector=True, selector_matrices=200):
     out["spmm_stencil27_k8"] = {"s": round(t_mm, 6), "eight_spmv_s": round(t_mv, 6),
                                 "speedup_vs_spmv": round(t_mv / t_mm, 3),
                                 "fp64_tfma_s": round(nnz * k / t_mm / 1e12, 4),
-                                "note": "bound by the FP64 pipe (one FMA per entry and column; ~0.6 TFMA/s measured)"}
+                                "note": "bound by the FP64 pipe (one FMA per entry and column; see ceilings.fp64_tfma_s)"}
     # BiCGSTAB on a nonsymmetric convection-diffusion operator (1024^2 grid)
     C = syn.convdiff2d(1024, 0.8)
     n = C["n_rows"]
