@@ -635,6 +635,13 @@ def run_extras(gko, torch, dev, st, selector=True, selector_matrices=200):
         x = torch.zeros_like(rhs)
         t, (s, infos) = _time_call(torch, lambda: G.cg(rhs, x, tol=1e-10, maxit=1000, stream=st))
     its = [i.iterations for i in infos]
+    # the other layout of the autotuner's space, timed on its own for the record
+    alt = {}
+    for bs_alt in (64, -128, -256):
+        for _ in range(2):
+            x2 = torch.zeros_like(rhs)
+            t_alt, _r = _time_call(torch, lambda: G.cg(rhs, x2, tol=1e-10, maxit=1000, block_size=bs_alt, stream=st))
+        alt[str(bs_alt)] = round(t_alt, 5)
     # roofline of the batched solve: every iteration re-streams the system's
     # CSR (values + indices + row pointers); vectors live in shared memory.
     # FP64 work per iteration and row: the product's FMAs plus five vector
@@ -649,6 +656,7 @@ def run_extras(gko, torch, dev, st, selector=True, selector_matrices=200):
                               "max_rel_residual": max(i.rel_residual for i in infos),
                               "iterations_mean": round(float(np.mean(its)), 2),
                               "matrix_GBs": round(mat_bytes / t / 1e9, 1),
+                              "s_by_block_size": alt,
                               "fp64_tfma_s": round(fmas / t / 1e12, 4)}
     # hardware ceilings of this GPU (FP64 / FP32 FMA rate, random gathers)
     f64, f32, g16 = gko.binding.gko_measure_ceilings(1 << 21, st)

@@ -402,18 +402,24 @@ int gko_batch_create(int64_t count, const int64_t* row_off, const int32_t* row_p
 int gko_batch_destroy(gko_batch* B);
 
 /* Solve all systems of the batch by CG, one thread block per system taken
- * from a device work queue (largest systems first), vectors in shared
- * memory, launched as one persistent kernel inside a CUDA graph (the
- * instantiated graph is kept in the batch and relaunched by later calls
- * with the same block size, b, x, tol and maxit).
- * block_size 0 = autotuned choice.  b, x device vectors of row_off[count]
+ * from a device work queue (largest systems first), launched as one
+ * persistent kernel inside a CUDA graph (the instantiated graph is kept in
+ * the batch and relaunched by later calls with the same block size, b, x,
+ * tol and maxit).  block_size 64, 128, 256, 512 or 1024: x, r, p and A p
+ * of the system in shared memory; -128, -256, -512 or -1024: that many
+ * threads with 1024 / |block_size| rows each, x, r and A p of a thread's
+ * rows in registers and only p in shared memory (systems of at most 1024
+ * rows); 0 = the autotuned choice.  b, x device vectors of row_off[count]
  * entries (x: initial guess in, solution out).  infos: host array of count
  * entries or NULL.  Returns the worst status.  Synchronises the stream. */
 int gko_cg_batched(gko_batch* B, const double* b, double* x, double tol, int maxit, int block_size,
                    void* stream, gko_solve_info* infos);
 
-/* Run the batched-CG autotuner: times every candidate block size on this
- * batch and keeps the fastest for block_size 0.  *best receives it. */
+/* Run the batched-CG autotuner: times every candidate launch on this batch
+ * (the block sizes and layouts of gko_cg_batched: 64 .. 1024 with the
+ * vectors in shared memory, and, when no system exceeds 1024 rows, -128 ..
+ * -1024 with the rows' vectors in registers) and keeps the fastest for
+ * block_size 0.  *best receives it. */
 int gko_batch_autotune(gko_batch* B, const double* b, double* x, double tol, int maxit,
                        void* stream, int* best);
 

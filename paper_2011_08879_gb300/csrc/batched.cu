@@ -179,6 +179,220 @@ __global__ void __launch_bounds__(BS)
     }
 }
 
+// ---------------------------------------------------------------------------
+// Register-resident variant: thread t owns rows t, t + BS, ..., t + (R-1) BS
+// of its system (R rows per thread, BS * R >= the largest system), keeps x,
+// r and (A p) of those rows in registers and only the direction p, which
+// the product gathers, in shared memory (8 bytes per row instead of 32), so
+// more blocks share an SM.  Same recurrence, stops and outputs as
+// batched_cg_kernel; the autotuner times both layouts.
+
+template <int BS, int R>
+__device__ __forceinline__ void sys_spmv_reg(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
+                                             const double* __restrict__ val, int32_t base, const double* v, double* q)
+{
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+        const int i = threadIdx.x + k * BS;
+        double acc = 0.0;
+        if (i < n) {
+            const int32_t k1 = rp[i + 1] - base;
+            for (int32_t kk = rp[i] - base; kk < k1; ++kk) acc = fma(val[kk], v[col[kk]], acc);
+        }
+        q[k] = acc;
+    }
+}
+
+// sum over the thread's rows of (b_i - (A v)_i)^2
+template <int BS, int R>
+__device__ __forceinline__ double sys_resid2_reg(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
+                                                 const double* __restrict__ val, int32_t base, const double* v,
+                                                 const double* __restrict__ b)
+{
+    double tt = 0.0;
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+        const int i = threadIdx.x + k * BS;
+        if (i < n) {
+            double acc = 0.0;
+            const int32_t k1 = rp[i + 1] - base;
+            for (int32_t kk = rp[i] - base; kk < k1; ++kk) acc = fma(val[kk], v[col[kk]], acc);
+            const double t = b[i] - acc;
+            tt = fma(t, t, tt);
+        }
+    }
+    return tt;
+}
+
+template <int BS, int R>
+__global__ void __launch_bounds__(BS)
+    batched_cg_reg_kernel(int64_t count, const int64_t* __restrict__ row_off, const int32_t* __restrict__ row_ptr,
+                          const int32_t* __restrict__ col_all, const double* __restrict__ val_all,
+                          const int32_t* __restrict__ order, int32_t* queue, const double* __restrict__ b_all,
+                          double* __restrict__ x_all, double tol, int maxit, double* __restrict__ res_out,
+                          int32_t* __restrict__ it_out, int32_t* __restrict__ st_out)
+{
+    extern __shared__ __align__(16) double ps[];  // the direction p (or x while a residual is formed)
+    __shared__ double red[BS / 32];
+    __shared__ int s_next;
+
+    while (true) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_next = atomicAdd(queue, 1);
+        __syncthreads();
+        const int qi = s_next;
+        if (qi >= count) return;
+        const int sys = order[qi];
+        const int64_t r0 = row_off[sys];
+        const int n = static_cast<int>(row_off[sys + 1] - r0);
+        const int32_t* rp = row_ptr + r0;
+        const int32_t base = rp[0];
+        const int32_t* col = col_all + base;
+        const double* val = val_all + base;
+        const double* b = b_all + r0;
+        double* x = x_all + r0;
+
+        double xr[R], rr[R], qr[R];
+        double bb = 0.0;
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            const int i = threadIdx.x + k * BS;
+            xr[k] = i < n ? x[i] : 0.0;
+            rr[k] = i < n ? b[i] : 0.0;
+            bb = fma(rr[k], rr[k], bb);
+        }
+        const double bnorm = sqrt(block_dot_sum<BS>(bb, red));
+        if (bnorm == 0.0) {
+#pragma unroll
+            for (int k = 0; k < R; ++k)
+                if (threadIdx.x + k * BS < n) x[threadIdx.x + k * BS] = 0.0;
+            if (threadIdx.x == 0) {
+                res_out[sys] = 0.0;
+                it_out[sys] = 0;
+                st_out[sys] = GKO_OK;
+            }
+            continue;
+        }
+        // r = b - A x (the product gathers x, staged in ps); then p = r
+#pragma unroll
+        for (int k = 0; k < R; ++k)
+            if (threadIdx.x + k * BS < n) ps[threadIdx.x + k * BS] = xr[k];
+        __syncthreads();
+        sys_spmv_reg<BS, R>(n, rp, col, val, base, ps, qr);
+        __syncthreads();  // every gather of x done before ps becomes p
+        double rho = 0.0;
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            const int i = threadIdx.x + k * BS;
+            if (i < n) {
+                rr[k] -= qr[k];
+                ps[i] = rr[k];
+                rho = fma(rr[k], rr[k], rho);
+            }
+        }
+        rho = block_dot_sum<BS>(rho, red);  // its barrier also completes p
+        int status = GKO_ERR_NOT_CONVERGED, iter = 0, checks = 0;
+        double true_res = -1.0;
+        bool stop = sqrt(rho) <= tol * bnorm;
+        if (stop) status = GKO_OK;
+        while (!stop && iter < maxit) {
+            sys_spmv_reg<BS, R>(n, rp, col, val, base, ps, qr);
+            double pq = 0.0;
+#pragma unroll
+            for (int k = 0; k < R; ++k)
+                if (threadIdx.x + k * BS < n) pq = fma(ps[threadIdx.x + k * BS], qr[k], pq);
+            pq = block_dot_sum<BS>(pq, red);
+            ++iter;
+            if (!(pq > 0.0)) {
+                status = GKO_ERR_BREAKDOWN;
+                break;
+            }
+            const double alpha = rho / pq;
+            double rn = 0.0;
+#pragma unroll
+            for (int k = 0; k < R; ++k) {
+                const int i = threadIdx.x + k * BS;
+                if (i < n) {
+                    xr[k] = fma(alpha, ps[i], xr[k]);
+                    rr[k] = fma(-alpha, qr[k], rr[k]);
+                    rn = fma(rr[k], rr[k], rn);
+                }
+            }
+            const double rho_new = block_dot_sum<BS>(rn, red);  // every read of p done past its barrier
+            if (!(rho_new == rho_new)) {
+                status = GKO_ERR_BREAKDOWN;
+                break;
+            }
+            if (sqrt(rho_new) <= tol * bnorm) {
+                // confirm with the true residual: stage x in ps, keeping p's own rows in qr
+#pragma unroll
+                for (int k = 0; k < R; ++k) {
+                    const int i = threadIdx.x + k * BS;
+                    if (i < n) {
+                        qr[k] = ps[i];
+                        ps[i] = xr[k];
+                    }
+                }
+                __syncthreads();
+                const double tt = sys_resid2_reg<BS, R>(n, rp, col, val, base, ps, b);
+                true_res = sqrt(block_dot_sum<BS>(tt, red)) / bnorm;  // every gather of x done past its barrier
+#pragma unroll
+                for (int k = 0; k < R; ++k)
+                    if (threadIdx.x + k * BS < n) ps[threadIdx.x + k * BS] = qr[k];
+                ++checks;
+                if (true_res <= tol) {
+                    status = GKO_OK;
+                    break;
+                }
+                if (checks >= 4) break;
+                true_res = -1.0;
+            }
+            const double beta = rho_new / rho;
+            rho = rho_new;
+#pragma unroll
+            for (int k = 0; k < R; ++k)
+                if (threadIdx.x + k * BS < n) ps[threadIdx.x + k * BS] = fma(beta, ps[threadIdx.x + k * BS], rr[k]);
+            __syncthreads();  // p complete before the next product
+        }
+        if (true_res < 0.0) {
+            __syncthreads();  // no thread still gathers p
+#pragma unroll
+            for (int k = 0; k < R; ++k)
+                if (threadIdx.x + k * BS < n) ps[threadIdx.x + k * BS] = xr[k];
+            __syncthreads();
+            const double tt = sys_resid2_reg<BS, R>(n, rp, col, val, base, ps, b);
+            true_res = sqrt(block_dot_sum<BS>(tt, red)) / bnorm;
+        }
+#pragma unroll
+        for (int k = 0; k < R; ++k)
+            if (threadIdx.x + k * BS < n) x[threadIdx.x + k * BS] = xr[k];
+        if (threadIdx.x == 0) {
+            res_out[sys] = true_res;
+            it_out[sys] = iter;
+            st_out[sys] = status;
+        }
+    }
+}
+
+template <int BS, int R>
+static int launch_batched_reg(gko_batch* B, const double* b, double* x, double tol, int maxit, cudaStream_t st)
+{
+    if (B->max_rows > BS * R) return fail(GKO_ERR_INVALID_ARG, "batched CG: systems larger than block x rows");
+    const size_t smem = static_cast<size_t>(B->max_rows) * sizeof(double);
+    GKO_CUDA(smem_limit_once(reinterpret_cast<const void*>(batched_cg_reg_kernel<BS, R>), static_cast<int>(smem)));
+    int per_sm = 0;
+    const int sms = device_sm_count();
+    GKO_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_cg_reg_kernel<BS, R>, BS, smem));
+    if (per_sm < 1) return fail(GKO_ERR_INVALID_ARG, "batched CG: block does not fit on an SM");
+    const int64_t grid = std::min<int64_t>(static_cast<int64_t>(per_sm) * sms, B->count);
+    GKO_CUDA(cudaMemsetAsync(B->queue, 0, sizeof(int32_t), st));
+    batched_cg_reg_kernel<BS, R><<<static_cast<unsigned>(std::max<int64_t>(grid, 1)), BS, smem, st>>>(
+        B->count, B->row_off, B->row_ptr, B->col, B->val, B->order, B->queue, b, x, tol, maxit, B->res, B->iters,
+        B->status);
+    GKO_CUDA(cudaGetLastError());
+    return GKO_OK;
+}
+
 struct BatchLaunch {
     const void* fn;
     int bs;
@@ -202,16 +416,23 @@ static int launch_batched(gko_batch* B, const double* b, double* x, double tol, 
     return GKO_OK;
 }
 
+// Launch configurations: block sizes 64..1024 with the vectors in shared
+// memory; -BS for the register-resident layout of BS threads with R =
+// 1024 / BS rows per thread.
 static int launch_any(gko_batch* B, int bs, const double* b, double* x, double tol, int maxit, cudaStream_t st)
 {
     switch (bs) {
+        case -128: return launch_batched_reg<128, 8>(B, b, x, tol, maxit, st);
+        case -256: return launch_batched_reg<256, 4>(B, b, x, tol, maxit, st);
+        case -512: return launch_batched_reg<512, 2>(B, b, x, tol, maxit, st);
+        case -1024: return launch_batched_reg<1024, 1>(B, b, x, tol, maxit, st);
         case 64: return launch_batched<64>(B, b, x, tol, maxit, st);
         case 128: return launch_batched<128>(B, b, x, tol, maxit, st);
         case 256: return launch_batched<256>(B, b, x, tol, maxit, st);
         case 512: return launch_batched<512>(B, b, x, tol, maxit, st);
         case 1024: return launch_batched<1024>(B, b, x, tol, maxit, st);
     }
-    return fail(GKO_ERR_INVALID_ARG, "block_size must be 0, 64, 128, 256, 512 or 1024");
+    return fail(GKO_ERR_INVALID_ARG, "block_size must be 0, 64, 128, 256, 512, 1024 or -128, -256, -512, -1024");
 }
 
 // run [queue reset + kernel] as a captured CUDA graph; the instantiated
@@ -378,8 +599,9 @@ int gko_batch_autotune(gko_batch* B, const double* b, double* x, double tol, int
     GKO_CUDA(cudaEventCreate(&e1));
     float best_ms = 0.0f;
     int best_bs = 0;
-    const int cands[] = {64, 128, 256, 512, 1024};
+    const int cands[] = {64, 128, 256, 512, 1024, -128, -256, -512, -1024};
     for (int bs : cands) {
+        if (bs < 0 && B->max_rows > 1024) continue;  // R = 1024 / BS rows per thread must cover the systems
         float tot = 0.0f;
         int s = GKO_OK;
         for (int rep = 0; rep < 3 && s == GKO_OK; ++rep) {
@@ -404,7 +626,7 @@ int gko_batch_autotune(gko_batch* B, const double* b, double* x, double tol, int
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (!best_bs) return fail(GKO_ERR_INVALID_ARG, "no block size could be launched");
-    B->best_block = best_bs;
+    B->best_block = best_bs;  // negative: the register-resident layout
     *best = best_bs;
     return GKO_OK;
 }
