@@ -86,6 +86,10 @@ def _declare(L):
         "orc_cg": (_INT, [_I64, _P, _P, _P, _P, _P, _D, _INT, _P, _P]),
         "orc_cg_single_reduction": (_INT, [_I64, _P, _P, _P, _P, _P, _D, _INT, _P, _P]),
         "orc_pcg_jacobi": (_INT, [_I64, _P, _P, _P, _P, _P, _D, _INT, _P, _P]),
+        "orc_bj_blocks": (_INT, [_I64, _P, _P, _INT, _P, _P]),
+        "orc_bj_invert": (_INT, [_I64, _P, _P, _P, _INT, _P, _I64, _P]),
+        "orc_bj_apply": (None, [_INT, _P, _I64, _P, _P, _P]),
+        "orc_pcg_block_jacobi": (_INT, [_I64, _P, _P, _P, _INT, _P, _P, _D, _INT, _P, _P]),
         "orc_bicgstab": (_INT, [_I64, _P, _P, _P, _P, _P, _D, _INT, _P, _P]),
         "orc_spmm_csr": (None, [_I64, _P, _P, _P, _I64, _P, _I64, _D, _D, _P, _I64]),
         "orc_gmres": (_INT, [_I64, _P, _P, _P, _P, _P, _D, _INT, _INT, _P, _P]),
@@ -347,6 +351,52 @@ def pcg_jacobi(A, b, x0=None, tol=1e-10, maxit=10000):
     x = np.zeros(n) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
     it, res = C.c_int(0), C.c_double(0.0)
     st = lib().orc_pcg_jacobi(n, _p(rp), _p(ci), _p(v), _p(b), _p(x), tol, maxit, C.byref(it), C.byref(res))
+    return x, int(st), it.value, res.value
+
+
+def bj_blocks(A, max_bs):
+    """Block boundaries of the block-Jacobi preconditioner (supervariables
+    of identical column lists, cut at max_bs rows, merged greedily up to
+    max_bs rows): int32 array of n_blocks + 1 row offsets."""
+    n, rp, ci, _ = _csr(A)
+    bp = np.zeros(n + 1, dtype=np.int32)
+    nb = C.c_int64(0)
+    st = lib().orc_bj_blocks(n, _p(rp), _p(ci), int(max_bs), _p(bp), C.byref(nb))
+    if st != OK:
+        raise ValueError("max_bs must be in 1..32")
+    return bp[:nb.value + 1].copy()
+
+
+def bj_invert(A, block_ptr, max_bs):
+    """Inverses of the diagonal blocks, n * max_bs doubles: entry (i, j) of
+    the block starting at row o with s rows at o * max_bs + j * s + i.
+    Returns (status, inv); status BREAKDOWN for a singular block."""
+    n, rp, ci, v = _csr(A)
+    bp = _c(block_ptr, np.int32)
+    inv = np.zeros(max(n, 1) * max_bs)
+    st = lib().orc_bj_invert(n, _p(rp), _p(ci), _p(v), int(max_bs), _p(bp), len(bp) - 1, _p(inv))
+    return int(st), inv[:n * max_bs]
+
+
+def bj_apply(block_ptr, max_bs, inv, r):
+    """z = M^-1 r with the inverses of bj_invert."""
+    bp = _c(block_ptr, np.int32)
+    r = _c(r, np.float64)
+    z = np.zeros(len(r))
+    inv = _c(inv, np.float64)
+    lib().orc_bj_apply(int(max_bs), _p(bp), len(bp) - 1, _p(inv), _p(r), _p(z))
+    return z
+
+
+def pcg_block_jacobi(A, b, max_bs, x0=None, tol=1e-10, maxit=10000):
+    """CG preconditioned by block-Jacobi with blocks of at most max_bs rows.
+    Returns (x, status, iterations, true rel. residual)."""
+    n, rp, ci, v = _csr(A)
+    b = _c(b, np.float64)
+    x = np.zeros(n) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
+    it, res = C.c_int(0), C.c_double(0.0)
+    st = lib().orc_pcg_block_jacobi(n, _p(rp), _p(ci), _p(v), int(max_bs), _p(b), _p(x), tol, maxit,
+                                    C.byref(it), C.byref(res))
     return x, int(st), it.value, res.value
 
 

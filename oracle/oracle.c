@@ -812,6 +812,242 @@ int orc_pcg_jacobi(int64_t n, const int32_t *row_ptr, const int32_t *col, const 
     return status;
 }
 
+/* ---------------------------------------------------- block-Jacobi
+ * A block-Jacobi preconditioner M = blockdiag(A_11, ..., A_kk), the
+ * diagonal blocks of A on runs of consecutive rows, applied as
+ * z = M^-1 r.  The paper benchmarks Krylov solvers (Sec. 6.2) without
+ * defining a preconditioner; this is the textbook block-Jacobi (Saad,
+ * Iterative Methods for Sparse Linear Systems, 2nd ed., Sec. 10.2, with the
+ * blocks chosen as below).
+ *
+ * Blocks, in two steps:
+ *   1. supervariables: maximal runs of consecutive rows whose stored column
+ *      index lists are identical (same length, same indices in the same
+ *      order), cut into pieces of at most max_bs rows (full pieces first);
+ *   2. agglomeration: in row order, each piece joins the current block when
+ *      the block then has at most max_bs rows, else it opens a new block.
+ * block_ptr receives n_blocks + 1 boundaries (room for n + 1). */
+static int same_pattern(const int32_t *row_ptr, const int32_t *col, int64_t a, int64_t b)
+{
+    int64_t la = row_ptr[a + 1] - row_ptr[a], lb = row_ptr[b + 1] - row_ptr[b];
+    if (la != lb)
+        return 0;
+    for (int64_t k = 0; k < la; ++k)
+        if (col[row_ptr[a] + k] != col[row_ptr[b] + k])
+            return 0;
+    return 1;
+}
+
+int orc_bj_blocks(int64_t n, const int32_t *row_ptr, const int32_t *col, int max_bs, int32_t *block_ptr,
+                  int64_t *n_blocks)
+{
+    if (max_bs < 1 || max_bs > 32)
+        return ORC_INVALID;
+    /* step 1: the starts of the supervariable pieces, then a sentinel n */
+    int64_t *piece = (int64_t *)malloc((size_t)(n + 1) * sizeof(int64_t));
+    int64_t n_pieces = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        int starts = i == 0 || !same_pattern(row_ptr, col, i - 1, i) ||
+                     i - piece[n_pieces - 1] == max_bs;
+        if (starts)
+            piece[n_pieces++] = i;
+    }
+    piece[n_pieces] = n;
+    /* step 2: greedy agglomeration of consecutive pieces */
+    int64_t nb = 0;
+    block_ptr[0] = 0;
+    for (int64_t v = 0; v < n_pieces; ++v) {
+        int64_t end = piece[v + 1];
+        if (end - block_ptr[nb] > max_bs) { /* the piece opens a new block */
+            ++nb;
+            block_ptr[nb] = (int32_t)piece[v];
+        }
+    }
+    if (n > 0) {
+        ++nb;
+        block_ptr[nb] = (int32_t)n;
+    }
+    *n_blocks = nb;
+    free(piece);
+    return ORC_OK;
+}
+
+/* The inverse of every diagonal block B (rows and columns o .. o+s-1 of A,
+ * duplicates summed), by Gauss-Jordan elimination with partial pivoting on
+ * [B | I] (Golub and Van Loan, Matrix Computations, Sec. 3.4): for each
+ * column c the row of largest |B(i, c)|, i >= c, is swapped into row c,
+ * row c is divided by the pivot, and c is eliminated from every other row.
+ * Layout: entry (i, j) of the inverse of the block starting at row o with
+ * s rows is inv[o * max_bs + j * s + i] (n * max_bs doubles in all).  A
+ * zero pivot (a singular block) returns ORC_BREAKDOWN. */
+int orc_bj_invert(int64_t n, const int32_t *row_ptr, const int32_t *col, const double *val, int max_bs,
+                  const int32_t *block_ptr, int64_t n_blocks, double *inv)
+{
+    double B[32][32], E[32][32];
+    (void)n;
+    for (int64_t k = 0; k < n_blocks; ++k) {
+        int64_t o = block_ptr[k];
+        int s = (int)(block_ptr[k + 1] - o);
+        for (int i = 0; i < s; ++i)
+            for (int j = 0; j < s; ++j) {
+                B[i][j] = 0.0;
+                E[i][j] = i == j ? 1.0 : 0.0;
+            }
+        for (int i = 0; i < s; ++i)
+            for (int64_t e = row_ptr[o + i]; e < row_ptr[o + i + 1]; ++e)
+                if (col[e] >= o && col[e] < o + s)
+                    B[i][col[e] - o] += val[e];
+        for (int c = 0; c < s; ++c) {
+            int p = c;
+            for (int i = c + 1; i < s; ++i)
+                if (fabs(B[i][c]) > fabs(B[p][c]))
+                    p = i;
+            if (B[p][c] == 0.0)
+                return ORC_BREAKDOWN;
+            for (int j = 0; j < s; ++j) {
+                double t = B[c][j];
+                B[c][j] = B[p][j];
+                B[p][j] = t;
+                t = E[c][j];
+                E[c][j] = E[p][j];
+                E[p][j] = t;
+            }
+            double piv = B[c][c];
+            for (int j = 0; j < s; ++j) {
+                B[c][j] = B[c][j] / piv;
+                E[c][j] = E[c][j] / piv;
+            }
+            for (int i = 0; i < s; ++i) {
+                if (i == c)
+                    continue;
+                double f = B[i][c];
+                for (int j = 0; j < s; ++j) {
+                    B[i][j] = B[i][j] - f * B[c][j];
+                    E[i][j] = E[i][j] - f * E[c][j];
+                }
+            }
+        }
+        for (int i = 0; i < s; ++i)
+            for (int j = 0; j < s; ++j)
+                inv[o * max_bs + (int64_t)j * s + i] = E[i][j];
+    }
+    return ORC_OK;
+}
+
+/* z = M^-1 r, block by block: z(o+i) = sum_j inv(i, j) r(o+j). */
+void orc_bj_apply(int max_bs, const int32_t *block_ptr, int64_t n_blocks, const double *inv, const double *r,
+                  double *z)
+{
+    for (int64_t k = 0; k < n_blocks; ++k) {
+        int64_t o = block_ptr[k];
+        int s = (int)(block_ptr[k + 1] - o);
+        for (int i = 0; i < s; ++i) {
+            double acc = 0.0;
+            for (int j = 0; j < s; ++j)
+                acc = acc + inv[o * max_bs + (int64_t)j * s + i] * r[o + j];
+            z[o + i] = acc;
+        }
+    }
+}
+
+/* Preconditioned CG (Saad, Algorithm 9.1) with the block-Jacobi M above:
+ *   r = b - A x, z = M^-1 r, p = z, rho = r.z
+ *   repeat: q = A p; alpha = rho / (p.q); x += alpha p; r -= alpha q;
+ *           stop when ||r|| <= tol ||b|| (true-residual confirmation as in
+ *           orc_cg); z = M^-1 r; rho' = r.z; p = z + (rho'/rho) p
+ * A singular diagonal block is a breakdown before any step, as are a
+ * non-positive p.q and a NaN.  *iters counts the products q = A p. */
+int orc_pcg_block_jacobi(int64_t n, const int32_t *row_ptr, const int32_t *col, const double *val, int max_bs,
+                         const double *b, double *x, double tol, int maxit, int *iters, double *rel_res)
+{
+    double nb = nrm2(n, b);
+    *iters = 0;
+    if (max_bs < 1 || max_bs > 32)
+        return ORC_INVALID;
+    if (nb == 0.0) {
+        for (int64_t i = 0; i < n; ++i)
+            x[i] = 0.0;
+        *rel_res = 0.0;
+        return ORC_OK;
+    }
+    size_t bytes = (size_t)(n > 0 ? n : 1) * sizeof(double);
+    double *r = (double *)malloc(bytes), *p = (double *)malloc(bytes), *q = (double *)malloc(bytes),
+           *z = (double *)malloc(bytes), *inv = (double *)malloc(bytes * (size_t)max_bs);
+    int32_t *bp = (int32_t *)malloc((size_t)(n + 1) * sizeof(int32_t));
+    int64_t n_blocks = 0;
+    int status = ORC_NOT_CONVERGED, checks = 0;
+    orc_bj_blocks(n, row_ptr, col, max_bs, bp, &n_blocks);
+    if (orc_bj_invert(n, row_ptr, col, val, max_bs, bp, n_blocks, inv) != ORC_OK) {
+        status = ORC_BREAKDOWN;
+        maxit = 0;
+    }
+    for (int64_t i = 0; i < n; ++i)
+        r[i] = b[i];
+    orc_spmv_csr(n, row_ptr, col, val, x, -1.0, 1.0, r);
+    double rho = 0.0;
+    if (status != ORC_BREAKDOWN) {
+        orc_bj_apply(max_bs, bp, n_blocks, inv, r, z);
+        for (int64_t i = 0; i < n; ++i)
+            p[i] = z[i];
+        rho = orc_dot(n, r, z);
+        if (sqrt(orc_dot(n, r, r)) <= tol * nb) {
+            status = ORC_OK;
+            maxit = 0;
+        }
+    }
+    for (int it = 0; it < maxit; ++it) {
+        orc_spmv_csr(n, row_ptr, col, val, p, 1.0, 0.0, q);
+        *iters = it + 1;
+        double pq = orc_dot(n, p, q);
+        if (!(pq > 0.0)) {
+            status = ORC_BREAKDOWN;
+            break;
+        }
+        double alpha = rho / pq;
+        for (int64_t i = 0; i < n; ++i) {
+            double t = alpha * p[i];
+            x[i] = x[i] + t;
+            double u = alpha * q[i];
+            r[i] = r[i] - u;
+        }
+        double rr = orc_dot(n, r, r);
+        if (!(rr == rr)) {
+            status = ORC_BREAKDOWN;
+            break;
+        }
+        if (sqrt(rr) <= tol * nb) {
+            double t = orc_true_rel_residual(n, row_ptr, col, val, b, x);
+            ++checks;
+            if (t <= tol) {
+                status = ORC_OK;
+                break;
+            }
+            if (checks >= 4)
+                break;
+        }
+        orc_bj_apply(max_bs, bp, n_blocks, inv, r, z);
+        double rho_new = orc_dot(n, r, z);
+        if (!(rho_new == rho_new)) {
+            status = ORC_BREAKDOWN;
+            break;
+        }
+        double beta = rho_new / rho;
+        for (int64_t i = 0; i < n; ++i) {
+            double t = beta * p[i];
+            p[i] = z[i] + t;
+        }
+        rho = rho_new;
+    }
+    *rel_res = orc_true_rel_residual(n, row_ptr, col, val, b, x);
+    free(r);
+    free(p);
+    free(q);
+    free(z);
+    free(inv);
+    free(bp);
+    return status;
+}
+
 /* BiCGSTAB (van der Vorst, "Bi-CGSTAB: a fast and smoothly converging
  * variant of Bi-CG for the solution of nonsymmetric linear systems", SISC
  * 13, 1992) for general square A, shadow residual r^ = r0:

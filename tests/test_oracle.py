@@ -428,6 +428,192 @@ def test_pcg_jacobi_special_cases(orc):
     assert st == orc.BREAKDOWN and it == 0
 
 
+def _csr_rows(n, rows):
+    """CSR dict from a list of (column list, value list) per row."""
+    L = [len(c) for c, _ in rows]
+    return dict(n_rows=n, n_cols=n, row_ptr=np.concatenate([[0], np.cumsum(L)]).astype(np.int32),
+                col_idx=np.array([c for cs, _ in rows for c in cs], dtype=np.int32),
+                val=np.array([v for _, vs in rows for v in vs], dtype=np.float64))
+
+
+def _laplace1d(n):
+    rows = []
+    for i in range(n):
+        cs = [j for j in (i - 1, i, i + 1) if 0 <= j < n]
+        rows.append((cs, [2.0 if j == i else -1.0 for j in cs]))
+    return _csr_rows(n, rows)
+
+
+@pytest.mark.parametrize("max_bs,want", [(4, [0, 4, 8, 10]), (32, [0, 10]), (1, list(range(11))),
+                                         (3, [0, 3, 4, 7, 10]), (5, [0, 4, 9, 10])])
+def test_bj_blocks_by_hand(orc, max_bs, want):
+    """Rows 0-2 share one column list, row 3 has its own, rows 4-9 share a
+    third: supervariables of 3, 1 and 6 rows.  The expected boundaries are
+    worked out by hand from the two steps (cut at max_bs, merge greedily)."""
+    rows = [([0, 1, 2], [4.0, 1.0, 1.0])] * 3 + [([3], [2.0])] + [(list(range(4, 10)), [1.0] * 6)] * 6
+    A = _csr_rows(10, rows)
+    assert orc.bj_blocks(A, max_bs).tolist() == want
+
+
+def test_bj_blocks_distinct_rows_and_empty_runs(orc):
+    """Every row of the 1-D Laplacian has its own column list: blocks of
+    max_bs rows and a short tail.  A run of empty rows is one supervariable
+    (identical, empty lists)."""
+    A = _laplace1d(70)
+    assert orc.bj_blocks(A, 8).tolist() == list(range(0, 70, 8)) + [70]
+    assert orc.bj_blocks(A, 32).tolist() == [0, 32, 64, 70]
+    E = _csr_rows(9, [([0], [1.0]), ([1], [1.0])] + [([], [])] * 5 + [([7], [1.0]), ([8], [1.0])])
+    # pieces 1, 1 | 4 empty rows (the run cut at 4) | the fifth empty row, 1, 1 merged
+    assert orc.bj_blocks(E, 4).tolist() == [0, 2, 6, 9]
+    assert orc.bj_blocks(_csr_rows(0, []), 8).tolist() == [0]
+    with pytest.raises(ValueError):
+        orc.bj_blocks(A, 33)
+
+
+@pytest.mark.parametrize("max_bs", [8, 5, 32])
+def test_bj_invert_tridiagonal_closed_form(orc, max_bs):
+    """The diagonal blocks of the 1-D Laplacian are tridiag(-1, 2, -1) of
+    order s, whose inverse is min(i, j) (s + 1 - max(i, j)) / (s + 1) with
+    1-based i, j."""
+    n = 70
+    A = _laplace1d(n)
+    bp = orc.bj_blocks(A, max_bs)
+    st, inv = orc.bj_invert(A, bp, max_bs)
+    assert st == orc.OK
+    for o, e in zip(bp[:-1], bp[1:]):
+        s = e - o
+        for i in range(s):
+            for j in range(s):
+                want = min(i + 1, j + 1) * (s + 1 - max(i + 1, j + 1)) / (s + 1)
+                assert abs(inv[o * max_bs + j * s + i] - want) <= 1e-13 * s, (o, s, i, j)
+
+
+def test_bj_invert_layout_lower_triangular(orc):
+    """A = I + a S (S the subdiagonal): every diagonal block of 4 rows is
+    unit lower bidiagonal, with inverse (-a)^(i-j) for i >= j and 0 above
+    the diagonal; the stored layout (column j, row i at j * s + i) puts the
+    nonzeros below the diagonal, so a transposed store fails."""
+    a = 0.75
+    n = 12
+    rows = [([0], [1.0])] + [([i - 1, i], [a, 1.0]) for i in range(1, n)]
+    A = _csr_rows(n, rows)
+    bp = orc.bj_blocks(A, 4)
+    assert bp.tolist() == [0, 4, 8, 12]
+    st, inv = orc.bj_invert(A, bp, 4)
+    assert st == orc.OK
+    for o in (0, 4, 8):
+        for i in range(4):
+            for j in range(4):
+                want = (-a) ** (i - j) if i >= j else 0.0
+                assert abs(inv[o * 4 + j * 4 + i] - want) <= 1e-15
+
+
+@pytest.mark.parametrize("max_bs", [3, 8, 32])
+def test_bj_invert_and_apply_match_numpy(orc, max_bs):
+    """Non-symmetric diagonally dominant matrix: each stored inverse equals
+    numpy's inverse of the block the test extracts from the dense matrix,
+    and z = M^-1 r equals numpy's block solves."""
+    A = syn.random_csr(300, 300, 12, seed=31)
+    n = 300
+    D = dense(A)
+    D[np.arange(n), np.arange(n)] += 20.0
+    keep = D != 0
+    r_i, c_i = np.nonzero(keep)
+    B = dict(n_rows=n, n_cols=n, row_ptr=np.concatenate([[0], np.cumsum(keep.sum(1))]).astype(np.int32),
+             col_idx=c_i.astype(np.int32), val=D[r_i, c_i])
+    bp = orc.bj_blocks(B, max_bs)
+    st, inv = orc.bj_invert(B, bp, max_bs)
+    assert st == orc.OK
+    r = syn.vector(n, 32)
+    z = orc.bj_apply(bp, max_bs, inv, r)
+    for o, e in zip(bp[:-1], bp[1:]):
+        s = e - o
+        Bk = D[o:e, o:e]
+        got = inv[o * max_bs:o * max_bs + s * s].reshape(s, s).T  # column-major
+        assert np.allclose(got, np.linalg.inv(Bk), rtol=0, atol=1e-14)
+        assert np.allclose(z[o:e], np.linalg.solve(Bk, r[o:e]), rtol=0, atol=1e-13)
+
+
+def test_bj_singular_block_is_breakdown(orc):
+    A = _laplace1d(16)
+    Z = dict(A)
+    Z["val"] = A["val"].copy()
+    Z["val"][A["row_ptr"][5]:A["row_ptr"][6]] = 0.0  # row 5 zero: its block is singular
+    st, _ = orc.bj_invert(Z, orc.bj_blocks(Z, 4), 4)
+    assert st == orc.BREAKDOWN
+    b = syn.vector(16, 3)
+    x, st, it, res = orc.pcg_block_jacobi(Z, b, 4)
+    assert st == orc.BREAKDOWN and it == 0
+
+
+def _spd_block_diagonal(n, b, seed):
+    """Block-diagonal SPD matrix: each dense b x b block R R^T + b I."""
+    A = syn.block_diagonal(n, b, seed=seed)
+    D = dense(A)
+    S = np.zeros_like(D)
+    for o in range(0, n, b):
+        R = D[o:o + b, o:o + b]
+        S[o:o + b, o:o + b] = R @ R.T + b * np.eye(b)
+    r_i, c_i = np.nonzero(S)
+    return dict(n_rows=n, n_cols=n, row_ptr=np.concatenate([[0], np.cumsum((S != 0).sum(1))]).astype(np.int32),
+                col_idx=c_i.astype(np.int32), val=S[r_i, c_i])
+
+
+def test_pcg_block_jacobi_exact_preconditioner_one_step(orc):
+    """Rows of one dense 8 x 8 block share a column list, so with
+    max_bs = 8 the blocks are A's own blocks, M = A, and one step gives
+    alpha = 1 and the exact solution."""
+    A = _spd_block_diagonal(64, 8, seed=33)
+    assert orc.bj_blocks(A, 8).tolist() == list(range(0, 65, 8))
+    xt = syn.vector(64, 34)
+    b = dense(A) @ xt
+    x, st, it, res = orc.pcg_block_jacobi(A, b, 8, tol=1e-13)
+    assert st == orc.OK and it == 1
+    assert np.linalg.norm(x - xt) <= 1e-13 * np.linalg.norm(xt)
+
+
+def test_pcg_block_jacobi_size_one_is_jacobi(orc):
+    """Blocks of one row: M = diag(A), the iterates of Jacobi PCG."""
+    A = _scaled(syn.laplace2d(24), 10.0 ** (2.0 * syn.uniform01(35, 1, np.arange(576, dtype=np.uint64))))
+    b = orc.spmv_csr(A, syn.vector(576, 36))
+    for k in (1, 4, 20):
+        xa, _, _, _ = orc.pcg_jacobi(A, b, maxit=k)
+        xb, _, ib, _ = orc.pcg_block_jacobi(A, b, 1, maxit=k)
+        assert ib == k and np.linalg.norm(xa - xb) <= 1e-11 * np.linalg.norm(xa)
+    _, s0, i0, _ = orc.pcg_jacobi(A, b, tol=1e-10)
+    _, s1, i1, r1 = orc.pcg_block_jacobi(A, b, 1, tol=1e-10)
+    assert s0 == s1 == orc.OK and abs(i0 - i1) <= 1 and r1 <= 1e-10
+
+
+def test_pcg_block_jacobi_diffusion(orc):
+    """7-point diffusion: larger blocks (consecutive rows along x) take
+    fewer steps than point Jacobi, and the solve reaches the manufactured
+    solution with a confirmed true residual."""
+    A = syn.diffusion7(12, 1.0, seed=6)
+    n = A["n_rows"]
+    xt = syn.vector(n, 37)
+    b = orc.spmv_csr(A, xt)
+    _, s0, i0, _ = orc.pcg_jacobi(A, b, tol=1e-10)
+    x, st, it, res = orc.pcg_block_jacobi(A, b, 12, tol=1e-10)
+    assert s0 == st == orc.OK and res <= 1e-10 and it < i0
+    assert orc.true_rel_residual(A, b, x) <= 1e-10
+    assert np.linalg.norm(x - xt) <= 1e-7 * np.linalg.norm(xt)
+    xd = np.linalg.solve(dense(A), b)
+    assert np.linalg.norm(x - xd) <= 1e-7 * np.linalg.norm(xd)
+
+
+def test_pcg_block_jacobi_special_cases(orc):
+    A = _laplace1d(40)
+    x, st, it, res = orc.pcg_block_jacobi(A, np.zeros(40), 8, x0=np.ones(40))
+    assert st == orc.OK and it == 0 and np.all(x == 0)
+    b = orc.spmv_csr(A, syn.vector(40, 2))
+    x, st, it, res = orc.pcg_block_jacobi(A, b, 8, maxit=3)
+    assert st == orc.NOT_CONVERGED and it == 3
+    # one block holding the whole matrix: M = A, one step
+    x, st, it, res = orc.pcg_block_jacobi(_laplace1d(20), orc.spmv_csr(_laplace1d(20), np.ones(20)), 32)
+    assert st == orc.OK and it == 1 and np.allclose(x, 1.0, rtol=0, atol=1e-13)
+
+
 def test_bicgstab_scaled_identity_one_step(orc):
     """A = c I: v = c p, alpha = 1/c, s = 0 after the first half step, so
     x = b / c exactly (a closed form of one step)."""
