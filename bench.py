@@ -564,6 +564,20 @@ def run_extras(gko, torch, dev, st, selector=True, selector_matrices=200):
         err = float(torch.linalg.vector_norm(x - xt) / torch.linalg.vector_norm(xt))
         res[key] = {"s": round(t, 4), "iterations": info.iterations, "rel_residual": info.rel_residual,
                     "status": info.status, "rel_error_vs_x_true": err}
+    # block-Jacobi PCG: blocks of up to 8 / 32 consecutive rows (along x on
+    # this grid ordering); set-up (supervariables + inversions) timed apart
+    for bs in (8, 32):
+        for _ in range(2):
+            t_setup, P = _time_call(torch, lambda: gko.BlockJacobi(M, bs, stream=st))
+            x = torch.zeros_like(b)
+            t, info = _time_call(torch, lambda: M.pcg_block_jacobi(P, b, x, tol=1e-10, maxit=20000, fmt="ell",
+                                                                   stream=st))
+        err = float(torch.linalg.vector_norm(x - xt) / torch.linalg.vector_norm(xt))
+        res["fp64_block_jacobi%d_pcg_ell" % bs] = {
+            "s": round(t, 4), "setup_s": round(t_setup, 4), "iterations": info.iterations,
+            "rel_residual": info.rel_residual, "status": info.status, "rel_error_vs_x_true": err,
+            "us_per_iteration": round(t / max(info.iterations, 1) * 1e6, 1)}
+        P.close()
     # mixed: inner tolerances chosen by measurement (FP32 1e-2, BF16 1e-1),
     # without and with the Jacobi-preconditioned inner solve
     for key, prec, itol, pc in (("fp32", "fp32", 1e-2, "none"), ("bf16", "bf16", 1e-1, "none"),

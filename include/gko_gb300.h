@@ -327,6 +327,52 @@ int gko_cg_single_reduction(const gko_matrix* A, int fmt, const double* b, doubl
 int gko_pcg_jacobi(const gko_matrix* A, int fmt, const double* b, double* x, double tol, int maxit, void* stream,
                    gko_solve_info* info);
 
+/* ------------------------------------------ block-Jacobi preconditioner
+ * M = blockdiag(A_11, ..., A_kk): the diagonal blocks of A on runs of
+ * consecutive rows, each inverted once in FP64, applied as z = M^-1 r.  A
+ * companion of the Krylov solvers of Sec. 6.2 (which the paper benchmarks
+ * without defining a preconditioner): the textbook block-Jacobi of Saad,
+ * Iterative Methods for Sparse Linear Systems, Sec. 10.2.  Blocks:
+ * supervariables (maximal runs of consecutive rows whose stored column
+ * lists are identical) are cut into pieces of at most max_block_size rows,
+ * then merged greedily in row order while a block stays at most
+ * max_block_size rows.  An opaque, device-resident object. */
+typedef struct gko_block_jacobi gko_block_jacobi;
+
+/* Builds M for A (square, CSR part materialised) with blocks of 1..32
+ * rows.  The supervariable flags and the inversions (Gauss-Jordan with
+ * partial pivoting, one warp per block, duplicates in A summed) run on the
+ * device; the greedy merge scans the flags on the host (one copy of n_rows
+ * bytes).  Device memory: n_rows * (8 * max_block_size + 4) bytes plus the
+ * block boundaries.  Synchronises the stream.  Errors: GKO_ERR_INVALID_ARG
+ * (NULL, max_block_size outside 1..32, wrong device), GKO_ERR_DIM_MISMATCH
+ * (not square), GKO_ERR_FORMAT_UNAVAILABLE (no CSR part), GKO_ERR_BREAKDOWN
+ * (a diagonal block is singular: a zero pivot), GKO_ERR_OUT_OF_MEMORY.  On
+ * error *out is NULL.  M does not reference A after it is built. */
+int gko_block_jacobi_create(const gko_matrix* A, int max_block_size, void* stream, gko_block_jacobi** out);
+int gko_block_jacobi_destroy(gko_block_jacobi* M);
+
+/* Copies M to host buffers: *n_blocks; block_ptr (n_blocks + 1 row
+ * offsets, or NULL); inv (n_rows * max_block_size doubles, or NULL): entry
+ * (i, j) of the inverse of the block that starts at row o and has s rows
+ * at inv[o * max_block_size + j * s + i] (column-major within the block;
+ * the slots past each block's s * s entries are zero).  Synchronises. */
+int gko_block_jacobi_export(const gko_block_jacobi* M, int64_t* n_blocks, int32_t* block_ptr, double* inv,
+                            void* stream);
+
+/* z = M^-1 r (device vectors of n_rows doubles, not overlapping).
+ * Asynchronous on the stream. */
+int gko_block_jacobi_apply(const gko_block_jacobi* M, const double* r, double* z, void* stream);
+
+/* Conjugate gradients preconditioned by M (built from the same A): the
+ * preconditioned CG of gko_pcg_jacobi with z = M^-1 r stored, five launches
+ * per step (product; p.q; x += alpha p, r -= alpha q with ||r||^2 and the
+ * stop tests; z = M^-1 r with rho' = r.z; p = z + beta p).  Stopping,
+ * breakdown, errors and synchronisation as gko_pcg_jacobi; M must have as
+ * many rows as A (GKO_ERR_DIM_MISMATCH) and live on the same device. */
+int gko_pcg_block_jacobi(const gko_matrix* A, int fmt, const gko_block_jacobi* M, const double* b, double* x,
+                         double tol, int maxit, void* stream, gko_solve_info* info);
+
 /* BiCGSTAB (van der Vorst, SIAM J. Sci. Stat. Comput. 13, 1992) on A x = b
  * for a general (nonsymmetric) square A, a Krylov solver of Sec. 6.2 for
  * systems CG does not cover.  Shadow residual r^ = r0; per step

@@ -169,6 +169,11 @@ class Matrix:
         return binding.gko_pcg_jacobi(self.handle, _fmt(fmt), _dev_f64(b, self.n_rows, "b"),
                                       _dev_f64(x, self.n_rows, "x"), tol, maxit, _stream(stream))
 
+    def pcg_block_jacobi(self, M, b, x, tol=1e-10, maxit=10000, fmt="csr", stream=None):
+        """CG preconditioned by M, a BlockJacobi built from this matrix."""
+        return binding.gko_pcg_block_jacobi(self.handle, _fmt(fmt), M.handle, _dev_f64(b, self.n_rows, "b"),
+                                            _dev_f64(x, self.n_rows, "x"), tol, maxit, _stream(stream))
+
     def bicgstab(self, b, x, tol=1e-10, maxit=10000, fmt="csr", stream=None):
         return binding.gko_bicgstab(self.handle, _fmt(fmt), _dev_f64(b, self.n_rows, "b"),
                                     _dev_f64(x, self.n_rows, "x"), tol, maxit, _stream(stream))
@@ -205,6 +210,40 @@ class Matrix:
         candidates this handle can run (times in the order of
         binding.N_CANDIDATES; NaN: not applicable)."""
         return binding.gko_autotune_format(self.handle, _stream(stream))
+
+
+class BlockJacobi:
+    """Owning wrapper of a gko_block_jacobi preconditioner built from a Matrix."""
+
+    def __init__(self, A, max_block_size=8, stream=None):
+        self.n_rows = A.n_rows
+        self.max_block_size = int(max_block_size)
+        self.handle = None
+        self.handle = binding.gko_block_jacobi_create(A.handle, self.max_block_size, _stream(stream))
+
+    def close(self):
+        if self.handle:
+            binding.gko_block_jacobi_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def export(self, stream=None):
+        """(block_ptr int32 [n_blocks + 1], inv float64 [n_rows * max_block_size]) on the host."""
+        nb = binding.gko_block_jacobi_export(self.handle, None, None, _stream(stream))
+        bp = np.zeros(nb + 1, dtype=np.int32)
+        inv = np.zeros(self.n_rows * self.max_block_size, dtype=np.float64)
+        binding.gko_block_jacobi_export(self.handle, bp.ctypes.data, inv.ctypes.data if inv.size else None,
+                                        _stream(stream))
+        return bp, inv
+
+    def apply(self, r, z, stream=None):
+        binding.gko_block_jacobi_apply(self.handle, _dev_f64(r, self.n_rows, "r"), _dev_f64(z, self.n_rows, "z"),
+                                       _stream(stream))
 
 
 class Batch:

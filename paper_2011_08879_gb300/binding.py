@@ -65,6 +65,11 @@ _SIGS = {
     "gko_cg_single_reduction": (_INT, [_P, _INT, _P, _P, _D, _INT, _P, C.POINTER(SolveInfo)]),
     "gko_pcg_jacobi": (_INT, [_P, _INT, _P, _P, _D, _INT, _P, C.POINTER(SolveInfo)]),
     "gko_bicgstab": (_INT, [_P, _INT, _P, _P, _D, _INT, _P, C.POINTER(SolveInfo)]),
+    "gko_block_jacobi_create": (_INT, [_P, _INT, _P, C.POINTER(_P)]),
+    "gko_block_jacobi_destroy": (_INT, [_P]),
+    "gko_block_jacobi_export": (_INT, [_P, C.POINTER(_I64), _P, _P, _P]),
+    "gko_block_jacobi_apply": (_INT, [_P, _P, _P, _P]),
+    "gko_pcg_block_jacobi": (_INT, [_P, _INT, _P, _P, _P, _D, _INT, _P, C.POINTER(SolveInfo)]),
     "gko_spmm": (_INT, [_P, _I64, _P, _I64, _P, _I64, _D, _D, _P]),
     "gko_gmres": (_INT, [_P, _INT, _P, _P, _D, _INT, _INT, _P, C.POINTER(SolveInfo)]),
     "gko_cg_mixed_precond": (_INT, [_P, _INT, _INT, _P, _P, _D, _INT, _D, _INT, _P, C.POINTER(SolveInfo)]),
@@ -219,6 +224,37 @@ def gko_pcg_jacobi(A, fmt, b, x, tol, maxit, stream=0, raise_on=()) -> SolveInfo
     s = lib.gko_pcg_jacobi(A, fmt, b, x, tol, maxit, stream, C.byref(info))
     allow = tuple(c for c in (ERR_NOT_CONVERGED, ERR_BREAKDOWN) if c not in raise_on)
     _check(s, "gko_pcg_jacobi", allow)
+    info.status = s
+    return info
+
+
+def gko_block_jacobi_create(A, max_block_size, stream=0) -> int:
+    out = _P()
+    _check(lib.gko_block_jacobi_create(A, max_block_size, stream, C.byref(out)), "gko_block_jacobi_create")
+    return out.value
+
+
+def gko_block_jacobi_destroy(M) -> None:
+    _check(lib.gko_block_jacobi_destroy(M), "gko_block_jacobi_destroy")
+
+
+def gko_block_jacobi_export(M, block_ptr=None, inv=None, stream=0) -> int:
+    """Returns n_blocks; fills the host buffers block_ptr / inv when given."""
+    nb = _I64(0)
+    _check(lib.gko_block_jacobi_export(M, C.byref(nb), block_ptr, inv, stream), "gko_block_jacobi_export")
+    return nb.value
+
+
+def gko_block_jacobi_apply(M, r, z, stream=0) -> None:
+    _check(lib.gko_block_jacobi_apply(M, r, z, stream), "gko_block_jacobi_apply")
+
+
+def gko_pcg_block_jacobi(A, fmt, M, b, x, tol, maxit, stream=0, raise_on=()) -> SolveInfo:
+    """As gko_pcg_jacobi, preconditioned by the block-Jacobi object M."""
+    info = SolveInfo()
+    s = lib.gko_pcg_block_jacobi(A, fmt, M, b, x, tol, maxit, stream, C.byref(info))
+    allow = tuple(c for c in (ERR_NOT_CONVERGED, ERR_BREAKDOWN) if c not in raise_on)
+    _check(s, "gko_pcg_block_jacobi", allow)
     info.status = s
     return info
 

@@ -222,6 +222,53 @@ __global__ void __launch_bounds__(kRedThreads)
     });
 }
 
+// Block-Jacobi PCG step, first half: x += alpha p; r -= alpha q; ||r||^2 and
+// the stop tests (rho' = r.M^-1 r and beta come from the z kernel that
+// follows, which needs the whole updated r)
+__global__ void __launch_bounds__(kRedThreads)
+    xr_update_kernel(int64_t n, double* __restrict__ x, double* __restrict__ r, const double* __restrict__ p,
+                     const double* __restrict__ q, SolverState* s, double* part, cudaGraphConditionalHandle h)
+{
+    if (s->done) return;
+    const double alpha = s->alpha;
+    double acc = 0.0;
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(kRedThreads) + threadIdx.x; i < n;
+         i += static_cast<int64_t>(gridDim.x) * kRedThreads) {
+        x[i] = fma(alpha, p[i], x[i]);
+        const double ri = fma(-alpha, q[i], r[i]);
+        r[i] = ri;
+        acc = fma(ri, ri, acc);
+    }
+    grid_sum(acc, part, &s->ticket, [&](double rr) {
+        if (!(rr == rr)) {
+            s->status = GKO_ERR_BREAKDOWN;
+            stop_loop(s, h);
+            return;
+        }
+        s->dot_out = rr;
+        if (sqrt(rr) <= s->tol * s->stop_ref) {
+            s->conv = 1;
+            s->status = GKO_OK;
+            stop_loop(s, h);
+        } else if (s->iter >= s->maxit) {
+            s->status = GKO_ERR_NOT_CONVERGED;
+            stop_loop(s, h);
+        }
+    });
+}
+
+// p = z + beta p (initial: p = z)
+__global__ void __launch_bounds__(kRedThreads)
+    zupdate_kernel(int64_t n, double* __restrict__ p, const double* __restrict__ z, const SolverState* s, int force,
+                   int initial)
+{
+    if (s->done && !force) return;
+    const double beta = initial ? 0.0 : s->beta;
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(kRedThreads) + threadIdx.x; i < n;
+         i += static_cast<int64_t>(gridDim.x) * kRedThreads)
+        p[i] = initial ? z[i] : fma(beta, p[i], z[i]);
+}
+
 static int red_grid(int64_t n)
 {
     return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(kRedBlocks, (n + kRedThreads - 1) / kRedThreads)));
@@ -494,9 +541,10 @@ static void fill_info(gko_solve_info* info, int iters, int outer, double res, in
 // -------------------------------------------------------------- FP64 CG
 
 // Hestenes-Stiefel CG; jacobi: preconditioned by the diagonal of A (the
-// matrix's CSR part supplies the diagonal).
+// matrix's CSR part supplies the diagonal); bj: preconditioned by a
+// block-Jacobi M (z = M^-1 r stored, two more launches per step).
 static int cg_solve_impl(const gko_matrix* A, int fmt, const double* b, double* x, double tol, int maxit,
-                         cudaStream_t st, gko_solve_info* info, bool jacobi)
+                         cudaStream_t st, gko_solve_info* info, bool jacobi, const gko_block_jacobi* bj = nullptr)
 {
     const int64_t n = A->n_rows;
     if (n == 0) {
@@ -504,7 +552,7 @@ static int cg_solve_impl(const gko_matrix* A, int fmt, const double* b, double* 
         return GKO_OK;
     }
     Workspace ws(st);
-    double *r, *p, *q, *part, *dinv = nullptr;
+    double *r, *p, *q, *part, *dinv = nullptr, *z = nullptr;
     SolverState* ds;
     GKO_TRY(ws.get(&r, n));
     GKO_TRY(ws.get(&p, n));
@@ -512,6 +560,7 @@ static int cg_solve_impl(const gko_matrix* A, int fmt, const double* b, double* 
     GKO_TRY(ws.get(&part, 2 * kRedBlocks));
     GKO_TRY(ws.get(&ds, 1));
     const int grid = red_grid(n);
+    if (bj) GKO_TRY(ws.get(&z, n));
     if (jacobi) {
         int32_t* bad;
         GKO_TRY(ws.get(&dinv, n));
@@ -548,7 +597,10 @@ static int cg_solve_impl(const gko_matrix* A, int fmt, const double* b, double* 
     hs.maxit = maxit;
     hs.status = GKO_ERR_NOT_CONVERGED;
     GKO_TRY(write_state(ds, &hs, st));
-    if (jacobi) {
+    if (bj) {
+        bj_z_launch(bj, r, z, ds, part, grid, 0, kBjInit, 1, st);
+        zupdate_kernel<<<grid, kRedThreads, 0, st>>>(n, p, z, ds, 1, 1);
+    } else if (jacobi) {
         pcg_pupdate_kernel<<<grid, kRedThreads, 0, st>>>(n, p, r, dinv, ds, 1, 1);
         pcg_init_dots_kernel<<<grid, kRedThreads, 0, st>>>(n, r, dinv, ds, part);
     } else {
@@ -573,7 +625,11 @@ static int cg_solve_impl(const gko_matrix* A, int fmt, const double* b, double* 
     GKO_TRY(build_while_graph(&gh, [&](cudaGraphConditionalHandle h, cudaStream_t cs) -> int {
         GKO_TRY(spmv_fmt(A, fmt, p, q, 1.0, 0.0, cs));
         dot_kernel<double, kDotPQ><<<grid, kRedThreads, 0, cs>>>(n, p, q, ds, part, h, A->d_err);
-        if (jacobi) {
+        if (bj) {
+            xr_update_kernel<<<grid, kRedThreads, 0, cs>>>(n, x, r, p, q, ds, part, h);
+            bj_z_launch(bj, r, z, ds, part, grid, h, kBjStep, 0, cs);
+            zupdate_kernel<<<grid, kRedThreads, 0, cs>>>(n, p, z, ds, 0, 0);
+        } else if (jacobi) {
             pcg_update_kernel<<<grid, kRedThreads, 0, cs>>>(n, x, r, p, q, dinv, ds, part, h);
             pcg_pupdate_kernel<<<grid, kRedThreads, 0, cs>>>(n, p, r, dinv, ds, 0, 0);
         } else {
@@ -609,7 +665,10 @@ static int cg_solve_impl(const gko_matrix* A, int fmt, const double* b, double* 
             hs.done = 0;
             hs.status = GKO_ERR_NOT_CONVERGED;
             GKO_CUDA(cudaMemcpyAsync(ds, &hs, sizeof(SolverState), cudaMemcpyHostToDevice, st));
-            if (jacobi)
+            if (bj) {
+                bj_z_launch(bj, r, z, ds, part, grid, 0, kBjStep, 1, st);
+                zupdate_kernel<<<grid, kRedThreads, 0, st>>>(n, p, z, ds, 1, 0);
+            } else if (jacobi)
                 pcg_pupdate_kernel<<<grid, kRedThreads, 0, st>>>(n, p, r, dinv, ds, 1, 0);
             else
                 pupdate_kernel<double><<<grid, kRedThreads, 0, st>>>(n, p, r, ds, 1);
@@ -638,6 +697,12 @@ int pcg_jacobi_solve(const gko_matrix* A, int fmt, const double* b, double* x, d
                      cudaStream_t st, gko_solve_info* info)
 {
     return cg_solve_impl(A, fmt, b, x, tol, maxit, st, info, true);
+}
+
+int pcg_block_jacobi_solve(const gko_matrix* A, int fmt, const gko_block_jacobi* M, const double* b, double* x,
+                           double tol, int maxit, cudaStream_t st, gko_solve_info* info)
+{
+    return cg_solve_impl(A, fmt, b, x, tol, maxit, st, info, false, M);
 }
 
 // ------------------------------------------------ single-reduction CG

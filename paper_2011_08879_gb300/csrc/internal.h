@@ -178,7 +178,29 @@ struct gko_batch {
     double graph_tol = 0.0;
 };
 
+// Block-Jacobi preconditioner (block_jacobi.cu): boundaries of the diagonal
+// blocks, the block of every row, and the inverses (entry (i, j) of the
+// block starting at row o with s rows at inv[o * max_bs + j * s + i]).
+struct gko_block_jacobi {
+    int device = 0;
+    int64_t n_rows = 0, n_blocks = 0;
+    int max_bs = 1;
+    int32_t* block_ptr = nullptr;  // device, n_blocks + 1
+    int32_t* row_block = nullptr;  // device, n_rows
+    double* inv = nullptr;         // device, n_rows * max_bs
+};
+
 namespace gko {
+
+struct SolverState;
+
+// z = M^-1 r fused with rho' = r.z (block_jacobi.cu).  mode kBjInit: also
+// ||r||^2 and the initial stop test, rho = rho0 = r.z; kBjStep: beta = rho'/rho,
+// rho = rho'.  Skipped when the state says done, unless force.  h: the loop's
+// conditional handle (0 outside a graph).
+enum { kBjInit = 0, kBjStep = 1 };
+void bj_z_launch(const gko_block_jacobi* M, const double* r, double* z, SolverState* s, double* part, int grid,
+                 cudaGraphConditionalHandle h, int mode, int force, cudaStream_t st);
 
 // Launchers exported by the kernel translation units.  All asynchronous on
 // the given stream; they validate nothing (the C-ABI layer does).
@@ -244,6 +266,8 @@ cudaError_t lp_ell_cg1(const gko_matrix* A, bool bf16, const float* r, const flo
 int lp_ell_grid(const gko_matrix* A);
 int pcg_jacobi_solve(const gko_matrix* A, int fmt, const double* b, double* x, double tol, int maxit,
                      cudaStream_t st, gko_solve_info* info);
+int pcg_block_jacobi_solve(const gko_matrix* A, int fmt, const gko_block_jacobi* M, const double* b, double* x,
+                           double tol, int maxit, cudaStream_t st, gko_solve_info* info);
 int bicgstab_solve(const gko_matrix* A, int fmt, const double* b, double* x, double tol, int maxit,
                    cudaStream_t st, gko_solve_info* info);
 int spmm_csr(const gko_matrix* A, int64_t k, const double* x, int64_t ldx, double* y, int64_t ldy, double alpha,
