@@ -2,11 +2,11 @@
 // paper's Sec. 6.2 runs on SpMV, plus mixed-precision CG with FP64
 // iterative refinement.
 //
-// One CG step is four launches:
+// One CG step is four launches (three on ELL, whose product carries p.q):
 //   q = A p                                  (format kernel of choice)
 //   alpha = rho / (p.q)                      (dot with grid reduction)
-//   x += alpha p, r -= alpha q, rho' = r.r   (fused update + grid reduction)
-//   p = r + beta p                           (beta = rho'/rho)
+//   r -= alpha q, rho' = r.r                 (fused update + grid reduction)
+//   x += alpha p, p = r + beta p             (beta = rho'/rho)
 // Each dot is one grid-wide reduction: every block writes its partial, the
 // last block to finish (atomic ticket) sums the partials in index order, so
 // results do not depend on block scheduling.  Scalars stay on the device.
@@ -22,6 +22,7 @@
 
 #include "common.cuh"
 #include "internal.h"
+#include "ell.cuh"
 #include "segmented.cuh"
 #include "solver.cuh"
 
@@ -32,6 +33,55 @@ int launch_seg(int64_t n_rows, int64_t n_cols, int64_t nnz, const int32_t* row_p
                double alpha, double beta, uint32_t* err, bool coo, cudaStream_t st, bool accumulate, int coo_p);
 
 enum { kDotStore = 0, kDotRhoInit = 1, kDotPQ = 2 };
+
+// Scalar step after p.q: alpha = rho / p.q, iteration count, breakdown and
+// timeout tests; step_ok tells the x update of this step whether alpha
+// was formed.
+__device__ __forceinline__ void pq_step(SolverState* s, double tot, cudaGraphConditionalHandle h,
+                                        const uint32_t* err)
+{
+    s->step_ok = 0;
+    if (s->done || s->iter >= s->maxit) {
+        // already stopped (e.g. converged before the first step):
+        // clear the loop condition so the WHILE node always ends
+        stop_loop(s, h);
+        return;
+    }
+    s->pq = tot;
+    s->iter += 1;
+    // a product whose bulk copies did not land leaves q undefined and
+    // sets the timeout bit of the handle's error word
+    if (err && (*reinterpret_cast<const volatile uint32_t*>(err) & 1u)) {
+        s->status = GKO_ERR_TIMEOUT;
+        stop_loop(s, h);
+    } else if (!(tot > 0.0)) {
+        s->status = GKO_ERR_BREAKDOWN;
+        stop_loop(s, h);
+    } else {
+        s->alpha = s->rho / tot;
+        s->step_ok = 1;
+    }
+}
+
+// Scalar step after rho' = r.r: beta = rho'/rho, rho = rho', stop tests.
+__device__ __forceinline__ void rr_step(SolverState* s, double rho_new, cudaGraphConditionalHandle h)
+{
+    if (!(rho_new == rho_new)) {
+        s->status = GKO_ERR_BREAKDOWN;
+        stop_loop(s, h);
+        return;
+    }
+    s->beta = rho_new / s->rho;
+    s->rho = rho_new;
+    if (sqrt(rho_new) <= s->tol * s->stop_ref) {
+        s->conv = 1;
+        s->status = GKO_OK;
+        stop_loop(s, h);
+    } else if (s->iter >= s->maxit) {
+        s->status = GKO_ERR_NOT_CONVERGED;
+        stop_loop(s, h);
+    }
+}
 
 // dot(a, b) with per-thread accumulation in T, cross-thread in FP64
 template <typename T, int kMode>
@@ -56,60 +106,7 @@ __global__ void __launch_bounds__(kRedThreads)
                 s->done = 1;
             }
         } else {  // p.q -> alpha
-            if (s->done || s->iter >= s->maxit) {
-                // already stopped (e.g. converged before the first step):
-                // clear the loop condition so the WHILE node always ends
-                stop_loop(s, h);
-                return;
-            }
-            s->pq = tot;
-            s->iter += 1;
-            // a product whose bulk copies did not land leaves q undefined and
-            // sets the timeout bit of the handle's error word
-            if (err && (*reinterpret_cast<const volatile uint32_t*>(err) & 1u)) {
-                s->status = GKO_ERR_TIMEOUT;
-                stop_loop(s, h);
-            } else if (!(tot > 0.0)) {
-                s->status = GKO_ERR_BREAKDOWN;
-                stop_loop(s, h);
-            } else {
-                s->alpha = s->rho / tot;
-            }
-        }
-    });
-}
-
-// x += alpha p; r -= alpha q; rho' = r.r; beta = rho'/rho; stop tests
-template <typename T>
-__global__ void __launch_bounds__(kRedThreads)
-    update_kernel(int64_t n, T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p,
-                  const T* __restrict__ q, SolverState* s, double* part, cudaGraphConditionalHandle h)
-{
-    if (s->done) return;  // only the last block of the previous kernel can set it
-    const T alpha = static_cast<T>(s->alpha);
-    T acc = T(0);
-    for (int64_t i = blockIdx.x * static_cast<int64_t>(kRedThreads) + threadIdx.x; i < n;
-         i += static_cast<int64_t>(gridDim.x) * kRedThreads) {
-        x[i] = fma(alpha, p[i], x[i]);
-        const T ri = fma(-alpha, q[i], r[i]);
-        r[i] = ri;
-        acc = fma(ri, ri, acc);
-    }
-    grid_sum(static_cast<double>(acc), part, &s->ticket, [&](double rho_new) {
-        if (!(rho_new == rho_new)) {
-            s->status = GKO_ERR_BREAKDOWN;
-            stop_loop(s, h);
-            return;
-        }
-        s->beta = rho_new / s->rho;
-        s->rho = rho_new;
-        if (sqrt(rho_new) <= s->tol * s->stop_ref) {
-            s->conv = 1;
-            s->status = GKO_OK;
-            stop_loop(s, h);
-        } else if (s->iter >= s->maxit) {
-            s->status = GKO_ERR_NOT_CONVERGED;
-            stop_loop(s, h);
+            pq_step(s, tot, h, err);
         }
     });
 }
@@ -125,6 +122,106 @@ __global__ void __launch_bounds__(kRedThreads)
          i += static_cast<int64_t>(gridDim.x) * kRedThreads)
         p[i] = fma(beta, p[i], r[i]);
 }
+
+// --------------------------------- FP64 CG step with regrouped updates
+//
+// The plain FP64 step runs as
+//   q = A p and p.q -> alpha       (ELL: one kernel, the dot fused)
+//   r -= alpha q, rho' = r.r -> beta, stop tests
+//   x += alpha p, p = r + beta p   (one pass over x, p, r)
+// which moves two vector passes fewer than product, dot, (x, r) update and
+// p update as separate kernels.  When the solve stops at the r update, the
+// last kernel still applies x += alpha p (step_ok) but leaves p.
+
+// q = A p for ELL with p.q in the same pass (persistent grid; one grid
+// reduction, partials summed in block order)
+__global__ void __launch_bounds__(256)
+    ell_pq_kernel(int64_t n, int64_t n_pad, int64_t K, const int32_t* __restrict__ col,
+                  const double* __restrict__ val, const double* __restrict__ p, double* __restrict__ q,
+                  SolverState* s, double* part, cudaGraphConditionalHandle h)
+{
+    double acc = 0.0;
+    for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; 2 * t < n;
+         t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int64_t r = 2 * t;
+        double a0, a1;
+        ell_pair_sum(r, n_pad, K, col, val, p, a0, a1);
+        store_pair<false, false>(q, r, n, a0, a1, 1.0, 0.0);
+        acc = fma(p[r], a0, acc);
+        if (r + 1 < n) acc = fma(p[r + 1], a1, acc);
+    }
+    grid_sum(acc, part, &s->ticket, [&](double tot) { pq_step(s, tot, h, nullptr); });
+}
+
+// r -= alpha q; rho' = r.r; beta; stop tests (kVec: 128-bit accesses, the
+// vectors 16-byte aligned)
+template <bool kVec>
+__global__ void __launch_bounds__(kRedThreads)
+    r_update_kernel(int64_t n, double* __restrict__ r, const double* __restrict__ q, SolverState* s, double* part,
+                    cudaGraphConditionalHandle h)
+{
+    if (s->done) return;  // only the last block of the previous kernel can set it
+    const double alpha = s->alpha;
+    const int64_t tid = blockIdx.x * static_cast<int64_t>(kRedThreads) + threadIdx.x;
+    const int64_t nth = static_cast<int64_t>(gridDim.x) * kRedThreads;
+    double acc = 0.0;
+    int64_t i0 = 0;
+    if (kVec) {
+        const int64_t nv = n / 2;
+        for (int64_t i = tid; i < nv; i += nth) {
+            double2 rv = reinterpret_cast<const double2*>(r)[i];
+            const double2 qv = reinterpret_cast<const double2*>(q)[i];
+            rv.x = fma(-alpha, qv.x, rv.x);
+            rv.y = fma(-alpha, qv.y, rv.y);
+            reinterpret_cast<double2*>(r)[i] = rv;
+            acc = fma(rv.x, rv.x, acc);
+            acc = fma(rv.y, rv.y, acc);
+        }
+        i0 = 2 * nv;
+    }
+    for (int64_t i = i0 + tid; i < n; i += nth) {
+        const double ri = fma(-alpha, q[i], r[i]);
+        r[i] = ri;
+        acc = fma(ri, ri, acc);
+    }
+    grid_sum(acc, part, &s->ticket, [&](double rho_new) { rr_step(s, rho_new, h); });
+}
+
+// x += alpha p; then p = r + beta p unless the solve stopped at this step
+template <bool kVec>
+__global__ void __launch_bounds__(kRedThreads)
+    px_update_kernel(int64_t n, double* __restrict__ x, double* __restrict__ p, const double* __restrict__ r,
+                     const SolverState* s)
+{
+    if (!s->step_ok) return;
+    const double alpha = s->alpha, beta = s->beta;
+    const bool more = !s->done;
+    const int64_t tid = blockIdx.x * static_cast<int64_t>(kRedThreads) + threadIdx.x;
+    const int64_t nth = static_cast<int64_t>(gridDim.x) * kRedThreads;
+    int64_t i0 = 0;
+    if (kVec) {
+        const int64_t nv = n / 2;
+        for (int64_t i = tid; i < nv; i += nth) {
+            const double2 pv = reinterpret_cast<const double2*>(p)[i];
+            double2 xv = reinterpret_cast<const double2*>(x)[i];
+            xv.x = fma(alpha, pv.x, xv.x);
+            xv.y = fma(alpha, pv.y, xv.y);
+            reinterpret_cast<double2*>(x)[i] = xv;
+            if (more) {
+                const double2 rv = reinterpret_cast<const double2*>(r)[i];
+                reinterpret_cast<double2*>(p)[i] = make_double2(fma(beta, pv.x, rv.x), fma(beta, pv.y, rv.y));
+            }
+        }
+        i0 = 2 * nv;
+    }
+    for (int64_t i = i0 + tid; i < n; i += nth) {
+        const double pi = p[i];
+        x[i] = fma(alpha, pi, x[i]);
+        if (more) p[i] = fma(beta, pi, r[i]);
+    }
+}
+
+static bool aligned16(const void* a) { return (reinterpret_cast<uintptr_t>(a) & 15) == 0; }
 
 // ------------------------------------------------ Jacobi preconditioning
 
@@ -148,7 +245,7 @@ __global__ void diag_inv_kernel(int64_t n, const int32_t* __restrict__ row_ptr, 
 
 // Preconditioned CG step (z = D^-1 r is never stored):
 // x += alpha p; r -= alpha q; rr = r.r (stopping), rz = r.D^-1 r
-// (rho' for beta); stop tests on sqrt(rr) as in update_kernel
+// (rho' for beta); stop tests on sqrt(rr) as in r_update_kernel
 __global__ void __launch_bounds__(kRedThreads)
     pcg_update_kernel(int64_t n, double* __restrict__ x, double* __restrict__ r, const double* __restrict__ p,
                       const double* __restrict__ q, const double* __restrict__ dinv, SolverState* s, double* part,
@@ -621,10 +718,24 @@ static int cg_solve_impl(const gko_matrix* A, int fmt, const double* b, double* 
         return GKO_ERR_NOT_CONVERGED;
     }
 
+    // plain CG on ELL: the product carries p.q (persistent grid, its own partials)
+    const bool fused_pq = !bj && !jacobi && fmt == GKO_FMT_ELL && A->ell.K > 0;
+    int pq_grid = 0;
+    double* pq_part = part;
+    if (fused_pq) {
+        pq_grid = static_cast<int>(std::max<int64_t>(
+            1, std::min<int64_t>((n + 511) / 512, static_cast<int64_t>(device_sm_count()) * 5)));
+        if (pq_grid > 2 * kRedBlocks) GKO_TRY(ws.get(&pq_part, pq_grid));
+    }
     GraphHolder gh;
     GKO_TRY(build_while_graph(&gh, [&](cudaGraphConditionalHandle h, cudaStream_t cs) -> int {
-        GKO_TRY(spmv_fmt(A, fmt, p, q, 1.0, 0.0, cs));
-        dot_kernel<double, kDotPQ><<<grid, kRedThreads, 0, cs>>>(n, p, q, ds, part, h, A->d_err);
+        if (fused_pq) {
+            ell_pq_kernel<<<pq_grid, 256, 0, cs>>>(n, A->ell.n_pad, A->ell.K, A->ell.col, A->ell.val, p, q, ds,
+                                                   pq_part, h);
+        } else {
+            GKO_TRY(spmv_fmt(A, fmt, p, q, 1.0, 0.0, cs));
+            dot_kernel<double, kDotPQ><<<grid, kRedThreads, 0, cs>>>(n, p, q, ds, part, h, A->d_err);
+        }
         if (bj) {
             xr_update_kernel<<<grid, kRedThreads, 0, cs>>>(n, x, r, p, q, ds, part, h);
             bj_z_launch(bj, r, z, ds, part, grid, h, kBjStep, 0, cs);
@@ -633,8 +744,16 @@ static int cg_solve_impl(const gko_matrix* A, int fmt, const double* b, double* 
             pcg_update_kernel<<<grid, kRedThreads, 0, cs>>>(n, x, r, p, q, dinv, ds, part, h);
             pcg_pupdate_kernel<<<grid, kRedThreads, 0, cs>>>(n, p, r, dinv, ds, 0, 0);
         } else {
-            update_kernel<double><<<grid, kRedThreads, 0, cs>>>(n, x, r, p, q, ds, part, h);
-            pupdate_kernel<double><<<grid, kRedThreads, 0, cs>>>(n, p, r, ds, 0);
+            // 2 * kRedBlocks partials fit the wider grid of the vector kernels
+            const int vgrid = static_cast<int>(
+                std::max<int64_t>(1, std::min<int64_t>(2 * kRedBlocks, (n / 2 + kRedThreads - 1) / kRedThreads)));
+            if (aligned16(x)) {
+                r_update_kernel<true><<<vgrid, kRedThreads, 0, cs>>>(n, r, q, ds, part, h);
+                px_update_kernel<true><<<vgrid, kRedThreads, 0, cs>>>(n, x, p, r, ds);
+            } else {
+                r_update_kernel<false><<<grid, kRedThreads, 0, cs>>>(n, r, q, ds, part, h);
+                px_update_kernel<false><<<grid, kRedThreads, 0, cs>>>(n, x, p, r, ds);
+            }
         }
         GKO_CUDA(cudaGetLastError());
         return GKO_OK;

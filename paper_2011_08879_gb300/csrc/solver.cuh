@@ -25,6 +25,7 @@ struct SolverState {
     double dot_out;   // result of a plain dot
     int32_t iter, maxit, done, status, conv, rel_inner;
     int32_t skip_test;  // single-reduction CG: skip the next stop test once
+    int32_t step_ok;    // CG: this step's alpha was formed (x += alpha p is still due)
     uint32_t ticket;
 };
 

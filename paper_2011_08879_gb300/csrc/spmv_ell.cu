@@ -12,42 +12,13 @@
 #include "common.cuh"
 #include "internal.h"
 #include "segmented.cuh"
+#include "ell.cuh"
 
 namespace gko {
 
 int launch_seg(int64_t n_rows, int64_t n_cols, int64_t nnz, const int32_t* row_ptr, const int32_t* rows, const int32_t* col,
                const double* val, const int32_t* thr_row, const SegArrays& sa, const double* x, double* y,
                double alpha, double beta, uint32_t* err, bool coo, cudaStream_t st, bool accumulate, int coo_p);
-
-template <bool kAlpha, bool kBeta>
-__device__ __forceinline__ void store_pair(double* y, int64_t r, int64_t n, double a0, double a1, double alpha,
-                                           double beta)
-{
-    if (r + 1 < n) {
-        // y is caller-owned: vector access only when y + r is 16-byte aligned
-        const bool vec = (reinterpret_cast<uintptr_t>(y + r) & 15) == 0;
-        double2 o;
-        o.x = kAlpha ? alpha * a0 : a0;
-        o.y = kAlpha ? alpha * a1 : a1;
-        if (kBeta) {
-            double2 yo;
-            if (vec)
-                yo = *reinterpret_cast<const double2*>(y + r);
-            else
-                yo = make_double2(y[r], y[r + 1]);
-            o.x = fma(beta, yo.x, o.x);
-            o.y = fma(beta, yo.y, o.y);
-        }
-        if (vec)
-            *reinterpret_cast<double2*>(y + r) = o;
-        else {
-            y[r] = o.x;
-            y[r + 1] = o.y;
-        }
-    } else if (r < n) {
-        seg_store<kAlpha, kBeta>(y, r, a0, alpha, beta);
-    }
-}
 
 // Two rows per thread; slot k of rows (2p, 2p+1) at k*ld + 2p.
 template <bool kAlpha, bool kBeta>
@@ -59,31 +30,8 @@ __global__ void __launch_bounds__(256)
     const int64_t p = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
     const int64_t r = 2 * p;
     if (r >= n_rows) return;
-    double a0 = 0.0, a1 = 0.0;
-    const int2* c2 = reinterpret_cast<const int2*>(col + r);
-    const double2* v2 = reinterpret_cast<const double2*>(val + r);
-    const int64_t step = n_pad / 2;
-    int64_t k = 0;
-    for (; k + 4 <= K; k += 4) {
-        int2 c[4];
-        double2 v[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            c[u] = __ldcs(c2 + (k + u) * step);
-            v[u] = __ldcs(v2 + (k + u) * step);
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            if (c[u].x >= 0) a0 = fma(v[u].x, ldg(x + c[u].x), a0);
-            if (c[u].y >= 0) a1 = fma(v[u].y, ldg(x + c[u].y), a1);
-        }
-    }
-    for (; k < K; ++k) {
-        const int2 c = __ldcs(c2 + k * step);
-        const double2 v = __ldcs(v2 + k * step);
-        if (c.x >= 0) a0 = fma(v.x, ldg(x + c.x), a0);
-        if (c.y >= 0) a1 = fma(v.y, ldg(x + c.y), a1);
-    }
+    double a0, a1;
+    ell_pair_sum(r, n_pad, K, col, val, x, a0, a1);
     store_pair<kAlpha, kBeta>(y, r, n_rows, a0, a1, alpha, beta);
 }
 

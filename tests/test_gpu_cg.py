@@ -38,6 +38,31 @@ def test_cg_laplace_128(gko, dev, orc, fmt):
     assert e_g <= 10 * e_o + 1e-15
 
 
+@pytest.mark.parametrize("fmt", ["csr", "ell"])
+def test_cg_unaligned_solution_vector(gko, dev, orc, fmt):
+    """x 8 bytes off a 16-byte boundary takes the scalar update kernels; the
+    same solve from an aligned x takes the 128-bit ones: both match the
+    oracle (odd n, so the vector loops also leave a tail)."""
+    import torch
+    A = syn.diffusion7(17, 1.0, seed=6)
+    n = A["n_rows"]
+    assert n % 2 == 1
+    xt = syn.vector(n, 3)
+    b = orc.spmv_csr(A, xt)
+    x_o, _, it_o, _ = orc.cg(A, b, tol=1e-10)
+    M = gko.Matrix(A)
+    if fmt != "csr":
+        M.convert(fmt)
+    buf = torch.zeros(n + 1, dtype=torch.float64, device=dev)
+    for x in (buf[:n], buf[1:]):
+        x.zero_()
+        info = M.cg(_t(b, dev), x, tol=1e-10, fmt=fmt)
+        assert info.status == 0 and abs(info.iterations - it_o) <= max(5, 0.02 * it_o)
+        xg = x.cpu().numpy()
+        assert orc.true_rel_residual(A, b, xg) <= 1e-10
+        assert np.linalg.norm(xg - x_o) <= 1e-8 * np.linalg.norm(x_o)
+
+
 def _skewed_spd(n, seed):
     """SPD matrix with power-law row lengths: the symmetrised pattern of a
     power-law matrix, off-diagonals -|a|, diagonal 1 + sum of |off-diagonals|
