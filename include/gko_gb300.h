@@ -110,7 +110,7 @@ typedef struct {
     int32_t outer_iterations; /* mixed CG: refinement corrections; 0 otherwise */
     double rel_residual;      /* true ||b - A x||_2 / ||b||_2 formed in FP64 at exit */
     int32_t status;
-    int32_t reserved;
+    int32_t aux;              /* GMRES: Arnoldi steps whose second Gram-Schmidt update ran in FP32; 0 otherwise */
 } gko_solve_info;
 
 /* Message of the last failing call on this thread ("" if none). */
@@ -401,7 +401,11 @@ int gko_bicgstab(const gko_matrix* A, int fmt, const double* b, double* x, doubl
  * Arnoldi steps, rotations and back substitution run on the device (one
  * CUDA graph per cycle, one host synchronisation per cycle).  Products with
  * format fmt; the basis ((restart + 1) n doubles) is allocated
- * stream-ordered for the call.  maxit bounds the Arnoldi steps
+ * stream-ordered for the call, with a float copy of it: the second
+ * Gram-Schmidt update, whose coefficients are rounding-level corrections,
+ * runs in FP32 on that copy when they are at most 2^-33 of ||w1|| (its
+ * error then stays below the FP64 rounding of w1), else in FP64;
+ * info->aux counts the steps that took FP32.  maxit bounds the Arnoldi steps
  * (info->iterations counts them): GKO_ERR_NOT_CONVERGED; a NaN or a zero
  * rotation before convergence: GKO_ERR_BREAKDOWN.  ||b|| = 0 returns x = 0.
  * Synchronises the stream. */

@@ -38,7 +38,7 @@ class GkoError(RuntimeError):
 
 class SolveInfo(C.Structure):
     _fields_ = [("iterations", C.c_int32), ("outer_iterations", C.c_int32), ("rel_residual", C.c_double),
-                ("status", C.c_int32), ("reserved", C.c_int32)]
+                ("status", C.c_int32), ("aux", C.c_int32)]
 
 
 _P, _I64, _I32, _D, _F, _INT, _U32P = C.c_void_p, C.c_int64, C.c_int32, C.c_double, C.c_float, C.c_int, C.c_void_p

@@ -580,7 +580,7 @@ int gko_cg_batched(gko_batch* B, const double* b, double* x, double tol, int max
             infos[s].outer_iterations = 0;
             infos[s].rel_residual = res[s];
             infos[s].status = stv[s];
-            infos[s].reserved = 0;
+            infos[s].aux = 0;
         }
     }
     if (worst != GKO_OK) set_error("batched CG: some systems did not converge");

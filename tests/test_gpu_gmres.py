@@ -43,6 +43,45 @@ def test_gmres_convection_diffusion(gko, dev, orc, fmt, restart):
     assert np.linalg.norm(x7.cpu().numpy() - xo7) <= 1e-10 * np.linalg.norm(xo7)
 
 
+def _near_identity(n, eps, seed):
+    """I + eps R, R a random sparse matrix with entries in [-1, 1)."""
+    R = syn.random_csr(n, n, 6, seed=seed)
+    rows = np.repeat(np.arange(n), np.diff(R["row_ptr"]))
+    D = np.zeros((n, n))
+    D[rows, R["col_idx"]] = eps * R["val"]
+    D[np.arange(n), np.arange(n)] += 1.0
+    r, c = np.nonzero(D)
+    return dict(n_rows=n, n_cols=n, row_ptr=np.concatenate([[0], np.cumsum((D != 0).sum(1))]).astype(np.int32),
+                col_idx=c.astype(np.int32), val=D[r, c])
+
+
+def test_gmres_second_pass_precision_paths(gko, dev, orc):
+    """The second Gram-Schmidt update runs in FP32 when its coefficients are
+    rounding-level against ||w1|| (convection-diffusion: nearly every step)
+    and in FP64 when the first pass cancels most of w (A = I + 1e-8 R:
+    w = A v_j lies within ~1e-8 of the basis, so the second-pass
+    coefficients reach ~1e-16 / 1e-8 of ||w1||, above the 2^-33 bound).
+    Both paths match the oracle's FP64 CGS2."""
+    A = syn.convdiff2d(64, 0.8)
+    n = A["n_rows"]
+    b = orc.spmv_csr(A, syn.vector(n, 38))
+    M = gko.Matrix(A)
+    x = _t(np.zeros(n), dev)
+    info = M.gmres(_t(b, dev), x, tol=1e-10, restart=30)
+    assert info.status == 0 and info.aux >= 0.9 * info.iterations, (info.aux, info.iterations)
+    B = _near_identity(3000, 1e-8, seed=39)
+    xt = syn.vector(3000, 40)
+    bb = orc.spmv_csr(B, xt)
+    x_o, st_o, it_o, _ = orc.gmres(B, bb, tol=1e-13, restart=30)
+    MB = gko.Matrix(B)
+    x = _t(np.zeros(3000), dev)
+    info = MB.gmres(_t(bb, dev), x, tol=1e-13, restart=30)
+    assert st_o == 0 and info.status == 0 and abs(info.iterations - it_o) <= 1
+    assert info.aux < info.iterations, (info.aux, info.iterations)  # FP64 updates taken
+    assert np.linalg.norm(x.cpu().numpy() - x_o) <= 1e-12 * np.linalg.norm(x_o)
+    assert orc.true_rel_residual(B, bb, x.cpu().numpy()) <= 1e-13
+
+
 def test_gmres_three_eigenvalues_and_special_cases(gko, dev, orc):
     blocks = [((1.0, 0.7), (0.0, 2.0)), ((2.0, 0.3), (0.0, 3.0)), ((3.0, -0.5), (0.0, 1.0))]
     nb = 3000
