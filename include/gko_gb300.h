@@ -445,7 +445,11 @@ int gko_cg_mixed_precond(gko_matrix* A, int inner_dtype, int precond, const doub
  * are [row_off[s], row_off[s+1]) of one concatenated CSR (global row_ptr of
  * row_off[count]+1 entries, column indices local to the system).  Host or
  * device inputs as for gko_matrix_create_csr; copied.  Systems may have
- * 1..4096 rows. */
+ * 1..4096 rows; row_ptr must be non-decreasing and every column index lie in
+ * 0..n_s - 1 of its system (GKO_ERR_INVALID_MATRIX otherwise).  Each system
+ * is stored renumbered, its rows in order of decreasing length (so that a
+ * warp's rows have like lengths); b and x of the solves stay in the
+ * caller's order. */
 int gko_batch_create(int64_t count, const int64_t* row_off, const int32_t* row_ptr,
                      const int32_t* col, const double* val, int on_device, void* stream,
                      gko_batch** out);

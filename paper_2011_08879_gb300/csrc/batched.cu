@@ -51,9 +51,10 @@ template <int BS>
 __global__ void __launch_bounds__(BS)
     batched_cg_kernel(int64_t count, const int64_t* __restrict__ row_off, const int32_t* __restrict__ row_ptr,
                       const int32_t* __restrict__ col_all, const double* __restrict__ val_all,
-                      const int32_t* __restrict__ order, int32_t* queue, const double* __restrict__ b_all,
-                      double* __restrict__ x_all, double tol, int maxit, double* __restrict__ res_out,
-                      int32_t* __restrict__ it_out, int32_t* __restrict__ st_out, int max_rows)
+                      const int32_t* __restrict__ order, const int32_t* __restrict__ perm, int32_t* queue,
+                      const double* __restrict__ b_all, double* __restrict__ x_all, double tol, int maxit,
+                      double* __restrict__ res_out, int32_t* __restrict__ it_out, int32_t* __restrict__ st_out,
+                      int max_rows)
 {
     extern __shared__ __align__(16) double sm[];
     double* xs = sm;
@@ -78,16 +79,18 @@ __global__ void __launch_bounds__(BS)
         const double* val = val_all + base;
         const double* b = b_all + r0;
         double* x = x_all + r0;
+        const int32_t* pm = perm + r0;  // b and x are indexed in the caller's row order
 
         double bb = 0.0;
         for (int i = threadIdx.x; i < n; i += BS) {
-            xs[i] = x[i];
-            bb = fma(b[i], b[i], bb);
+            xs[i] = x[pm[i]];
+            const double bi = b[pm[i]];
+            bb = fma(bi, bi, bb);
         }
         const double bnorm = sqrt(block_dot_sum<BS>(bb, red));
         __syncthreads();
         if (bnorm == 0.0) {
-            for (int i = threadIdx.x; i < n; i += BS) x[i] = 0.0;
+            for (int i = threadIdx.x; i < n; i += BS) x[pm[i]] = 0.0;
             if (threadIdx.x == 0) {
                 res_out[sys] = 0.0;
                 it_out[sys] = 0;
@@ -100,7 +103,7 @@ __global__ void __launch_bounds__(BS)
         __syncthreads();
         double rr = 0.0;
         for (int i = threadIdx.x; i < n; i += BS) {
-            const double ri = b[i] - qs[i];
+            const double ri = b[pm[i]] - qs[i];
             rs[i] = ri;
             ps[i] = ri;
             rr = fma(ri, ri, rr);
@@ -108,7 +111,10 @@ __global__ void __launch_bounds__(BS)
         double rho = block_dot_sum<BS>(rr, red);
         int status = GKO_ERR_NOT_CONVERGED, iter = 0, checks = 0;
         double true_res = -1.0;
-        bool stop = sqrt(rho) <= tol * bnorm;
+        // ||r|| <= tol ||b|| tested as rho <= (tol ||b||)^2: no FP64 square
+        // root per step (FP64 work is charged per warp instruction)
+        const double thr2 = (tol * bnorm) * (tol * bnorm);
+        bool stop = rho <= thr2;
         if (stop) status = GKO_OK;
         while (!stop && iter < maxit) {
             __syncthreads();
@@ -135,14 +141,14 @@ __global__ void __launch_bounds__(BS)
                 status = GKO_ERR_BREAKDOWN;
                 break;
             }
-            if (sqrt(rho_new) <= tol * bnorm) {
+            if (rho_new <= thr2) {
                 // confirm with the true residual b - A x
                 __syncthreads();
                 sys_spmv(n, BS, rp, col, val, base, xs, qs);
                 __syncthreads();
                 double tt = 0.0;
                 for (int i = threadIdx.x; i < n; i += BS) {
-                    const double ti = b[i] - qs[i];
+                    const double ti = b[pm[i]] - qs[i];
                     tt = fma(ti, ti, tt);
                 }
                 true_res = sqrt(block_dot_sum<BS>(tt, red)) / bnorm;
@@ -165,12 +171,12 @@ __global__ void __launch_bounds__(BS)
             __syncthreads();
             double tt = 0.0;
             for (int i = threadIdx.x; i < n; i += BS) {
-                const double ti = b[i] - qs[i];
+                const double ti = b[pm[i]] - qs[i];
                 tt = fma(ti, ti, tt);
             }
             true_res = sqrt(block_dot_sum<BS>(tt, red)) / bnorm;
         }
-        for (int i = threadIdx.x; i < n; i += BS) x[i] = xs[i];
+        for (int i = threadIdx.x; i < n; i += BS) x[pm[i]] = xs[i];
         if (threadIdx.x == 0) {
             res_out[sys] = true_res;
             it_out[sys] = iter;
@@ -207,7 +213,7 @@ __device__ __forceinline__ void sys_spmv_reg(int n, const int32_t* __restrict__ 
 template <int BS, int R>
 __device__ __forceinline__ double sys_resid2_reg(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
                                                  const double* __restrict__ val, int32_t base, const double* v,
-                                                 const double* __restrict__ b)
+                                                 const double* __restrict__ b, const int32_t* __restrict__ pm)
 {
     double tt = 0.0;
 #pragma unroll
@@ -217,7 +223,7 @@ __device__ __forceinline__ double sys_resid2_reg(int n, const int32_t* __restric
             double acc = 0.0;
             const int32_t k1 = rp[i + 1] - base;
             for (int32_t kk = rp[i] - base; kk < k1; ++kk) acc = fma(val[kk], v[col[kk]], acc);
-            const double t = b[i] - acc;
+            const double t = b[pm[i]] - acc;
             tt = fma(t, t, tt);
         }
     }
@@ -228,9 +234,9 @@ template <int BS, int R>
 __global__ void __launch_bounds__(BS)
     batched_cg_reg_kernel(int64_t count, const int64_t* __restrict__ row_off, const int32_t* __restrict__ row_ptr,
                           const int32_t* __restrict__ col_all, const double* __restrict__ val_all,
-                          const int32_t* __restrict__ order, int32_t* queue, const double* __restrict__ b_all,
-                          double* __restrict__ x_all, double tol, int maxit, double* __restrict__ res_out,
-                          int32_t* __restrict__ it_out, int32_t* __restrict__ st_out)
+                          const int32_t* __restrict__ order, const int32_t* __restrict__ perm, int32_t* queue,
+                          const double* __restrict__ b_all, double* __restrict__ x_all, double tol, int maxit,
+                          double* __restrict__ res_out, int32_t* __restrict__ it_out, int32_t* __restrict__ st_out)
 {
     extern __shared__ __align__(16) double ps[];  // the direction p (or x while a residual is formed)
     __shared__ double red[BS / 32];
@@ -251,21 +257,22 @@ __global__ void __launch_bounds__(BS)
         const double* val = val_all + base;
         const double* b = b_all + r0;
         double* x = x_all + r0;
+        const int32_t* pm = perm + r0;  // b and x are indexed in the caller's row order
 
         double xr[R], rr[R], qr[R];
         double bb = 0.0;
 #pragma unroll
         for (int k = 0; k < R; ++k) {
             const int i = threadIdx.x + k * BS;
-            xr[k] = i < n ? x[i] : 0.0;
-            rr[k] = i < n ? b[i] : 0.0;
+            xr[k] = i < n ? x[pm[i]] : 0.0;
+            rr[k] = i < n ? b[pm[i]] : 0.0;
             bb = fma(rr[k], rr[k], bb);
         }
         const double bnorm = sqrt(block_dot_sum<BS>(bb, red));
         if (bnorm == 0.0) {
 #pragma unroll
             for (int k = 0; k < R; ++k)
-                if (threadIdx.x + k * BS < n) x[threadIdx.x + k * BS] = 0.0;
+                if (threadIdx.x + k * BS < n) x[pm[threadIdx.x + k * BS]] = 0.0;
             if (threadIdx.x == 0) {
                 res_out[sys] = 0.0;
                 it_out[sys] = 0;
@@ -293,7 +300,10 @@ __global__ void __launch_bounds__(BS)
         rho = block_dot_sum<BS>(rho, red);  // its barrier also completes p
         int status = GKO_ERR_NOT_CONVERGED, iter = 0, checks = 0;
         double true_res = -1.0;
-        bool stop = sqrt(rho) <= tol * bnorm;
+        // ||r|| <= tol ||b|| tested as rho <= (tol ||b||)^2: no FP64 square
+        // root per step (FP64 work is charged per warp instruction)
+        const double thr2 = (tol * bnorm) * (tol * bnorm);
+        bool stop = rho <= thr2;
         if (stop) status = GKO_OK;
         while (!stop && iter < maxit) {
             sys_spmv_reg<BS, R>(n, rp, col, val, base, ps, qr);
@@ -323,7 +333,7 @@ __global__ void __launch_bounds__(BS)
                 status = GKO_ERR_BREAKDOWN;
                 break;
             }
-            if (sqrt(rho_new) <= tol * bnorm) {
+            if (rho_new <= thr2) {
                 // confirm with the true residual: stage x in ps, keeping p's own rows in qr
 #pragma unroll
                 for (int k = 0; k < R; ++k) {
@@ -334,7 +344,7 @@ __global__ void __launch_bounds__(BS)
                     }
                 }
                 __syncthreads();
-                const double tt = sys_resid2_reg<BS, R>(n, rp, col, val, base, ps, b);
+                const double tt = sys_resid2_reg<BS, R>(n, rp, col, val, base, ps, b, pm);
                 true_res = sqrt(block_dot_sum<BS>(tt, red)) / bnorm;  // every gather of x done past its barrier
 #pragma unroll
                 for (int k = 0; k < R; ++k)
@@ -360,12 +370,12 @@ __global__ void __launch_bounds__(BS)
             for (int k = 0; k < R; ++k)
                 if (threadIdx.x + k * BS < n) ps[threadIdx.x + k * BS] = xr[k];
             __syncthreads();
-            const double tt = sys_resid2_reg<BS, R>(n, rp, col, val, base, ps, b);
+            const double tt = sys_resid2_reg<BS, R>(n, rp, col, val, base, ps, b, pm);
             true_res = sqrt(block_dot_sum<BS>(tt, red)) / bnorm;
         }
 #pragma unroll
         for (int k = 0; k < R; ++k)
-            if (threadIdx.x + k * BS < n) x[threadIdx.x + k * BS] = xr[k];
+            if (threadIdx.x + k * BS < n) x[pm[threadIdx.x + k * BS]] = xr[k];
         if (threadIdx.x == 0) {
             res_out[sys] = true_res;
             it_out[sys] = iter;
@@ -387,7 +397,7 @@ static int launch_batched_reg(gko_batch* B, const double* b, double* x, double t
     const int64_t grid = std::min<int64_t>(static_cast<int64_t>(per_sm) * sms, B->count);
     GKO_CUDA(cudaMemsetAsync(B->queue, 0, sizeof(int32_t), st));
     batched_cg_reg_kernel<BS, R><<<static_cast<unsigned>(std::max<int64_t>(grid, 1)), BS, smem, st>>>(
-        B->count, B->row_off, B->row_ptr, B->col, B->val, B->order, B->queue, b, x, tol, maxit, B->res, B->iters,
+        B->count, B->row_off, B->row_ptr, B->col, B->val, B->order, B->perm, B->queue, b, x, tol, maxit, B->res, B->iters,
         B->status);
     GKO_CUDA(cudaGetLastError());
     return GKO_OK;
@@ -410,7 +420,7 @@ static int launch_batched(gko_batch* B, const double* b, double* x, double tol, 
     const int64_t grid = std::min<int64_t>(static_cast<int64_t>(per_sm) * sms, B->count);
     GKO_CUDA(cudaMemsetAsync(B->queue, 0, sizeof(int32_t), st));
     batched_cg_kernel<BS><<<static_cast<unsigned>(std::max<int64_t>(grid, 1)), BS, smem, st>>>(
-        B->count, B->row_off, B->row_ptr, B->col, B->val, B->order, B->queue, b, x, tol, maxit, B->res, B->iters,
+        B->count, B->row_off, B->row_ptr, B->col, B->val, B->order, B->perm, B->queue, b, x, tol, maxit, B->res, B->iters,
         B->status, B->max_rows);
     GKO_CUDA(cudaGetLastError());
     return GKO_OK;
@@ -506,6 +516,59 @@ int gko_batch_create(int64_t count, const int64_t* row_off, const int32_t* row_p
     GKO_CUDA(cudaMemcpy(&last, row_ptr + n_rows, sizeof(int32_t), kind));
     const int64_t nnz = last;
     if (nnz > 0 && (!col || !val)) return fail(GKO_ERR_INVALID_ARG, "NULL array");
+    // host copies of the systems, validated, then renumbered
+    std::vector<int32_t> hrp(n_rows + 1), hcol(nnz), hperm(n_rows);
+    std::vector<double> hval(nnz);
+    GKO_CUDA(cudaMemcpy(hrp.data(), row_ptr, (n_rows + 1) * sizeof(int32_t), kind));
+    if (nnz) {
+        GKO_CUDA(cudaMemcpy(hcol.data(), col, nnz * sizeof(int32_t), kind));
+        GKO_CUDA(cudaMemcpy(hval.data(), val, nnz * sizeof(double), kind));
+    }
+    if (hrp[0] != 0) return fail(GKO_ERR_INVALID_MATRIX, "row_ptr[0] must be 0");
+    for (int64_t i = 0; i < n_rows; ++i)
+        if (hrp[i + 1] < hrp[i]) return fail(GKO_ERR_INVALID_MATRIX, "row_ptr must be non-decreasing");
+    for (int64_t sy = 0; sy < count; ++sy) {
+        const int64_t ns = ro[sy + 1] - ro[sy];
+        for (int64_t k = hrp[ro[sy]]; k < hrp[ro[sy + 1]]; ++k)
+            if (hcol[k] < 0 || hcol[k] >= ns) return fail(GKO_ERR_INVALID_MATRIX, "column index outside its system");
+    }
+    // Every system is stored renumbered, P A P^T with its rows in order of
+    // decreasing length (stable): the kernels give a thread one row at a time
+    // and a warp's FMA loop runs to its longest row, so rows of like length
+    // side by side waste fewer FP64 slots (on the 4,096-system benchmark
+    // batch: 1.06 instead of 1.53 issued per stored entry).  perm[r0 + k] is
+    // the caller's row of stored row k; the kernels gather b and x and
+    // scatter x through it.
+    std::vector<int32_t> nrp(n_rows + 1), ncol(nnz), inv;
+    std::vector<double> nval(nnz);
+    nrp[0] = 0;
+    for (int64_t sy = 0; sy < count; ++sy) {
+        const int64_t r0 = ro[sy], ns = ro[sy + 1] - r0;
+        int32_t* pm = hperm.data() + r0;
+        std::iota(pm, pm + ns, 0);
+        std::stable_sort(pm, pm + ns, [&](int32_t a, int32_t c) {
+            return hrp[r0 + a + 1] - hrp[r0 + a] > hrp[r0 + c + 1] - hrp[r0 + c];
+        });
+        inv.assign(ns, 0);
+        for (int64_t k = 0; k < ns; ++k) inv[pm[k]] = static_cast<int32_t>(k);
+        std::vector<std::pair<int32_t, double>> rowbuf;
+        for (int64_t k = 0; k < ns; ++k) {
+            const int64_t src = r0 + pm[k];
+            rowbuf.clear();
+            for (int64_t e = hrp[src]; e < hrp[src + 1]; ++e) rowbuf.emplace_back(inv[hcol[e]], hval[e]);
+            std::stable_sort(rowbuf.begin(), rowbuf.end(),
+                             [](const std::pair<int32_t, double>& a, const std::pair<int32_t, double>& c) {
+                                 return a.first < c.first;
+                             });
+            int64_t d = nrp[r0 + k];
+            for (const auto& pr : rowbuf) {
+                ncol[d] = pr.first;
+                nval[d] = pr.second;
+                ++d;
+            }
+            nrp[r0 + k + 1] = static_cast<int32_t>(d);
+        }
+    }
     gko_batch* B = new gko_batch();
     auto cleanup = [&](int s) {
         gko_batch_destroy(B);
@@ -520,22 +583,23 @@ int gko_batch_create(int64_t count, const int64_t* row_off, const int32_t* row_p
     if ((s = dev_alloc(&B->row_off, count + 1)) || (s = dev_alloc(&B->row_ptr, n_rows + 1)) ||
         (s = dev_alloc(&B->col, nnz)) || (s = dev_alloc(&B->val, nnz)) || (s = dev_alloc(&B->order, count)) ||
         (s = dev_alloc(&B->queue, 1)) || (s = dev_alloc(&B->res, count)) || (s = dev_alloc(&B->iters, count)) ||
-        (s = dev_alloc(&B->status, count)) || (s = dev_alloc(&B->d_err, 1)))
+        (s = dev_alloc(&B->status, count)) || (s = dev_alloc(&B->d_err, 1)) || (s = dev_alloc(&B->perm, n_rows)))
         return cleanup(s);
-    const cudaMemcpyKind k2 = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     // work-queue order: decreasing size, ties by index
     std::vector<int32_t> ord(count);
     std::iota(ord.begin(), ord.end(), 0);
     std::stable_sort(ord.begin(), ord.end(),
                      [&](int32_t a, int32_t c) { return ro[a + 1] - ro[a] > ro[c + 1] - ro[c]; });
     cudaError_t e = cudaMemcpyAsync(B->row_off, ro.data(), (count + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(B->row_ptr, row_ptr, (n_rows + 1) * sizeof(int32_t), k2, st);
-    if (e == cudaSuccess && nnz) e = cudaMemcpyAsync(B->col, col, nnz * sizeof(int32_t), k2, st);
-    if (e == cudaSuccess && nnz) e = cudaMemcpyAsync(B->val, val, nnz * sizeof(double), k2, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(B->row_ptr, nrp.data(), (n_rows + 1) * sizeof(int32_t), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && nnz) e = cudaMemcpyAsync(B->col, ncol.data(), nnz * sizeof(int32_t), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && nnz) e = cudaMemcpyAsync(B->val, nval.data(), nnz * sizeof(double), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(B->perm, hperm.data(), n_rows * sizeof(int32_t), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(B->order, ord.data(), count * sizeof(int32_t), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cleanup(cuda_fail(e, "copying the batch"));
-    if ((s = validate_csr(n_rows, max_rows, nnz, B->row_ptr, B->col, st)) != GKO_OK) return cleanup(s);
     *out = B;
     return GKO_OK;
 }
@@ -553,6 +617,7 @@ int gko_batch_destroy(gko_batch* B)
     dev_free(B->iters);
     dev_free(B->status);
     dev_free(B->d_err);
+    dev_free(B->perm);
     if (B->graph) cudaGraphExecDestroy(B->graph);
     delete B;
     return GKO_OK;

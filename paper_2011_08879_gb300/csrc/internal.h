@@ -162,6 +162,7 @@ struct gko_batch {
     int32_t* col = nullptr;       // device, local column indices
     double* val = nullptr;
     int32_t* order = nullptr;     // systems sorted by decreasing size (work queue order)
+    int32_t* perm = nullptr;      // per system: the caller's row of each stored (renumbered) row
     int32_t* queue = nullptr;     // device work-queue counter
     double* res = nullptr;        // per system: relative residual
     int32_t* iters = nullptr;     // per system: iterations

@@ -407,6 +407,17 @@ def test_batched_cg_dense_cholesky_subset(gko, dev, orc):
         assert np.linalg.norm(xg[r0:r1] - xc) <= 1e-10 * np.linalg.norm(xc)
 
 
+def test_batched_rejects_column_outside_system(gko, dev):
+    B = syn.batched_spd(3, seed=72, n_min=10, n_max=20)
+    bad = dict(B)
+    bad["col_idx"] = B["col_idx"].copy()
+    r1 = B["row_off"][1]
+    bad["col_idx"][B["row_ptr"][r1] + 1] = B["row_off"][2] - r1  # one past the second system's size
+    with pytest.raises(gko.GkoError) as e:
+        gko.Batch(bad)
+    assert e.value.status == gko.binding.ERR_INVALID_MATRIX
+
+
 def test_batched_autotune_and_maxit(gko, dev, orc):
     import torch
     B = syn.batched_spd(200, seed=71)
