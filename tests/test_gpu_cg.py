@@ -429,3 +429,22 @@ def test_batched_autotune_and_maxit(gko, dev, orc):
     s, infos = G.cg(_t(B["rhs"], dev), x, maxit=2)
     assert s == gko.binding.ERR_NOT_CONVERGED
     assert all(i.iterations == 2 for i in infos)
+
+
+def test_mixed_cg_inner_breakdown_on_indefinite_copy(gko, dev, orc):
+    """The BF16 copy of an SPD matrix made indefinite by rounding (see the
+    oracle's test of the same case): the inner CG breaks down at its first
+    step in every correction, the solve ends NOT_CONVERGED after
+    maxit_outer corrections with x unchanged and finite, as the oracle's."""
+    import test_oracle as to
+    A, b, lo_min, _ = to._indefinite_bf16_case(orc)
+    assert lo_min < -1e-4
+    _, st_o, o_o, _, res_o = orc.cg_mixed(A, b, prec="bf16", tol=1e-10, maxit_outer=5, inner_tol=1e-1)
+    M = gko.Matrix(A)
+    x = _t(np.zeros(A["n_rows"]), dev)
+    info = M.cg_mixed(_t(b, dev), x, inner="bf16", tol=1e-10, maxit_outer=5, inner_tol=1e-1)
+    assert info.status == st_o == gko.binding.ERR_NOT_CONVERGED
+    assert info.outer_iterations == o_o == 5 and info.iterations <= 5
+    xg = x.cpu().numpy()
+    assert np.all(np.isfinite(xg)) and abs(info.rel_residual - res_o) < 1e-12
+

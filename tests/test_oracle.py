@@ -1050,3 +1050,36 @@ def test_all_cores_row_loop_equals_the_oracle(orc, threads):
         a = orc.spmv_csr(A, x, 1.5, -0.5, y0)
         b = orc.spmv_csr_omp(A, x, threads, 1.5, -0.5, y0)
         assert np.array_equal(a, b)
+
+def _indefinite_bf16_case(orc):
+    """48 x 48 SPD matrix (eigenvalues 1e-6 and 1..2, seeded orthogonal basis)
+    whose BF16 copy (rounding the diagonal to nearest) has an eigenvalue of
+    -4e-4; b is that eigenvector, so the inner CG on A_lo meets p.Ap < 0 at
+    its first step."""
+    n = 48
+    U = syn.uniform_pm1(10, 1, np.arange(n * n, dtype=np.uint64)).reshape(n, n)
+    Q, _ = np.linalg.qr(U)
+    lam = np.linspace(1.0, 2.0, n)
+    lam[0] = 1e-6
+    D = (Q * lam) @ Q.T
+    D = 0.5 * (D + D.T)
+    r, c = np.nonzero(D)
+    A = dict(n_rows=n, n_cols=n, row_ptr=np.concatenate([[0], np.cumsum((D != 0).sum(1))]).astype(np.int32),
+             col_idx=c.astype(np.int32), val=D[r, c])
+    Dl = np.zeros((n, n))
+    Dl[r, c] = orc.round_matrix(A, "bf16")
+    ev, V = np.linalg.eigh(0.5 * (Dl + Dl.T))
+    return A, V[:, 0], ev[0], np.linalg.eigvalsh(D)[0]
+
+
+def test_mixed_cg_inner_breakdown_on_indefinite_copy(orc):
+    """Rounding the diagonal to nearest can leave A_lo indefinite though A is
+    SPD.  The inner CG then stops at its breakdown (p.Ap <= 0) and the outer
+    loop keeps its FP64 residual: no NaN, no progress along that direction,
+    NOT_CONVERGED after maxit_outer corrections of one inner step each."""
+    A, b, lo_min, a_min = _indefinite_bf16_case(orc)
+    assert a_min > 0 and lo_min < -1e-4
+    x, st, o, i, res = orc.cg_mixed(A, b, prec="bf16", tol=1e-10, maxit_outer=5, inner_tol=1e-1)
+    assert st == orc.NOT_CONVERGED and o == 5 and i == 5
+    assert np.all(np.isfinite(x)) and abs(res - 1.0) < 1e-12
+
