@@ -578,6 +578,24 @@ def run_extras(gko, torch, dev, st, selector=True, selector_matrices=200):
             "rel_residual": info.rel_residual, "status": info.status, "rel_error_vs_x_true": err,
             "us_per_iteration": round(t / max(info.iterations, 1) * 1e6, 1)}
         P.close()
+    # several right-hand sides: 8 columns sharing one SpMM per step against 8
+    # single-vector CG runs (CSR products), 200 steps each (tol 0: no stop)
+    kr, steps = 8, 200
+    Xt8 = torch.stack([torch.from_numpy(syn.vector(n, 40 + c)).to(dev) for c in range(kr)], dim=1).contiguous()
+    B8 = torch.empty_like(Xt8)
+    M.spmm(Xt8, B8, stream=st)
+    for _ in range(2):
+        X8 = torch.zeros_like(B8)
+        t_multi, (s8, inf8) = _time_call(torch, lambda: M.cg_multi(B8, X8, tol=0.0, maxit=steps, stream=st))
+    cols = [B8[:, c].contiguous() for c in range(kr)]
+    for _ in range(2):
+        xs = [torch.zeros(n, dtype=torch.float64, device=dev) for _c in range(kr)]
+        t_single, _r = _time_call(torch, lambda: [M.cg(cols[c], xs[c], tol=0.0, maxit=steps, fmt="csr", stream=st)
+                                                 for c in range(kr)])
+    res["fp64_cg_multi_rhs8_csr_200_steps"] = {
+        "s": round(t_multi, 4), "eight_single_cg_s": round(t_single, 4),
+        "speedup": round(t_single / t_multi, 3), "steps": [inf8[c].iterations for c in range(kr)],
+        "us_per_step": round(t_multi / steps * 1e6, 1)}
     # mixed: inner tolerances chosen by measurement (FP32 1e-2, BF16 1e-1),
     # without and with the Jacobi-preconditioned inner solve
     for key, prec, itol, pc in (("fp32", "fp32", 1e-2, "none"), ("bf16", "bf16", 1e-1, "none"),

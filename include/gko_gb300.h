@@ -373,6 +373,25 @@ int gko_block_jacobi_apply(const gko_block_jacobi* M, const double* r, double* z
 int gko_pcg_block_jacobi(const gko_matrix* A, int fmt, const gko_block_jacobi* M, const double* b, double* x,
                          double tol, int maxit, void* stream, gko_solve_info* info);
 
+/* CG for several right-hand sides at once, A X = B with k = 1..32 columns:
+ * k independent Hestenes-Stiefel recurrences (gko_cg per column, each with
+ * its own alpha, beta, stop test and iteration count) sharing one product
+ * per step, the SpMM of gko_spmm applied to the k search directions, so
+ * the matrix is read once per step for all columns.  B (n x k) and X
+ * (n x k, the initial guess on entry) are row-major device blocks (element
+ * (i, c) at i * ld + c), ldb, ldx >= k, not aliased; the CSR part must be
+ * materialised.  A column stops on ||r_c|| <= tol ||b_c|| confirmed by the
+ * FP64 true residual (up to four times), at maxit steps of its own, or on a
+ * breakdown of its own (p.q <= 0 or NaN); the others go on.  A zero column
+ * of B gives a zero column of X.  infos (k entries, or NULL) receives each
+ * column's steps, true relative residual and status; the return value is
+ * GKO_OK when every column converged, else the first failing column's
+ * status.  Workspace 3 n k doubles, stream-ordered; the loop runs in a CUDA
+ * graph with one host synchronisation per confirmation.  Synchronises the
+ * stream. */
+int gko_cg_multi(const gko_matrix* A, int64_t k, const double* B, int64_t ldb, double* X, int64_t ldx, double tol,
+                 int maxit, void* stream, gko_solve_info* infos);
+
 /* BiCGSTAB (van der Vorst, SIAM J. Sci. Stat. Comput. 13, 1992) on A x = b
  * for a general (nonsymmetric) square A, a Krylov solver of Sec. 6.2 for
  * systems CG does not cover.  Shadow residual r^ = r0; per step

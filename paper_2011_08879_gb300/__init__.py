@@ -169,6 +169,24 @@ class Matrix:
         return binding.gko_pcg_jacobi(self.handle, _fmt(fmt), _dev_f64(b, self.n_rows, "b"),
                                       _dev_f64(x, self.n_rows, "x"), tol, maxit, _stream(stream))
 
+    def cg_multi(self, B, X, tol=1e-10, maxit=10000, stream=None):
+        """CG on A X = B for the k <= 32 columns of the row-major device
+        blocks B, X (torch tensors of shape (n, k), last dimension
+        contiguous; X holds the initial guess).  Returns (status, infos)."""
+        import torch
+        for t, name in ((B, "B"), (X, "X")):
+            if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.dim() == 2):
+                raise TypeError("%s must be a 2-D float64 CUDA tensor" % name)
+        k = int(B.shape[1])
+        if tuple(B.shape) != (self.n_rows, k) or tuple(X.shape) != (self.n_rows, k):
+            raise ValueError("B and X must be (n_rows, k)")
+        if B.stride(1) != 1 or X.stride(1) != 1:
+            raise ValueError("B and X need a contiguous last dimension")
+        infos = (SolveInfo * k)()
+        s = binding.gko_cg_multi(self.handle, k, B.data_ptr(), B.stride(0), X.data_ptr(), X.stride(0), tol, maxit,
+                                 _stream(stream), infos)
+        return s, infos
+
     def pcg_block_jacobi(self, M, b, x, tol=1e-10, maxit=10000, fmt="csr", stream=None):
         """CG preconditioned by M, a BlockJacobi built from this matrix."""
         return binding.gko_pcg_block_jacobi(self.handle, _fmt(fmt), M.handle, _dev_f64(b, self.n_rows, "b"),

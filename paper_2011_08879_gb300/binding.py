@@ -65,6 +65,7 @@ _SIGS = {
     "gko_cg_single_reduction": (_INT, [_P, _INT, _P, _P, _D, _INT, _P, C.POINTER(SolveInfo)]),
     "gko_pcg_jacobi": (_INT, [_P, _INT, _P, _P, _D, _INT, _P, C.POINTER(SolveInfo)]),
     "gko_bicgstab": (_INT, [_P, _INT, _P, _P, _D, _INT, _P, C.POINTER(SolveInfo)]),
+    "gko_cg_multi": (_INT, [_P, _I64, _P, _I64, _P, _I64, _D, _INT, _P, _P]),
     "gko_block_jacobi_create": (_INT, [_P, _INT, _P, C.POINTER(_P)]),
     "gko_block_jacobi_destroy": (_INT, [_P]),
     "gko_block_jacobi_export": (_INT, [_P, C.POINTER(_I64), _P, _P, _P]),
@@ -226,6 +227,14 @@ def gko_pcg_jacobi(A, fmt, b, x, tol, maxit, stream=0, raise_on=()) -> SolveInfo
     _check(s, "gko_pcg_jacobi", allow)
     info.status = s
     return info
+
+
+def gko_cg_multi(A, k, B, ldb, X, ldx, tol, maxit, stream=0, infos=None) -> int:
+    """infos: optional ctypes array of k SolveInfo.  Returns the status
+    (NOT_CONVERGED / BREAKDOWN of a column are not raised)."""
+    s = lib.gko_cg_multi(A, k, B, ldb, X, ldx, tol, maxit, stream, infos)
+    _check(s, "gko_cg_multi", (ERR_NOT_CONVERGED, ERR_BREAKDOWN))
+    return s
 
 
 def gko_block_jacobi_create(A, max_block_size, stream=0) -> int:

@@ -269,6 +269,8 @@ int pcg_jacobi_solve(const gko_matrix* A, int fmt, const double* b, double* x, d
                      cudaStream_t st, gko_solve_info* info);
 int pcg_block_jacobi_solve(const gko_matrix* A, int fmt, const gko_block_jacobi* M, const double* b, double* x,
                            double tol, int maxit, cudaStream_t st, gko_solve_info* info);
+int cg_multi_solve(const gko_matrix* A, int64_t k, const double* B, int64_t ldb, double* X, int64_t ldx, double tol,
+                   int maxit, cudaStream_t st, gko_solve_info* infos);
 int bicgstab_solve(const gko_matrix* A, int fmt, const double* b, double* x, double tol, int maxit,
                    cudaStream_t st, gko_solve_info* info);
 int spmm_csr(const gko_matrix* A, int64_t k, const double* x, int64_t ldx, double* y, int64_t ldy, double alpha,

@@ -4,6 +4,9 @@
 // depend on scheduling) and the stop of a graph's conditional WHILE loop.
 #pragma once
 
+#include <algorithm>
+#include <vector>
+
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -164,5 +167,70 @@ struct Cg1Reduce {
     const uint32_t* err;
     cudaGraphConditionalHandle h;
 };
+
+// ----------------------------------------------------------- workspace
+
+struct Workspace {
+    cudaStream_t st;
+    std::vector<void*> ptrs;
+    explicit Workspace(cudaStream_t s) : st(s) {}
+    template <typename T>
+    int get(T** p, int64_t count)
+    {
+        *p = nullptr;
+        cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(p), std::max<int64_t>(count, 1) * sizeof(T), st);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync (solver workspace)");
+        ptrs.push_back(*p);
+        return GKO_OK;
+    }
+    ~Workspace()
+    {
+        for (void* q : ptrs) cudaFreeAsync(q, st);
+    }
+};
+
+struct GraphHolder {
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    ~GraphHolder()
+    {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (g) cudaGraphDestroy(g);
+    }
+};
+
+// Build a graph whose single node is WHILE(cond){ body(handle, cap) }.
+// The body is captured on a private non-blocking stream `cap` (capture is
+// not allowed on the legacy default stream the caller may be using); the
+// instantiated graph is then launched on the caller's stream.
+template <typename Body>
+inline int build_while_graph(GraphHolder* gh, Body body)
+{
+    GKO_CUDA(cudaGraphCreate(&gh->g, 0));
+    cudaGraphConditionalHandle handle;
+    GKO_CUDA(cudaGraphConditionalHandleCreate(&handle, gh->g, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams params = {};
+    params.type = cudaGraphNodeTypeConditional;
+    params.conditional.handle = handle;
+    params.conditional.type = cudaGraphCondTypeWhile;
+    params.conditional.size = 1;
+    cudaGraphNode_t node;
+    GKO_CUDA(cudaGraphAddNode(&node, gh->g, nullptr, nullptr, 0, &params));
+    cudaGraph_t bodyg = params.conditional.phGraph_out[0];
+    cudaStream_t cap;
+    GKO_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    cudaError_t e = cudaStreamBeginCaptureToGraph(cap, bodyg, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    int s = GKO_OK;
+    if (e == cudaSuccess) {
+        s = body(handle, cap);
+        cudaGraph_t captured = nullptr;
+        e = cudaStreamEndCapture(cap, &captured);
+    }
+    cudaStreamDestroy(cap);
+    if (s != GKO_OK) return s;
+    if (e != cudaSuccess) return cuda_fail(e, "capturing the CG body");
+    GKO_CUDA(cudaGraphInstantiate(&gh->exec, gh->g, 0));
+    return GKO_OK;
+}
 
 }  // namespace gko
