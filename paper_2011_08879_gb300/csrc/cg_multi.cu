@@ -8,8 +8,10 @@
 // saving is the matrix and index traffic and the launches of k-1 products.
 //
 // Blocks are row-major (element (i, c) at i * ld + c); the workspace blocks
-// R, P, Q have ld = k.  One step is six launches inside a CUDA-graph WHILE
-// loop:
+// R, P, Q have ld = k.  For k dividing 32 the vector kernels take a thread
+// per element (coalesced; a thread always meets the same column); for other
+// k a thread per row walks the row's k columns.  One step is six launches
+// inside a CUDA-graph WHILE loop:
 //   Q = A P                                       (SpMM)
 //   per-column partial sums of P.Q                (thread per row, k columns)
 //   alpha_c = rho_c / (P.Q)_c                     (one block, a warp per column)
@@ -116,7 +118,9 @@ __device__ __forceinline__ double mc_column_total(const double* __restrict__ par
 
 // ------------------------------------------------------------- kernels
 
-// per-column partial sums of P .* Q (rows by thread)
+// per-column partial sums of P .* Q (rows by thread).  With k == KM the
+// column loop has no bound test, so the compiler issues a row's loads
+// together; otherwise each column is guarded.
 template <int KM>
 __global__ void __launch_bounds__(kMcThreads)
     mc_pq_partial_kernel(int64_t n, int k, const double* __restrict__ P, const double* __restrict__ Q,
@@ -125,15 +129,128 @@ __global__ void __launch_bounds__(kMcThreads)
     double acc[KM];
 #pragma unroll
     for (int c = 0; c < KM; ++c) acc[c] = 0.0;
+    const bool full = k == KM;
     for (int64_t i = blockIdx.x * static_cast<int64_t>(kMcThreads) + threadIdx.x; i < n;
          i += static_cast<int64_t>(gridDim.x) * kMcThreads) {
         const double* p = P + i * k;
         const double* q = Q + i * k;
+        if (full) {
 #pragma unroll
-        for (int c = 0; c < KM; ++c)
-            if (c < k) acc[c] = fma(p[c], q[c], acc[c]);  // k is uniform: a branch, not a predicate
+            for (int c = 0; c < KM; ++c) acc[c] = fma(p[c], q[c], acc[c]);
+        } else {
+#pragma unroll
+            for (int c = 0; c < KM; ++c)
+                if (c < k) acc[c] = fma(p[c], q[c], acc[c]);
+        }
     }
     mc_block_partials(acc, part);
+}
+
+// ------------------------------------- element kernels (k divides 32)
+//
+// Thread per element of the row-major block (consecutive threads,
+// consecutive addresses), four elements per pass.  The grid's thread count
+// is a multiple of 32, so a thread always meets the same column
+// c = lane mod k and keeps one accumulator; lanes of equal c combine by a
+// butterfly over the distances 16 .. k.
+
+// the block's sums of a per-thread value by column (lane mod k) into
+// part[blockIdx.x * kMcMaxK + c], c < k
+__device__ __forceinline__ void mc_elem_partials(double acc, int k, double* __restrict__ part)
+{
+    __shared__ double sh[kMcMaxK][kMcThreads / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int d = 16; d >= k; d >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, d);
+    if (lane < k) sh[lane][w] = acc;
+    __syncthreads();
+    if (threadIdx.x < k) {
+        double t = 0.0;
+        for (int q = 0; q < kMcThreads / 32; ++q) t += sh[threadIdx.x][q];
+        part[blockIdx.x * static_cast<int64_t>(kMcMaxK) + threadIdx.x] = t;
+    }
+}
+
+__global__ void __launch_bounds__(kMcThreads)
+    mc_pq_elem_kernel(int64_t ne, int k, const double* __restrict__ P, const double* __restrict__ Q,
+                      double* __restrict__ part)
+{
+    const int64_t nth = static_cast<int64_t>(gridDim.x) * kMcThreads;
+    int64_t e = blockIdx.x * static_cast<int64_t>(kMcThreads) + threadIdx.x;
+    double acc = 0.0;
+    for (; e + 3 * nth < ne; e += 4 * nth) {
+        const double p0 = P[e], p1 = P[e + nth], p2 = P[e + 2 * nth], p3 = P[e + 3 * nth];
+        const double q0 = Q[e], q1 = Q[e + nth], q2 = Q[e + 2 * nth], q3 = Q[e + 3 * nth];
+        acc = fma(p3, q3, fma(p2, q2, fma(p1, q1, fma(p0, q0, acc))));
+    }
+    for (; e < ne; e += nth) acc = fma(P[e], Q[e], acc);
+    mc_elem_partials(acc, k, part);
+}
+
+// X += alpha P, R -= alpha Q (iterating columns), partial sums of R .* R;
+// X has leading dimension ldx
+__global__ void __launch_bounds__(kMcThreads)
+    mc_update_elem_kernel(int64_t ne, int k, double* __restrict__ X, int64_t ldx, double* __restrict__ R,
+                          const double* __restrict__ P, const double* __restrict__ Q, const MultiState* s,
+                          double* __restrict__ part)
+{
+    const int c = threadIdx.x % k;  // the thread's column (nth is a multiple of k)
+    const bool on = s->phase[c] == kMcIterating;
+    const double a = on ? s->alpha[c] : 0.0;
+    const int64_t nth = static_cast<int64_t>(gridDim.x) * kMcThreads;
+    int64_t e = blockIdx.x * static_cast<int64_t>(kMcThreads) + threadIdx.x;
+    double acc = 0.0;
+    const int lk = __ffs(k) - 1;  // k is a power of two
+    auto xi = [&](int64_t el) { return (el >> lk) * ldx + c; };
+    for (; e + 3 * nth < ne; e += 4 * nth) {
+        double xv[4], rv[4], pv[4], qv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int64_t el = e + u * nth;
+            xv[u] = X[xi(el)];
+            rv[u] = R[el];
+            pv[u] = P[el];
+            qv[u] = Q[el];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int64_t el = e + u * nth;
+            const double rn = on ? fma(-a, qv[u], rv[u]) : rv[u];
+            X[xi(el)] = on ? fma(a, pv[u], xv[u]) : xv[u];
+            R[el] = rn;
+            acc = fma(rn, rn, acc);
+        }
+    }
+    for (; e < ne; e += nth) {
+        const double rn = on ? fma(-a, Q[e], R[e]) : R[e];
+        if (on) X[xi(e)] = fma(a, P[e], X[xi(e)]);
+        R[e] = rn;
+        acc = fma(rn, rn, acc);
+    }
+    mc_elem_partials(acc, k, part);
+}
+
+// P = R + beta P (iterating columns; initial: P = R)
+__global__ void __launch_bounds__(kMcThreads)
+    mc_pupdate_elem_kernel(int64_t ne, int k, double* __restrict__ P, const double* __restrict__ R,
+                           const MultiState* s, int initial)
+{
+    const int c = threadIdx.x % k;
+    const bool on = initial || s->phase[c] == kMcIterating;
+    const double b = initial ? 0.0 : s->beta[c];
+    if (!on) return;  // nothing of this thread's column changes
+    const int64_t nth = static_cast<int64_t>(gridDim.x) * kMcThreads;
+    int64_t e = blockIdx.x * static_cast<int64_t>(kMcThreads) + threadIdx.x;
+    for (; e + 3 * nth < ne; e += 4 * nth) {
+        double pv[4], rv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            pv[u] = P[e + u * nth];
+            rv[u] = R[e + u * nth];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) P[e + u * nth] = fma(b, pv[u], rv[u]);
+    }
+    for (; e < ne; e += nth) P[e] = fma(b, P[e], R[e]);
 }
 
 // alpha_c = rho_c / (P.Q)_c for the iterating columns; a non-positive or
@@ -155,40 +272,68 @@ __global__ void __launch_bounds__(kMcFinal)
     }
 }
 
-// X += alpha P, R -= alpha Q for the iterating columns (alpha of the others
-// is not applied); per-column partial sums of R .* R
+// X += alpha P, R -= alpha Q for the iterating columns; per-column partial
+// sums of R .* R.  With k == KM every value of a row is loaded before any
+// store (so the loads issue together) and a stopped column keeps its
+// values by a select; with k < KM each column is guarded.
 template <int KM>
 __global__ void __launch_bounds__(kMcThreads)
     mc_update_kernel(int64_t n, int k, double* __restrict__ X, int64_t ldx, double* __restrict__ R,
                      const double* __restrict__ P, const double* __restrict__ Q, const MultiState* s,
                      double* __restrict__ part)
 {
-    __shared__ double al[kMcMaxK];
-    __shared__ int on[kMcMaxK];
+    __shared__ double al_s[kMcMaxK];
+    __shared__ int on_s[kMcMaxK];
     if (threadIdx.x < kMcMaxK) {
         const bool it = threadIdx.x < k && s->phase[threadIdx.x] == kMcIterating;
-        on[threadIdx.x] = it;
-        al[threadIdx.x] = it ? s->alpha[threadIdx.x] : 0.0;
+        on_s[threadIdx.x] = it;
+        al_s[threadIdx.x] = it ? s->alpha[threadIdx.x] : 0.0;
     }
     __syncthreads();
+    double al[KM];
+    bool on[KM];
+#pragma unroll
+    for (int c = 0; c < KM; ++c) {
+        al[c] = al_s[c];
+        on[c] = on_s[c] != 0;
+    }
     double acc[KM];
 #pragma unroll
     for (int c = 0; c < KM; ++c) acc[c] = 0.0;
+    const bool full = k == KM;
     for (int64_t i = blockIdx.x * static_cast<int64_t>(kMcThreads) + threadIdx.x; i < n;
          i += static_cast<int64_t>(gridDim.x) * kMcThreads) {
         double* x = X + i * ldx;
         double* r = R + i * k;
         const double* p = P + i * k;
         const double* q = Q + i * k;
+        if (full) {  // every load of the row first, then the stores
+            double xv[KM], rv[KM], pv[KM], qv[KM];
 #pragma unroll
-        for (int c = 0; c < KM; ++c)
-            if (c < k && on[c]) {
-                const double a = al[c];
-                x[c] = fma(a, p[c], x[c]);
-                const double rc = fma(-a, q[c], r[c]);
-                r[c] = rc;
-                acc[c] = fma(rc, rc, acc[c]);
+            for (int c = 0; c < KM; ++c) {
+                xv[c] = x[c];
+                rv[c] = r[c];
+                pv[c] = p[c];
+                qv[c] = q[c];
             }
+#pragma unroll
+            for (int c = 0; c < KM; ++c) {
+                const double xn = on[c] ? fma(al[c], pv[c], xv[c]) : xv[c];
+                const double rn = on[c] ? fma(-al[c], qv[c], rv[c]) : rv[c];
+                x[c] = xn;
+                r[c] = rn;
+                acc[c] = fma(rn, rn, acc[c]);
+            }
+        } else {
+#pragma unroll
+            for (int c = 0; c < KM; ++c)
+                if (c < k && on[c]) {
+                    x[c] = fma(al[c], p[c], x[c]);
+                    const double rn = fma(-al[c], q[c], r[c]);
+                    r[c] = rn;
+                    acc[c] = fma(rn, rn, acc[c]);
+                }
+        }
     }
     mc_block_partials(acc, part);
 }
@@ -227,27 +372,47 @@ __global__ void __launch_bounds__(kMcFinal)
 }
 
 // P = R + beta P for the iterating columns (initial: P = R for every
-// column)
+// column); with k == KM a row's loads precede its stores and stopped columns
+// are kept by a select
 template <int KM>
 __global__ void __launch_bounds__(kMcThreads)
     mc_pupdate_kernel(int64_t n, int k, double* __restrict__ P, const double* __restrict__ R, const MultiState* s,
                       int initial)
 {
-    __shared__ double be[kMcMaxK];
-    __shared__ int on[kMcMaxK];
+    __shared__ double be_s[kMcMaxK];
+    __shared__ int on_s[kMcMaxK];
     if (threadIdx.x < kMcMaxK) {
         const bool it = threadIdx.x < k && (initial || s->phase[threadIdx.x] == kMcIterating);
-        on[threadIdx.x] = it;
-        be[threadIdx.x] = initial ? 0.0 : (it ? s->beta[threadIdx.x] : 0.0);
+        on_s[threadIdx.x] = it;
+        be_s[threadIdx.x] = initial ? 0.0 : (it ? s->beta[threadIdx.x] : 0.0);
     }
     __syncthreads();
+    double be[KM];
+    bool on[KM];
+#pragma unroll
+    for (int c = 0; c < KM; ++c) {
+        be[c] = be_s[c];
+        on[c] = on_s[c] != 0;
+    }
+    const bool full = k == KM;
     for (int64_t i = blockIdx.x * static_cast<int64_t>(kMcThreads) + threadIdx.x; i < n;
          i += static_cast<int64_t>(gridDim.x) * kMcThreads) {
         double* p = P + i * k;
         const double* r = R + i * k;
+        if (full) {  // every load of the row first, then the stores
+            double pv[KM], rv[KM];
 #pragma unroll
-        for (int c = 0; c < KM; ++c)
-            if (c < k && on[c]) p[c] = fma(be[c], p[c], r[c]);
+            for (int c = 0; c < KM; ++c) {
+                pv[c] = p[c];
+                rv[c] = r[c];
+            }
+#pragma unroll
+            for (int c = 0; c < KM; ++c) p[c] = on[c] ? fma(be[c], pv[c], rv[c]) : pv[c];
+        } else {
+#pragma unroll
+            for (int c = 0; c < KM; ++c)
+                if (c < k && on[c]) p[c] = fma(be[c], p[c], r[c]);
+        }
     }
 }
 
@@ -331,7 +496,8 @@ static int mc_write(MultiState* d, const MultiState* h, cudaStream_t st)
     return GKO_OK;
 }
 
-// KM: column capacity of the row kernels' register accumulators (8 or 32)
+// KM: column capacity of the row kernels' register accumulators (8 or 32);
+// 0: k divides 32 and the element kernels run instead
 template <int KM>
 static int cg_multi_run(const gko_matrix* A, int64_t k, const double* B, int64_t ldb, double* X, int64_t ldx,
                         double tol, int maxit, cudaStream_t st, gko_solve_info* infos)
@@ -371,7 +537,8 @@ static int cg_multi_run(const gko_matrix* A, int64_t k, const double* B, int64_t
     auto residual = [&](double* dst, bool with_b) -> int {
         mc_copy_kernel<<<cgrid, 256, 0, st>>>(n, kk, B, ldb, dst);
         GKO_TRY(spmm_csr(A, k, X, ldx, dst, k, -1.0, 1.0, st));
-        mc_norms_kernel<KM><<<grid, kMcThreads, 0, st>>>(n, kk, dst, with_b ? B : nullptr, ldb, part, part2);
+        mc_norms_kernel<(KM == 0 ? (kMcMaxK) : KM)><<<grid, kMcThreads, 0, st>>>(n, kk, dst, with_b ? B : nullptr, ldb,
+                                                                               part, part2);
         mc_totals_kernel<<<1, kMcFinal, 0, st>>>(grid, part, with_b ? part2 : nullptr, ds, with_b ? bn2 : nullptr);
         GKO_CUDA(cudaGetLastError());
         return GKO_OK;
@@ -412,17 +579,35 @@ static int cg_multi_run(const gko_matrix* A, int64_t k, const double* B, int64_t
         }
     }
     GKO_TRY(mc_write(ds, &hs, st));
-    mc_pupdate_kernel<KM><<<grid, kMcThreads, 0, st>>>(n, kk, P, R, ds, 1);
+    auto pq = [&](cudaStream_t cs) {
+        if constexpr (KM == 0)
+            mc_pq_elem_kernel<<<grid, kMcThreads, 0, cs>>>(n * k, kk, P, Q, part);
+        else
+            mc_pq_partial_kernel<KM><<<grid, kMcThreads, 0, cs>>>(n, kk, P, Q, part);
+    };
+    auto update = [&](cudaStream_t cs) {
+        if constexpr (KM == 0)
+            mc_update_elem_kernel<<<grid, kMcThreads, 0, cs>>>(n * k, kk, X, ldx, R, P, Q, ds, part);
+        else
+            mc_update_kernel<KM><<<grid, kMcThreads, 0, cs>>>(n, kk, X, ldx, R, P, Q, ds, part);
+    };
+    auto pupdate = [&](cudaStream_t cs, int initial) {
+        if constexpr (KM == 0)
+            mc_pupdate_elem_kernel<<<grid, kMcThreads, 0, cs>>>(n * k, kk, P, R, ds, initial);
+        else
+            mc_pupdate_kernel<KM><<<grid, kMcThreads, 0, cs>>>(n, kk, P, R, ds, initial);
+    };
+    pupdate(st, 1);
     GKO_CUDA(cudaGetLastError());
     if (any) {
         GraphHolder gh;
         GKO_TRY(build_while_graph(&gh, [&](cudaGraphConditionalHandle h, cudaStream_t cs) -> int {
             GKO_TRY(spmm_csr(A, k, P, k, Q, k, 1.0, 0.0, cs));
-            mc_pq_partial_kernel<KM><<<grid, kMcThreads, 0, cs>>>(n, kk, P, Q, part);
+            pq(cs);
             mc_alpha_kernel<<<1, kMcFinal, 0, cs>>>(grid, part, ds);
-            mc_update_kernel<KM><<<grid, kMcThreads, 0, cs>>>(n, kk, X, ldx, R, P, Q, ds, part);
+            update(cs);
             mc_beta_kernel<<<1, kMcFinal, 0, cs>>>(grid, part, ds, h);
-            mc_pupdate_kernel<KM><<<grid, kMcThreads, 0, cs>>>(n, kk, P, R, ds, 0);
+            pupdate(cs, 0);
             GKO_CUDA(cudaGetLastError());
             return GKO_OK;
         }));
@@ -456,7 +641,7 @@ static int cg_multi_run(const gko_matrix* A, int64_t k, const double* B, int64_t
             }
             GKO_TRY(mc_write(ds, &hs, st));
             if (!again) break;
-            mc_pupdate_kernel<KM><<<grid, kMcThreads, 0, st>>>(n, kk, P, R, ds, 0);
+            pupdate(st, 0);
             GKO_CUDA(cudaGetLastError());
         }
     }
@@ -483,6 +668,8 @@ static int cg_multi_run(const gko_matrix* A, int64_t k, const double* B, int64_t
 int cg_multi_solve(const gko_matrix* A, int64_t k, const double* B, int64_t ldb, double* X, int64_t ldx, double tol,
                    int maxit, cudaStream_t st, gko_solve_info* infos)
 {
+    // KM = 0: k divides 32, the coalesced element kernels
+    if (32 % k == 0) return cg_multi_run<0>(A, k, B, ldb, X, ldx, tol, maxit, st, infos);
     if (k <= 8) return cg_multi_run<8>(A, k, B, ldb, X, ldx, tol, maxit, st, infos);
     return cg_multi_run<32>(A, k, B, ldb, X, ldx, tol, maxit, st, infos);
 }
