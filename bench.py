@@ -152,15 +152,20 @@ def measured_peaks():
 
 
 def kernel_source_hash():
-    """Hash of the CUDA sources with comments and whitespace removed (the
-    counters of a capture are valid only for the code they were taken on;
-    editing a comment does not change that code)."""
+    """Hash of the SpMV kernels' CUDA sources (the spmv_*.cu files and the
+    device headers they include: segmented.cuh, ell.cuh, common.cuh) with
+    comments and whitespace removed.  The DRAM counters of a capture are
+    valid only for the code they were taken on; the solvers' files and
+    comment edits do not change that code."""
     import glob
     import hashlib
     import re
     h = hashlib.sha256()
-    for p in sorted(glob.glob(os.path.join(ROOT, "paper_2011_08879_gb300", "csrc", "*"))):
-        if p.endswith((".cu", ".cuh", ".h")):
+    csrc = os.path.join(ROOT, "paper_2011_08879_gb300", "csrc")
+    files = glob.glob(os.path.join(csrc, "spmv_*.cu")) + [os.path.join(csrc, f) for f in
+                                                          ("segmented.cuh", "ell.cuh", "common.cuh")]
+    for p in sorted(files):
+        if os.path.exists(p):
             with open(p, encoding="utf-8") as f:
                 src = f.read()
             src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
