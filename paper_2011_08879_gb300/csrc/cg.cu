@@ -1216,6 +1216,13 @@ struct GmState {
     int32_t low_steps;  // steps whose second Gram-Schmidt update ran in FP32
     int32_t next_col;   // column of v_{j+1}
     uint32_t ticket;
+    // second update of this step (set by the last block of the second
+    // coefficient sums): low = FP32 path, its coefficients hf * sc, and hn
+    // from ||w1||^2 - ||h2||^2
+    int32_t low;
+    uint32_t coef_ticket;
+    double sc;
+    float hf[128];
 };
 
 // The block's share of V_c . w for the CNT columns c0 .. c0+CNT-1 into
@@ -1352,17 +1359,59 @@ __global__ void __launch_bounds__(kRedThreads, 4)
 // (no Hessenberg entry).
 __global__ void __launch_bounds__(kRedThreads)
     gm_coef_kernel(int nblocks, const double* __restrict__ part, int ldp, double* __restrict__ coef,
-                   double* __restrict__ hh, int second, const GmState* s)
+                   double* __restrict__ hh, int second, GmState* s)
 {
     __shared__ double sh[32];
-    const int c = blockIdx.x;
-    if (c > s->j + (second ? 1 : 0)) return;  // block-uniform
+    __shared__ bool last;
+    const int c = blockIdx.x, j = s->j;
+    if (c > j + (second ? 1 : 0)) return;  // block-uniform
     double t = 0.0;
     for (int b = threadIdx.x; b < nblocks; b += kRedThreads) t += part[b * static_cast<int64_t>(ldp) + c];
     t = block_sum(t, sh);
     if (threadIdx.x == 0) {
         coef[c] = t;
-        if (c <= s->j) hh[c] = second ? hh[c] + t : t;
+        if (c <= j) hh[c] = second ? hh[c] + t : t;
+    }
+    if (!second) return;
+    // the second pass: the last of its j + 2 blocks decides the update's
+    // precision once for the step (see gm_combine_norm_kernel)
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(&s->coef_ticket, 1u) == static_cast<unsigned>(j + 1);
+    }
+    __syncthreads();
+    if (!last || threadIdx.x >= 32) return;
+    __threadfence();
+    const int ncols = j + 1;
+    double hm = 0.0, h2 = 0.0;
+    for (int q = threadIdx.x; q < ncols; q += 32) {
+        const double h = __ldcg(coef + q);
+        hm = fmax(hm, fabs(h));
+        h2 = fma(h, h, h2);
+    }
+    for (int o = 16; o; o >>= 1) {
+        hm = fmax(hm, __shfl_xor_sync(0xffffffffu, hm, o));
+        h2 += __shfl_xor_sync(0xffffffffu, h2, o);
+    }
+    const double w1n2 = __ldcg(coef + ncols);
+    const double hn2 = w1n2 - h2;  // ||w2||^2: w1 is orthogonal to the basis up to rounding
+    const bool low = hm <= ldexp(sqrt(w1n2), -33) && hn2 > 0.0 && hn2 < INFINITY;  // false on NaN
+    int e = 0;
+    if (low && hm > 0.0) frexp(hm, &e);  // hm < 2^e <= 2 hm
+    const double isc = ldexp(1.0, -e);   // scaling by a power of two is exact
+    if (low)
+        for (int q = threadIdx.x; q < ncols; q += 32) s->hf[q] = static_cast<float>(__ldcg(coef + q) * isc);
+    if (threadIdx.x == 0) {
+        s->low = low;
+        s->sc = ldexp(1.0, e);
+        s->coef_ticket = 0;
+        if (low) {
+            const double hn = sqrt(hn2);
+            s->hn = hn;
+            s->hn_inv = 1.0 / hn;
+            s->next_col = j + 1;
+            s->low_steps += 1;
+        }
     }
 }
 
@@ -1449,85 +1498,76 @@ __device__ __forceinline__ void gm_givens_block(double* __restrict__ H, double* 
         for (int i = threadIdx.x; i <= j + 1; i += blockDim.x) H[i * m + j] = col[i];
 }
 
-// w1 - sum_{c < nc} h[c] V_c[i] with the sum formed in FP32 from the
-// float copy of the basis: h[c] = hf[c] * sc (sc a power of two, |hf| < 1),
-// the float sum converted exactly and applied by one FP64 FMA.  Two rows
-// per pass; *sq accumulates the squares of the new entries.
+// v = (w1 - sum_{c < nc} h[c] V_c[i]) / hn with the sum formed in FP32 from
+// the float copy of the basis: h[c] = hf[c] * sc (sc a power of two,
+// |hf| < 1), the float sum converted exactly and applied by one FP64 FMA;
+// v goes to the next basis column, its float copy and vcur.  Two rows per
+// pass.
 __device__ __forceinline__ void gm_correct_rows_f32(const float* __restrict__ Vf, int64_t n, const float* hf, int nc,
-                                                    double sc, double* __restrict__ w, double* sq)
+                                                    double sc, const double* __restrict__ w, double inv_hn,
+                                                    double* __restrict__ vnext, float* __restrict__ vnextf,
+                                                    double* __restrict__ vcur)
 {
     const int64_t nth = static_cast<int64_t>(gridDim.x) * kRedThreads;
     int64_t i = blockIdx.x * static_cast<int64_t>(kRedThreads) + threadIdx.x;
-    double acc = 0.0;
     for (; i + nth < n; i += 2 * nth) {
+        const double w0 = w[i], w1 = w[i + nth];  // issued before the column loop
         float c0 = 0.0f, c1 = 0.0f;
 #pragma unroll 8
         for (int c = 0; c < nc; ++c) {
             c0 = fmaf(hf[c], Vf[c * n + i], c0);
             c1 = fmaf(hf[c], Vf[c * n + i + nth], c1);
         }
-        const double t0 = fma(-sc, static_cast<double>(c0), w[i]);
-        const double t1 = fma(-sc, static_cast<double>(c1), w[i + nth]);
-        w[i] = t0;
-        w[i + nth] = t1;
-        acc = fma(t1, t1, fma(t0, t0, acc));
+        const double v0 = fma(-sc, static_cast<double>(c0), w0) * inv_hn;
+        const double v1 = fma(-sc, static_cast<double>(c1), w1) * inv_hn;
+        vnext[i] = v0;
+        vnext[i + nth] = v1;
+        vnextf[i] = static_cast<float>(v0);
+        vnextf[i + nth] = static_cast<float>(v1);
+        vcur[i] = v0;
+        vcur[i + nth] = v1;
     }
     if (i < n) {
         float c0 = 0.0f;
         for (int c = 0; c < nc; ++c) c0 = fmaf(hf[c], Vf[c * n + i], c0);
-        const double t = fma(-sc, static_cast<double>(c0), w[i]);
-        w[i] = t;
-        acc = fma(t, t, acc);
+        const double v = fma(-sc, static_cast<double>(c0), w[i]) * inv_hn;
+        vnext[i] = v;
+        vnextf[i] = static_cast<float>(v);
+        vcur[i] = v;
     }
-    *sq = acc;
 }
 
-// Second Gram-Schmidt update w = w1 - sum_{c <= j} coef[c] V_c and
-// hn = ||w|| (grid reduction; the last block stores it in the state with
-// the column the next basis vector goes to).  The second pass's
-// coefficients are rounding-level corrections: when
-// max |coef| <= 2^-33 ||w1|| (coef[j + 1] = ||w1||^2) the update runs in
-// FP32 on the float copy of the basis, whose error (below
-// 2^-23 sqrt(j + 1) max |coef|) then stays under the FP64 rounding of w1
-// itself; otherwise in FP64.  Every block takes the same decision from the
-// same coefficients.
+// Second Gram-Schmidt update w2 = w1 - sum_{c <= j} coef[c] V_c and the
+// next basis vector v = w2 / ||w2||.  The second pass's coefficients are
+// rounding-level corrections: when max |coef| <= 2^-33 ||w1|| (decided once
+// by gm_coef_kernel, s->low) the update runs in FP32 on the float copy of
+// the basis, whose error (below 2^-23 sqrt(j + 1) max |coef|) then stays
+// under the FP64 rounding of w1 itself; ||w2|| is then known beforehand
+// (||w1||^2 - ||coef||^2, no cancellation at that size) and v is written
+// here.  Otherwise the update runs in FP64, ||w2|| is reduced over the grid
+// (the last block stores it) and gm_next_vector_kernel normalises.
 __global__ void __launch_bounds__(kRedThreads, 4)
-    gm_combine_norm_kernel(int64_t n, const double* __restrict__ V, const float* __restrict__ Vf,
-                           double* __restrict__ w, const double* __restrict__ coef, double* __restrict__ part,
+    gm_combine_norm_kernel(int64_t n, double* __restrict__ V, float* __restrict__ Vf, double* __restrict__ w,
+                           double* __restrict__ vcur, const double* __restrict__ coef, double* __restrict__ part,
                            GmState* s)
 {
     __shared__ double hs[128];
     __shared__ float hf[128];
-    __shared__ double sc_sh;
-    __shared__ int low_sh;
     const int j = s->j, ncols = j + 1;
+    if (s->low) {  // the same for every block
+        for (int c = threadIdx.x; c < ncols; c += blockDim.x) hf[c] = s->hf[c];
+        __syncthreads();
+        gm_correct_rows_f32(Vf, n, hf, ncols, s->sc, w, s->hn_inv, V + (j + 1) * n, Vf + (j + 1) * n, vcur);
+        return;
+    }
     for (int c = threadIdx.x; c < ncols; c += blockDim.x) hs[c] = coef[c];
     __syncthreads();
-    if (threadIdx.x == 0) {
-        double hmax = 0.0;
-        for (int c = 0; c < ncols; ++c) hmax = fmax(hmax, fabs(hs[c]));
-        const bool low = hmax <= ldexp(sqrt(coef[ncols]), -33);  // false on NaN
-        int e = 0;
-        if (low && hmax > 0.0) frexp(hmax, &e);  // hmax < 2^e <= 2 hmax
-        sc_sh = ldexp(1.0, e);
-        low_sh = low;
-    }
-    __syncthreads();
-    const bool low = low_sh != 0;
     double acc;
-    if (low) {
-        const double sc = sc_sh;
-        for (int c = threadIdx.x; c < ncols; c += blockDim.x) hf[c] = static_cast<float>(hs[c] / sc);
-        __syncthreads();
-        gm_correct_rows_f32(Vf, n, hf, ncols, sc, w, &acc);
-    } else {
-        gm_project_rows(V, n, hs, ncols, w, &acc);
-    }
+    gm_project_rows(V, n, hs, ncols, w, &acc);
     grid_sum(acc, part, &s->ticket, [&](double tot) {
         s->hn = sqrt(tot);
         s->hn_inv = 1.0 / s->hn;
         s->next_col = j + 1;
-        s->low_steps += low;
     });
 }
 
@@ -1539,15 +1579,15 @@ __global__ void __launch_bounds__(128)
     gm_givens_block(H, cs, sn, g, hh, s, h, s->j);
 }
 
-// v_{j+1} = w / hn (as w * (1 / hn): one FP64 division per step instead of
-// one per entry) into basis column s->next_col, its float copy and vcur (the
-// next product's input); nothing when hn is zero or not finite (the cycle
-// stops there).
+// After an FP64 second update: v_{j+1} = w / hn (as w * (1 / hn): one FP64
+// division per step instead of one per entry) into basis column
+// s->next_col, its float copy and vcur (the next product's input); nothing
+// when hn is zero or not finite (the cycle stops there).
 __global__ void gm_next_vector_kernel(int64_t n, double* __restrict__ V, float* __restrict__ Vf,
                                       double* __restrict__ vcur, const double* __restrict__ w, const GmState* s)
 {
     const double hn = s->hn;
-    if (!(hn > 0.0) || !(hn < INFINITY)) return;
+    if (s->low || !(hn > 0.0) || !(hn < INFINITY)) return;  // s->low: written by the norm kernel
     const double inv = s->hn_inv;
     double* dst = V + static_cast<int64_t>(s->next_col) * n;
     float* dstf = Vf + static_cast<int64_t>(s->next_col) * n;
@@ -1689,7 +1729,7 @@ int gmres_solve(const gko_matrix* A, int fmt, const double* b, double* x, double
         gm_combine_dots_kernel<<<grid, kRedThreads, 0, cs_>>>(n, V, w, coef, part, ldp, gs);
         gm_coef_kernel<<<m + 2, kRedThreads, 0, cs_>>>(grid, part, ldp, coef2, hh, 1, gs);
         gm_combine_norm_kernel<<<grid, kRedThreads, 0, cs_>>>(
-            n, V, Vf, w, coef2, part + static_cast<int64_t>(std::max(grid, kRedBlocks)) * ldp, gs);
+            n, V, Vf, w, vcur, coef2, part + static_cast<int64_t>(std::max(grid, kRedBlocks)) * ldp, gs);
         gm_next_vector_kernel<<<grid, kRedThreads, 0, cs_>>>(n, V, Vf, vcur, w, gs);
         gm_givens_kernel<<<1, 128, 0, cs_>>>(H, cs, sn, g, hh, gs, h);
         GKO_CUDA(cudaGetLastError());
