@@ -106,6 +106,38 @@ def _sorted_unique(a: np.ndarray) -> np.ndarray:
     return a
 
 
+_TAIL_ROWS = 256  # rows left when _distinct_per_row switches to finishing them one at a time
+
+
+def _finish_rows(active, need, next_j, seen_all, stride, seed, stream, lo, hi, exclude):
+    """Keys completing each row of ``active``: its next ``need[i]`` distinct
+    values of the candidate sequence (from position next_j[i] on, skipping
+    the excluded value and the row's values in ``seen_all``), in sequence
+    order.  Drawing a longer run and keeping the first new values in order
+    gives the same values as drawing the deficit batch by batch."""
+    out = []
+    for i in active:
+        lo_i, hi_i = int(lo[i]), int(hi[i])
+        a, b = np.searchsorted(seen_all, [i * stride, (i + 1) * stride])
+        seen = seen_all[a:b] - i * stride  # offsets the row already has (sorted)
+        left, j = int(need[i]), int(next_j[i])
+        while left > 0:
+            chunk = max(4 * left, 1024)
+            counter = np.uint64(i) * np.uint64(1 << 32) + np.arange(j, j + chunk, dtype=np.uint64)
+            c = uniform_int(seed, stream, counter, lo_i, hi_i)
+            if exclude is not None:
+                c = c[c != exclude[i]]
+            vals, first = np.unique(c - lo_i, return_index=True)
+            vals = vals[np.argsort(first, kind="stable")]  # distinct values in order of first draw
+            vals = vals[~np.isin(vals, seen)]
+            take = vals[:left]
+            out.append(i * stride + take)
+            seen = np.union1d(seen, take)
+            left -= take.size
+            j += chunk
+    return _sorted_unique(np.concatenate(out)) if out else np.zeros(0, dtype=np.int64)
+
+
 def _distinct_per_row(n_rows, lengths, seed, stream, lo, hi, exclude=None):
     """For each row i, the first ``lengths[i]`` distinct integers of the row's
     candidate sequence c_{i,j} = uniform_int(counter = i * 2**32 + j, lo_i, hi_i),
@@ -141,6 +173,13 @@ def _distinct_per_row(n_rows, lengths, seed, stream, lo, hi, exclude=None):
     while True:
         active = np.nonzero(need > 0)[0]
         if active.size == 0:
+            break
+        if active.size <= _TAIL_ROWS:
+            # few rows left (typically long rows collecting their last
+            # columns): finish them row by row, see _finish_rows
+            seen_all = _sorted_unique(np.concatenate([base, extra])) if extra.size else base
+            extra = np.concatenate([extra, _finish_rows(active, need, next_j, seen_all, stride, seed, stream,
+                                                        lo, hi, exclude)])
             break
         keys = draw(active)
         for seen in (base, extra):

@@ -103,7 +103,8 @@ def test_selector_roundtrip(gko, dev):
 
 def _small_sweep(seeds):
     import synthetic
-    return [synthetic.sweep_matrix(s, n_max=3e5, nnz_cap=3e6) for s in seeds]
+    for s in seeds:  # generated as they are used
+        yield synthetic.sweep_matrix(s, n_max=3e5, nnz_cap=3e6)
 
 
 def test_sweep_candidates_match_oracle(gko, dev, orc):

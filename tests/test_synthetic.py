@@ -128,3 +128,23 @@ def test_workloads_deterministic(name):
     a, b = syn.workload(name), syn.workload(name)
     assert a["val"].tobytes() == b["val"].tobytes()
     assert a["col_idx"].tobytes() == b["col_idx"].tobytes()
+
+
+def test_distinct_columns_are_the_first_distinct_draws():
+    """Each row's columns are the first L distinct values of its candidate
+    sequence (counter = row * 2^32 + j): brute force, one draw at a time, on
+    rows that need almost every column of their window (the case the
+    generator finishes row by row) and on ordinary rows."""
+    n_rows, lo, hi = 40, 0, 299
+    lengths = np.array([300 if i % 7 == 0 else (290 if i % 5 == 0 else 3 + i % 11) for i in range(n_rows)])
+    rows, cols = syn._distinct_per_row(n_rows, lengths, 9, syn.S_COL, lo, hi)
+    for i in range(n_rows):
+        got = cols[rows == i]
+        want, j = [], 0
+        while len(want) < lengths[i]:
+            c = int(syn.uniform_int(9, syn.S_COL, np.array([i * (1 << 32) + j], dtype=np.uint64), lo, hi)[0])
+            if c not in want:
+                want.append(c)
+            j += 1
+        assert np.array_equal(got, np.sort(want)), i
+
