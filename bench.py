@@ -613,6 +613,16 @@ def run_extras(gko, torch, dev, st, selector=True, selector_matrices=200):
         res[key] = {"s": round(t, 4), "inner_tol": itol, "outer": info.outer_iterations,
                     "inner_iterations": info.iterations, "rel_residual": info.rel_residual, "status": info.status,
                     "rel_error_vs_x_true": err}
+    # roofline of the Hestenes-Stiefel step on ELL: the product with p.q
+    # (slots + p + q), r -= alpha q (r, q, r'), x += alpha p and
+    # p = r + beta p (x, p, r, x', p'): 12 slots + 10 vector passes of 8n
+    info = M.info("ell")
+    step_bytes = 12.0 * info[6] + 80.0 * n
+    hs = res["fp64_ell"]
+    t_step = hs["s"] / max(hs["iterations"], 1)
+    hbm, _kind = measured_peaks()
+    hs.update({"us_per_iteration": round(t_step * 1e6, 1), "bytes_per_iteration": int(step_bytes),
+               "GBs": round(step_bytes / t_step / 1e9, 1), "frac_hbm": round(step_bytes / t_step / 1e9 / hbm, 3)})
     plain64 = min(res[k]["s"] for k in res if k.startswith("fp64") and "jacobi" not in k)
     res["best_plain_fp64_cg_s"] = plain64
     res["speedup_fp32_vs_plain_fp64_cg"] = round(plain64 / res["fp32"]["s"], 3)
