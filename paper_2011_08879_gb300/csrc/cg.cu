@@ -1223,6 +1223,8 @@ struct GmState {
     uint32_t coef_ticket;
     double sc;
     float hf[128];
+    double beta0;        // ||r|| of the residual the cycle starts from
+    int32_t restart_ok;  // the cycle runs (no convergence, breakdown or maxit yet)
 };
 
 // The block's share of V_c . w for the CNT columns c0 .. c0+CNT-1 into
@@ -1607,6 +1609,7 @@ __global__ void __launch_bounds__(128)
                       const GmState* s)
 {
     extern __shared__ double hs[];
+    if (s->broke) return;  // x stays as it was
     const int j = s->j, m = s->m;
     double* gs = hs + static_cast<size_t>(j) * j;
     for (int t = threadIdx.x; t < j * j; t += blockDim.x) hs[t] = H[(t / j) * m + t % j];
@@ -1629,6 +1632,7 @@ __global__ void __launch_bounds__(kRedThreads)
                        const GmState* s)
 {
     __shared__ double ys[128];
+    if (s->broke) return;
     const int ncols = s->j;
     for (int c = threadIdx.x; c < ncols; c += blockDim.x) ys[c] = y[c];
     __syncthreads();
@@ -1640,15 +1644,39 @@ __global__ void __launch_bounds__(kRedThreads)
     }
 }
 
-// out = w * (1 / s) (s on the host), with its float copy outf
-__global__ void gm_scale_kernel(int64_t n, double* out, float* __restrict__ outf, const double* w, double s)
+// Start of a cycle, from beta^2 = ||r||^2 of the residual r = b - A x
+// (in V_0): the cycle runs unless ||r|| <= tol ||b||, beta is not a number,
+// the previous cycle broke down or maxit steps are spent; if it runs, the
+// cycle's state is reset and g = (beta, 0, ..., 0).  One thread.
+__global__ void gm_restart_kernel(const SolverState* ds, GmState* s, double* __restrict__ g)
 {
-    const double inv = 1.0 / s;
+    const double beta = sqrt(ds->dot_out);
+    s->beta0 = beta;
+    const bool run = !s->broke && beta == beta && !(beta <= s->tol * s->bnorm) && s->total < s->maxit;
+    s->restart_ok = run;
+    if (!run) return;
+    s->j = 0;
+    s->stop = 0;
+    s->hn = 0.0;
+    s->ticket = 0;
+    s->coef_ticket = 0;
+    g[0] = beta;
+    for (int i = 1; i <= s->m; ++i) g[i] = 0.0;
+}
+
+// V_0 = r / beta in place (with its float copy) and into vcur, when the
+// cycle runs
+__global__ void gm_scale_kernel(int64_t n, double* __restrict__ V, float* __restrict__ Vf, double* __restrict__ vcur,
+                                const GmState* s)
+{
+    if (!s->restart_ok) return;
+    const double inv = 1.0 / s->beta0;
     for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
          i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-        const double v = w[i] * inv;
-        out[i] = v;
-        outf[i] = static_cast<float>(v);
+        const double v = V[i] * inv;
+        V[i] = v;
+        Vf[i] = static_cast<float>(v);
+        vcur[i] = v;
     }
 }
 
@@ -1736,50 +1764,44 @@ int gmres_solve(const gko_matrix* A, int fmt, const double* b, double* x, double
         return GKO_OK;
     }));
 
+    // The host synchronises once per cycle: after the cycle's graph, x += V y
+    // and the next cycle's start (residual, its norm, the restart decision,
+    // V_0 and g) are queued behind it and the state is read once.
+    const int bs_smem = m * (m + 1) * static_cast<int>(sizeof(double));
+    GKO_CUDA(smem_limit_once(reinterpret_cast<const void*>(gm_backsub_kernel), bs_smem));
+    auto start_cycle = [&]() -> int {
+        // r = b - A x into V_0, ||r||^2, then the decision and V_0 = r / ||r||
+        GKO_CUDA(cudaMemcpyAsync(V, b, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        GKO_TRY(spmv_fmt(A, fmt, x, V, -1.0, 1.0, st));
+        dot_kernel<double, kDotStore><<<grid, kRedThreads, 0, st>>>(n, V, V, ds, part, 0);
+        gm_restart_kernel<<<1, 1, 0, st>>>(ds, gs, g);
+        gm_scale_kernel<<<grid, kRedThreads, 0, st>>>(n, V, Vf, vcur, gs);
+        GKO_CUDA(cudaGetLastError());
+        GKO_CUDA(cudaMemcpyAsync(&hg, gs, sizeof(GmState), cudaMemcpyDeviceToHost, st));
+        GKO_CUDA(cudaStreamSynchronize(st));
+        return GKO_OK;
+    };
+    GKO_CUDA(cudaMemcpyAsync(gs, &hg, sizeof(GmState), cudaMemcpyHostToDevice, st));
+    GKO_TRY(start_cycle());
     int status = GKO_ERR_NOT_CONVERGED, total = 0;
     double res = -1.0;
     while (true) {
-        // r = b - A x into V_0, beta = ||r||
-        GKO_CUDA(cudaMemcpyAsync(V, b, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
-        GKO_TRY(spmv_fmt(A, fmt, x, V, -1.0, 1.0, st));
-        double beta;
-        GKO_TRY(norm(V, &beta));
-        res = beta / bnorm;
-        if (!(beta == beta)) {
+        total = hg.total;
+        res = hg.beta0 / bnorm;
+        if (hg.broke || !(hg.beta0 == hg.beta0)) {
             status = GKO_ERR_BREAKDOWN;
             break;
         }
-        if (beta <= tol * bnorm) {
+        if (hg.beta0 <= tol * bnorm) {
             status = GKO_OK;
             break;
         }
-        if (total >= maxit) break;
-        gm_scale_kernel<<<grid, kRedThreads, 0, st>>>(n, V, Vf, V, beta);
-        GKO_CUDA(cudaMemcpyAsync(vcur, V, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
-        GKO_CUDA(cudaMemsetAsync(g, 0, (m + 1) * sizeof(double), st));
-        GKO_CUDA(cudaMemcpyAsync(g, &beta, sizeof(double), cudaMemcpyHostToDevice, st));
-        hg.j = 0;
-        hg.total = total;
-        hg.stop = 0;
-        hg.broke = 0;
-        hg.hn = 0.0;
-        hg.ticket = 0;
-        GKO_CUDA(cudaMemcpyAsync(gs, &hg, sizeof(GmState), cudaMemcpyHostToDevice, st));
+        if (!hg.restart_ok) break;  // maxit
         GKO_CUDA(cudaGraphLaunch(gh.exec, st));
-        GKO_CUDA(cudaMemcpyAsync(&hg, gs, sizeof(GmState), cudaMemcpyDeviceToHost, st));
-        GKO_CUDA(cudaStreamSynchronize(st));
-        total = hg.total;
-        if (hg.broke) {
-            status = GKO_ERR_BREAKDOWN;
-            break;
-        }
-        if (hg.j > 0) {
-            const int bs_smem = hg.j * (hg.j + 1) * static_cast<int>(sizeof(double));
-            GKO_CUDA(smem_limit_once(reinterpret_cast<const void*>(gm_backsub_kernel), bs_smem));
-            gm_backsub_kernel<<<1, 128, bs_smem, st>>>(H, g, yv, gs);
-            gm_update_x_kernel<<<grid, kRedThreads, 0, st>>>(n, x, V, yv, gs);
-            GKO_CUDA(cudaGetLastError());
-        }
+        gm_backsub_kernel<<<1, 128, bs_smem, st>>>(H, g, yv, gs);
+        gm_update_x_kernel<<<grid, kRedThreads, 0, st>>>(n, x, V, yv, gs);
+        GKO_CUDA(cudaGetLastError());
+        GKO_TRY(start_cycle());
     }
     GKO_CUDA(cudaStreamSynchronize(st));
     fill_info(info, total, 0, res, status);
