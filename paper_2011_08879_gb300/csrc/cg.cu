@@ -243,45 +243,6 @@ __global__ void diag_inv_kernel(int64_t n, const int32_t* __restrict__ row_ptr, 
     }
 }
 
-// Preconditioned CG step (z = D^-1 r is never stored):
-// x += alpha p; r -= alpha q; rr = r.r (stopping), rz = r.D^-1 r
-// (rho' for beta); stop tests on sqrt(rr) as in r_update_kernel
-__global__ void __launch_bounds__(kRedThreads)
-    pcg_update_kernel(int64_t n, double* __restrict__ x, double* __restrict__ r, const double* __restrict__ p,
-                      const double* __restrict__ q, const double* __restrict__ dinv, SolverState* s, double* part,
-                      cudaGraphConditionalHandle h)
-{
-    if (s->done) return;
-    const double alpha = s->alpha;
-    double rr = 0.0, rz = 0.0;
-    for (int64_t i = blockIdx.x * static_cast<int64_t>(kRedThreads) + threadIdx.x; i < n;
-         i += static_cast<int64_t>(gridDim.x) * kRedThreads) {
-        x[i] = fma(alpha, p[i], x[i]);
-        const double ri = fma(-alpha, q[i], r[i]);
-        r[i] = ri;
-        rr = fma(ri, ri, rr);
-        rz = fma(ri, ri * dinv[i], rz);
-    }
-    grid_sum2(rr, rz, part, &s->ticket, [&](double rr_new, double rho_new) {
-        if (!(rr_new == rr_new) || !(rho_new == rho_new)) {
-            s->status = GKO_ERR_BREAKDOWN;
-            stop_loop(s, h);
-            return;
-        }
-        s->beta = rho_new / s->rho;
-        s->rho = rho_new;
-        s->dot_out = rr_new;
-        if (sqrt(rr_new) <= s->tol * s->stop_ref) {
-            s->conv = 1;
-            s->status = GKO_OK;
-            stop_loop(s, h);
-        } else if (s->iter >= s->maxit) {
-            s->status = GKO_ERR_NOT_CONVERGED;
-            stop_loop(s, h);
-        }
-    });
-}
-
 // p = D^-1 r + beta p (beta_mode 0: the state's beta; 1: beta = 0, the
 // initial direction)
 __global__ void __launch_bounds__(kRedThreads)
@@ -364,6 +325,59 @@ __global__ void __launch_bounds__(kRedThreads)
     for (int64_t i = blockIdx.x * static_cast<int64_t>(kRedThreads) + threadIdx.x; i < n;
          i += static_cast<int64_t>(gridDim.x) * kRedThreads)
         p[i] = initial ? z[i] : fma(beta, p[i], z[i]);
+}
+
+// Jacobi PCG step regrouped like the plain one: r -= alpha q with
+// ||r||^2 (stop tests) and rho' = r.D^-1 r (beta); then x += alpha p and
+// p = D^-1 r + beta p in one pass (pcg_px_update_kernel)
+__global__ void __launch_bounds__(kRedThreads)
+    pcg_r_update_kernel(int64_t n, double* __restrict__ r, const double* __restrict__ q,
+                        const double* __restrict__ dinv, SolverState* s, double* part, cudaGraphConditionalHandle h)
+{
+    if (s->done) return;
+    const double alpha = s->alpha;
+    double rr = 0.0, rz = 0.0;
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(kRedThreads) + threadIdx.x; i < n;
+         i += static_cast<int64_t>(gridDim.x) * kRedThreads) {
+        const double ri = fma(-alpha, q[i], r[i]);
+        r[i] = ri;
+        rr = fma(ri, ri, rr);
+        rz = fma(ri, ri * dinv[i], rz);
+    }
+    grid_sum2(rr, rz, part, &s->ticket, [&](double rr_new, double rho_new) {
+        if (!(rr_new == rr_new) || !(rho_new == rho_new)) {
+            s->status = GKO_ERR_BREAKDOWN;
+            stop_loop(s, h);
+            return;
+        }
+        s->beta = rho_new / s->rho;
+        s->rho = rho_new;
+        s->dot_out = rr_new;
+        if (sqrt(rr_new) <= s->tol * s->stop_ref) {
+            s->conv = 1;
+            s->status = GKO_OK;
+            stop_loop(s, h);
+        } else if (s->iter >= s->maxit) {
+            s->status = GKO_ERR_NOT_CONVERGED;
+            stop_loop(s, h);
+        }
+    });
+}
+
+// x += alpha p; then p = D^-1 r + beta p unless the solve stopped here
+__global__ void __launch_bounds__(kRedThreads)
+    pcg_px_update_kernel(int64_t n, double* __restrict__ x, double* __restrict__ p, const double* __restrict__ r,
+                         const double* __restrict__ dinv, const SolverState* s)
+{
+    if (!s->step_ok) return;
+    const double alpha = s->alpha, beta = s->beta;
+    const bool more = !s->done;
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(kRedThreads) + threadIdx.x; i < n;
+         i += static_cast<int64_t>(gridDim.x) * kRedThreads) {
+        const double pi = p[i];
+        x[i] = fma(alpha, pi, x[i]);
+        if (more) p[i] = fma(beta, pi, r[i] * dinv[i]);
+    }
 }
 
 static int red_grid(int64_t n)
@@ -655,7 +669,7 @@ static int cg_solve_impl(const gko_matrix* A, int fmt, const double* b, double* 
     }
 
     // plain CG on ELL: the product carries p.q (persistent grid, its own partials)
-    const bool fused_pq = !bj && !jacobi && fmt == GKO_FMT_ELL && A->ell.K > 0;
+    const bool fused_pq = !bj && fmt == GKO_FMT_ELL && A->ell.K > 0;
     int pq_grid = 0;
     double* pq_part = part;
     if (fused_pq) {
@@ -677,8 +691,8 @@ static int cg_solve_impl(const gko_matrix* A, int fmt, const double* b, double* 
             bj_z_launch(bj, r, z, ds, part, grid, h, kBjStep, 0, cs);
             zupdate_kernel<<<grid, kRedThreads, 0, cs>>>(n, p, z, ds, 0, 0);
         } else if (jacobi) {
-            pcg_update_kernel<<<grid, kRedThreads, 0, cs>>>(n, x, r, p, q, dinv, ds, part, h);
-            pcg_pupdate_kernel<<<grid, kRedThreads, 0, cs>>>(n, p, r, dinv, ds, 0, 0);
+            pcg_r_update_kernel<<<grid, kRedThreads, 0, cs>>>(n, r, q, dinv, ds, part, h);
+            pcg_px_update_kernel<<<grid, kRedThreads, 0, cs>>>(n, x, p, r, dinv, ds);
         } else {
             // 2 * kRedBlocks partials fit the wider grid of the vector kernels
             const int vgrid = static_cast<int>(
