@@ -296,7 +296,7 @@ static void launch_subwarp(const gko_matrix* A, const double* x, double* y, doub
 // issued, then two FMA chains.  With x gathered at random from L2 (skewed,
 // unstructured matrices) each lane thus keeps four gathers in flight
 // instead of one per memory round trip.
-template <int S>
+template <int S, bool kL2 = false>
 __device__ __forceinline__ void fma4(int32_t k, int32_t k1, const int32_t* __restrict__ col,
                                      const double* __restrict__ val, const double* __restrict__ x, double& a0,
                                      double& a1)
@@ -310,7 +310,7 @@ __device__ __forceinline__ void fma4(int32_t k, int32_t k1, const int32_t* __res
         v[u] = kk < k1 ? val[kk] : 0.0;
     }
 #pragma unroll
-    for (int u = 0; u < 4; ++u) xv[u] = c[u] >= 0 ? ldg(x + c[u]) : 0.0;
+    for (int u = 0; u < 4; ++u) xv[u] = c[u] >= 0 ? (kL2 ? __ldcg(x + c[u]) : ldg(x + c[u])) : 0.0;
     if (c[0] >= 0) a0 = fma(v[0], xv[0], a0);
     if (c[1] >= 0) a1 = fma(v[1], xv[1], a1);
     if (c[2] >= 0) a0 = fma(v[2], xv[2], a0);
@@ -323,7 +323,7 @@ __device__ __forceinline__ void fma4(int32_t k, int32_t k1, const int32_t* __res
 // (power-law rows over 2M columns) every gather is a separate 32-byte L2
 // sector; GB300 serves such gathers at ~270 G/s (one per SM clock), which
 // bounds those products, not HBM bandwidth.
-template <int SW, bool kAlpha, bool kBeta>
+template <int SW, bool kAlpha, bool kBeta, bool kL2>
 __device__ __forceinline__ void task_rows(const int32_t* __restrict__ rows, int count,
                                           const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
                                           const double* __restrict__ val, const double* __restrict__ x,
@@ -340,14 +340,16 @@ __device__ __forceinline__ void task_rows(const int32_t* __restrict__ rows, int 
         double a0 = 0.0, a1 = 0.0;
         if (q < count) {
             const int32_t k1 = row_ptr[r + 1];
-            for (int32_t k = row_ptr[r] + lane; k < k1; k += 4 * SW) fma4<SW>(k, k1, col, val, x, a0, a1);
+            for (int32_t k = row_ptr[r] + lane; k < k1; k += 4 * SW) fma4<SW, kL2>(k, k1, col, val, x, a0, a1);
         }
         const double acc = G::reduce_sum(a0 + a1);
         if (q < count && lane == 0) seg_store<kAlpha, kBeta>(y, r, acc, alpha, beta);
     }
 }
 
-template <bool kAlpha, bool kBeta>
+// kL2: gathers of x through L2 only (ld.global.cg), for matrices whose
+// columns are spread over the whole vector: L1 would rarely reuse them
+template <bool kAlpha, bool kBeta, bool kL2>
 __global__ void __launch_bounds__(256)
     csr_binned_kernel(const int4* __restrict__ tasks, const int32_t* __restrict__ bin_rows,
                       const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
@@ -358,17 +360,17 @@ __global__ void __launch_bounds__(256)
     const int4 t = tasks[blockIdx.x];
     const int32_t* rows = bin_rows + t.x;
     switch (t.z) {
-        case 0: task_rows<1, kAlpha, kBeta>(rows, t.y, row_ptr, col, val, x, y, alpha, beta); break;
-        case 1: task_rows<2, kAlpha, kBeta>(rows, t.y, row_ptr, col, val, x, y, alpha, beta); break;
-        case 2: task_rows<4, kAlpha, kBeta>(rows, t.y, row_ptr, col, val, x, y, alpha, beta); break;
-        case 3: task_rows<8, kAlpha, kBeta>(rows, t.y, row_ptr, col, val, x, y, alpha, beta); break;
-        case 4: task_rows<32, kAlpha, kBeta>(rows, t.y, row_ptr, col, val, x, y, alpha, beta); break;
+        case 0: task_rows<1, kAlpha, kBeta, kL2>(rows, t.y, row_ptr, col, val, x, y, alpha, beta); break;
+        case 1: task_rows<2, kAlpha, kBeta, kL2>(rows, t.y, row_ptr, col, val, x, y, alpha, beta); break;
+        case 2: task_rows<4, kAlpha, kBeta, kL2>(rows, t.y, row_ptr, col, val, x, y, alpha, beta); break;
+        case 3: task_rows<8, kAlpha, kBeta, kL2>(rows, t.y, row_ptr, col, val, x, y, alpha, beta); break;
+        case 4: task_rows<32, kAlpha, kBeta, kL2>(rows, t.y, row_ptr, col, val, x, y, alpha, beta); break;
         default: {  // one long row, the whole CTA
             const int32_t r = rows[0];
             const int32_t k0 = row_ptr[r], k1 = row_ptr[r + 1];
             double a0 = 0.0, a1 = 0.0;
             for (int32_t k = k0 + static_cast<int32_t>(threadIdx.x); k < k1; k += 1024)
-                fma4<256>(k, k1, col, val, x, a0, a1);
+                fma4<256, kL2>(k, k1, col, val, x, a0, a1);
             const double s = subwarp<32>::reduce_sum(a0 + a1);
             if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
             __syncthreads();
@@ -393,8 +395,12 @@ static void launch_binned(const gko_matrix* A, const double* x, double* y, doubl
     const bool a = alpha != 1.0, b = beta != 0.0;
     if (c.n_bin_tasks > 0) {  // tasks <= rows < 2^31
         const unsigned g = static_cast<unsigned>(c.n_bin_tasks);
-#define GKO_BT(KA, KB) \
-    csr_binned_kernel<KA, KB><<<g, 256, 0, st>>>(c.bin_tasks, c.bin_rows, c.row_ptr, c.col, c.val, x, y, alpha, beta)
+        const bool l2 = coo_entries_per_thread(A) == kSegPCoo;  // scattered columns (the COO kernel's test)
+#define GKO_BT(KA, KB)                                                                                                  \
+    (l2 ? csr_binned_kernel<KA, KB, true><<<g, 256, 0, st>>>(c.bin_tasks, c.bin_rows, c.row_ptr, c.col, c.val, x, y, \
+                                                              alpha, beta)                                              \
+        : csr_binned_kernel<KA, KB, false><<<g, 256, 0, st>>>(c.bin_tasks, c.bin_rows, c.row_ptr, c.col, c.val, x, y, \
+                                                               alpha, beta))
         if (a && b)
             GKO_BT(true, true);
         else if (a)
