@@ -482,6 +482,31 @@ def _time_call(torch, fn):
     return time.perf_counter() - t0, r
 
 
+def run_batched_layouts(names):
+    """Profiling run: the 4,096-system batched CG solved once in each named
+    layout (one kernel launch each, no warm-up), its wall time and status
+    printed as one JSON line."""
+    import torch
+    import paper_2011_08879_gb300 as gko
+    dev = torch.device("cuda:0")
+    torch.cuda.set_device(dev)
+    st = torch.cuda.Stream()
+    B = load_workload("batched_4096")
+    G = gko.Batch(B, stream=st)
+    rhs = torch.from_numpy(B["rhs"]).to(dev)
+    out = {}
+    worst = 0
+    for name in names:
+        code = gko.binding.batch_layout_code(name)
+        x = torch.zeros_like(rhs)
+        t, (s, infos) = _time_call(torch, lambda: G.cg(rhs, x, tol=1e-10, maxit=1000, block_size=code, stream=st))
+        out[name] = {"s": round(t, 5), "status": s, "max_rel_residual": max(i.rel_residual for i in infos)}
+        worst = worst or s
+    print(json.dumps({"batched_cg_4096_layouts": out}))
+    if worst:
+        sys.exit(1)
+
+
 def run_selector_extra(gko, torch, n_test=200, workers=None):
     """Held-out evaluation of the committed selector on this GPU: the 200
     held-out sweep matrices (seeds 3000..3199) are generated again, every
@@ -682,15 +707,17 @@ def run_extras(gko, torch, dev, st, selector=True, selector_matrices=200):
         x = torch.zeros_like(rhs)
         t, (s, infos) = _time_call(torch, lambda: G.cg(rhs, x, tol=1e-10, maxit=1000, stream=st))
     its = [i.iterations for i in infos]
-    # the other layout of the autotuner's space, timed on its own for the record
+    # other layouts of the autotuner's space, timed on their own for the record
     alt = {}
-    for bs_alt in (64, -128, -256):
+    P, PQ = gko.binding.BATCH_SHARED_P, gko.binding.BATCH_SHARED_PQ
+    for bs_alt in (64, 128, -128, P | 64, P | 128, PQ | 128, P | 256):
         for _ in range(2):
             x2 = torch.zeros_like(rhs)
             t_alt, _r = _time_call(torch, lambda: G.cg(rhs, x2, tol=1e-10, maxit=1000, block_size=bs_alt, stream=st))
-        alt[str(bs_alt)] = round(t_alt, 5)
+        alt[gko.binding.batch_layout(bs_alt)] = round(t_alt, 5)
     # roofline of the batched solve: every iteration re-streams the system's
-    # CSR (values + indices + row pointers); vectors live in shared memory.
+    # CSR (values + indices + row pointers); vectors live in shared memory
+    # or a per-block scratch, depending on the layout (not counted).
     # FP64 work per iteration and row: the product's FMAs plus five vector
     # FMAs (p.q, x, r, r.r, p)
     ro, rp = B["row_off"], B["row_ptr"].astype(np.int64)
@@ -699,11 +726,11 @@ def run_extras(gko, torch, dev, st, selector=True, selector_matrices=200):
     its_a = np.array(its, dtype=np.float64)
     mat_bytes = float(np.sum(its_a * (12.0 * nnz_s + 4.0 * (n_s + 1))))
     fmas = float(np.sum(its_a * (nnz_s + 5.0 * n_s)))
-    out["batched_cg_4096"] = {"s": round(t, 5), "status": s, "block_size": best,
+    out["batched_cg_4096"] = {"s": round(t, 5), "status": s, "layout": gko.binding.batch_layout(best),
                               "max_rel_residual": max(i.rel_residual for i in infos),
                               "iterations_mean": round(float(np.mean(its)), 2),
                               "matrix_GBs": round(mat_bytes / t / 1e9, 1),
-                              "s_by_block_size": alt,
+                              "s_by_layout": alt,
                               "fp64_tfma_s": round(fmas / t / 1e12, 4)}
     # hardware ceilings of this GPU (FP64 / FP32 FMA rate, random gathers)
     f64, f32, g16 = gko.binding.gko_measure_ceilings(1 << 21, st)
@@ -797,6 +824,9 @@ def main():
     ap.add_argument("--no-selector", action="store_true", help="skip the selector's held-out re-timing")
     ap.add_argument("--selector-matrices", type=int, default=200,
                     help="held-out matrices re-timed for the selector's regret (seeds 3000 onwards)")
+    ap.add_argument("--batched", default="",
+                    help="profiling run: only the 4,096-system batched CG, once per layout of this comma list "
+                         "(e.g. shared_xrpq/64,shared_p/128)")
     ap.add_argument("--sweep", default="full", choices=["full", "small"],
                     help="small: quarter-size matrices of the same four kinds (profiling captures)")
     args = ap.parse_args()
@@ -804,6 +834,8 @@ def main():
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
         run_reference(args)
+    elif args.batched:
+        run_batched_layouts(args.batched.split(","))
     else:
         run_gpu(args)
 

@@ -474,6 +474,10 @@ int gko_batch_create(int64_t count, const int64_t* row_off, const int32_t* row_p
                      gko_batch** out);
 int gko_batch_destroy(gko_batch* B);
 
+/* Layout flags of gko_cg_batched's block_size (OR'ed with the block size). */
+#define GKO_BATCH_SHARED_P 0x10000
+#define GKO_BATCH_SHARED_PQ 0x20000
+
 /* Solve all systems of the batch by CG, one thread block per system taken
  * from a device work queue (largest systems first), launched as one
  * persistent kernel inside a CUDA graph (the instantiated graph is kept in
@@ -482,7 +486,12 @@ int gko_batch_destroy(gko_batch* B);
  * of the system in shared memory; -128, -256, -512 or -1024: that many
  * threads with 1024 / |block_size| rows each, x, r and A p of a thread's
  * rows in registers and only p in shared memory (systems of at most 1024
- * rows); 0 = the autotuned choice.  b, x device vectors of row_off[count]
+ * rows); GKO_BATCH_SHARED_P | bs or GKO_BATCH_SHARED_PQ | bs (bs = 32, 64,
+ * 128 or 256): bs threads with only p (or p and A p) in shared memory and
+ * the rest of the system's vectors in a device scratch the batch allocates
+ * and keeps (4 - 1 or 4 - 2 vectors of max_rows doubles per resident
+ * block), so that more systems share an SM; 0 = the autotuned choice.
+ * b, x device vectors of row_off[count]
  * entries (x: initial guess in, solution out).  infos: host array of count
  * entries or NULL.  Returns the worst status.  Synchronises the stream. */
 int gko_cg_batched(gko_batch* B, const double* b, double* x, double tol, int maxit, int block_size,
@@ -490,8 +499,9 @@ int gko_cg_batched(gko_batch* B, const double* b, double* x, double tol, int max
 
 /* Run the batched-CG autotuner: times every candidate launch on this batch
  * (the block sizes and layouts of gko_cg_batched: 64 .. 1024 with the
- * vectors in shared memory, and, when no system exceeds 1024 rows, -128 ..
- * -1024 with the rows' vectors in registers) and keeps the fastest for
+ * vectors in shared memory, the split layouts GKO_BATCH_SHARED_P / _PQ |
+ * 32 .. 256, and, when no system exceeds 1024 rows, -128 .. -1024 with the
+ * rows' vectors in registers) and keeps the fastest for
  * block_size 0.  *best receives it. */
 int gko_batch_autotune(gko_batch* B, const double* b, double* x, double tol, int maxit,
                        void* stream, int* best);

@@ -25,6 +25,34 @@ FORMATS = {"csr": FMT_CSR, "coo": FMT_COO, "ell": FMT_ELL, "sellp": FMT_SELLP, "
  ERR_NOT_CONVERGED, ERR_BREAKDOWN, ERR_INVALID_MATRIX, ERR_TIMEOUT, ERR_CUDA) = range(11)
 # value types
 F64, F32, BF16 = 0, 1, 2
+# batched-CG layout flags (OR'ed with the block size)
+BATCH_SHARED_P, BATCH_SHARED_PQ = 0x10000, 0x20000
+
+
+def batch_layout(code: int) -> str:
+    """Readable name of a gko_cg_batched block_size code."""
+    if code == 0:
+        return "autotuned"
+    if code < 0:
+        return "registers/%d" % -code
+    if code & BATCH_SHARED_P:
+        return "shared_p/%d" % (code & 0xFFFF)
+    if code & BATCH_SHARED_PQ:
+        return "shared_pq/%d" % (code & 0xFFFF)
+    return "shared_xrpq/%d" % code
+
+
+def batch_layout_code(name: str) -> int:
+    """Inverse of batch_layout: "shared_p/128" -> BATCH_SHARED_P | 128."""
+    kind, _, bs = name.partition("/")
+    flags = {"shared_p": BATCH_SHARED_P, "shared_pq": BATCH_SHARED_PQ, "shared_xrpq": 0, "registers": -1}
+    if kind == "autotuned" and not bs:
+        return 0
+    if kind not in flags or not bs.isdigit():
+        raise ValueError("unknown batched layout %r" % name)
+    return -int(bs) if flags[kind] == -1 else flags[kind] | int(bs)
+
+
 # kernel configurations
 (CFG_DEFAULT, CFG_CSR_SUBWARP_1, CFG_CSR_SUBWARP_2, CFG_CSR_SUBWARP_4, CFG_CSR_SUBWARP_8, CFG_CSR_SUBWARP_16,
  CFG_CSR_SUBWARP_32, CFG_CSR_NNZSPLIT, CFG_CSR_BANDED, CFG_CSR_ROWBLOCK, CFG_CSR_BINNED) = range(11)

@@ -1,12 +1,13 @@
 // Batched CG: many independent small SPD systems solved by one persistent
 // kernel.  Each thread block repeatedly takes the next system from a device
 // work queue (systems ordered by decreasing size, so the largest start
-// first and the tail is short), keeps x, r, p, q of that system in shared
-// memory, streams the system's CSR through L1/L2 every step and runs the
-// Hestenes-Stiefel recurrence (the Krylov solver of the paper's Sec. 6.2)
-// to its own tolerance.  Dots are block-wide reductions in a fixed order;
-// there is no inter-block communication except the queue ticket.  The
-// queue reset and the kernel are replayed as one CUDA graph.
+// first and the tail is short), keeps the system's vectors in shared
+// memory, registers or a per-block scratch (the layouts below), streams the
+// system's CSR through L1/L2 every step and runs the Hestenes-Stiefel
+// recurrence (the Krylov solver of the paper's Sec. 6.2) to its own
+// tolerance.  Dots are block-wide reductions in a fixed order; there is no
+// inter-block communication except the queue ticket.  The queue reset and
+// the kernel are replayed as one CUDA graph.
 #include <algorithm>
 #include <cmath>
 #include <numeric>
@@ -32,37 +33,90 @@ __device__ __forceinline__ double block_dot_sum(double v, double* red)
     return t;
 }
 
-// q = A v for the rows of one system (thread per row, local columns).
+
+// One row of q = A v for a system (thread per row, local columns).
 // (Taking the rows by decreasing length, so that a warp's rows end together,
 // was measured slower: 4.96 against 3.62 ms for 4,096 systems, the warps'
 // loads of the matrix no longer falling on neighbouring rows.)
-__device__ __forceinline__ void sys_spmv(int n, int bs, const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
-                                         const double* __restrict__ val, int32_t base, const double* v, double* q)
+__device__ __forceinline__ double sys_row_dot(const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
+                                              const double* __restrict__ val, int32_t base, int i, const double* v)
 {
-    for (int i = threadIdx.x; i < n; i += bs) {
-        double acc = 0.0;
-        const int32_t k1 = rp[i + 1] - base;
-        for (int32_t k = rp[i] - base; k < k1; ++k) acc = fma(val[k], v[col[k]], acc);
-        q[i] = acc;
-    }
+    double acc = 0.0;
+    const int32_t k1 = rp[i + 1] - base;
+    for (int32_t k = rp[i] - base; k < k1; ++k) acc = fma(val[k], v[col[k]], acc);
+    return acc;
 }
 
+// Sum of part[0 .. BS), called by warp 0 alone: lane l adds part[l],
+// part[l + 32], ..., then the warp's tree; the total lands in lane 0.
+// FP64 work is charged per warp instruction, whatever the active lanes, so
+// one warp adding for the block (BS / 32 + 4 additions) costs the FP64
+// pipe 1 / (BS / 32) of every warp reducing its own share and then all
+// warps adding the warp totals.
 template <int BS>
+__device__ __forceinline__ double warp0_sum(const double* part)
+{
+    double s = part[threadIdx.x];
+#pragma unroll
+    for (int k = 1; k < BS / 32; ++k) s += part[threadIdx.x + 32 * k];
+    for (int o = 16; o; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    return s;
+}
+
+// Block-wide sum of every thread's v, returned to every thread.
+template <int BS>
+__device__ __forceinline__ double block_sum_bcast(double v, double* part, double* bc)
+{
+    part[threadIdx.x] = v;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        const double s = warp0_sum<BS>(part);
+        if (threadIdx.x == 0) *bc = s;
+    }
+    __syncthreads();
+    return *bc;
+}
+
+enum { kStepGo = 0, kStepBreakdown = 1, kStepCheck = 2 };
+
+// Layouts by the number NS of the system's vectors in shared memory:
+//   NS = 4: x, r, p and q = A p all in shared memory (32 bytes per row);
+//   NS = 2: p and q in shared memory, x and r in this block's slice of a
+//           global scratch;
+//   NS = 1: only p, which the product gathers, in shared memory; x, r and
+//           q in the scratch.
+// Thread t reads and writes only the entries of x, r and q of its own rows
+// t, t + BS, ..., so no barrier guards them and scratch entries stay close
+// in L1/L2; with 16 or 8 bytes of shared memory per row, 2x or 4x as many
+// systems share an SM.  The product and p.q are one pass over the rows.
+// Each step's scalars (alpha, beta, the breakdown and stopping tests) are
+// derived once, by thread 0 after warp 0 has added the block's partials,
+// and read by the other threads from shared memory.
+template <int BS, int NS>
 __global__ void __launch_bounds__(BS)
     batched_cg_kernel(int64_t count, const int64_t* __restrict__ row_off, const int32_t* __restrict__ row_ptr,
                       const int32_t* __restrict__ col_all, const double* __restrict__ val_all,
                       const int32_t* __restrict__ order, const int32_t* __restrict__ perm, int32_t* queue,
                       const double* __restrict__ b_all, double* __restrict__ x_all, double tol, int maxit,
                       double* __restrict__ res_out, int32_t* __restrict__ it_out, int32_t* __restrict__ st_out,
-                      int max_rows)
+                      double* scratch, int max_rows)
 {
+    static_assert(NS == 1 || NS == 2 || NS == 4, "1, 2 or 4 vectors in shared memory");
     extern __shared__ __align__(16) double sm[];
-    double* xs = sm;
-    double* rs = xs + max_rows;
-    double* ps = rs + max_rows;
-    double* qs = ps + max_rows;
-    __shared__ double red[BS / 32];
-    __shared__ int s_next;
+    double* ps = sm;
+    double *qv, *xg, *rg;
+    if (NS == 4) {
+        qv = sm + max_rows;
+        xg = sm + 2 * max_rows;
+        rg = sm + 3 * max_rows;
+    } else {
+        xg = scratch + static_cast<size_t>(blockIdx.x) * (4 - NS) * max_rows;
+        rg = xg + max_rows;
+        qv = NS == 2 ? sm + max_rows : rg + max_rows;
+    }
+    __shared__ double part[BS];
+    __shared__ double s_alpha, s_beta, s_bc;
+    __shared__ int s_code, s_next;
 
     while (true) {
         __syncthreads();
@@ -83,12 +137,13 @@ __global__ void __launch_bounds__(BS)
 
         double bb = 0.0;
         for (int i = threadIdx.x; i < n; i += BS) {
-            xs[i] = x[pm[i]];
+            const double xi = x[pm[i]];
+            xg[i] = xi;
+            ps[i] = xi;  // staged for the gathers of A x
             const double bi = b[pm[i]];
             bb = fma(bi, bi, bb);
         }
-        const double bnorm = sqrt(block_dot_sum<BS>(bb, red));
-        __syncthreads();
+        const double bnorm = sqrt(block_sum_bcast<BS>(bb, part, &s_bc));  // its barriers also complete ps
         if (bnorm == 0.0) {
             for (int i = threadIdx.x; i < n; i += BS) x[pm[i]] = 0.0;
             if (threadIdx.x == 0) {
@@ -98,60 +153,88 @@ __global__ void __launch_bounds__(BS)
             }
             continue;
         }
-        // r = b - A x, p = r
-        sys_spmv(n, BS, rp, col, val, base, xs, qs);
-        __syncthreads();
+        // r = b - A x; p = r once every gather of x is done
         double rr = 0.0;
         for (int i = threadIdx.x; i < n; i += BS) {
-            const double ri = b[pm[i]] - qs[i];
-            rs[i] = ri;
-            ps[i] = ri;
+            const double ri = b[pm[i]] - sys_row_dot(rp, col, val, base, i, ps);
+            rg[i] = ri;
             rr = fma(ri, ri, rr);
         }
-        double rho = block_dot_sum<BS>(rr, red);
+        double rho = block_sum_bcast<BS>(rr, part, &s_bc);  // after this, kept up to date by thread 0 only
+        for (int i = threadIdx.x; i < n; i += BS) ps[i] = rg[i];
         int status = GKO_ERR_NOT_CONVERGED, iter = 0, checks = 0;
         double true_res = -1.0;
         // ||r|| <= tol ||b|| tested as rho <= (tol ||b||)^2: no FP64 square
-        // root per step (FP64 work is charged per warp instruction)
+        // root per step
         const double thr2 = (tol * bnorm) * (tol * bnorm);
         bool stop = rho <= thr2;
         if (stop) status = GKO_OK;
         while (!stop && iter < maxit) {
-            __syncthreads();
-            sys_spmv(n, BS, rp, col, val, base, ps, qs);
-            __syncthreads();
+            __syncthreads();  // p complete before the product
             double pq = 0.0;
-            for (int i = threadIdx.x; i < n; i += BS) pq = fma(ps[i], qs[i], pq);
-            pq = block_dot_sum<BS>(pq, red);
+            for (int i = threadIdx.x; i < n; i += BS) {
+                const double q = sys_row_dot(rp, col, val, base, i, ps);
+                qv[i] = q;
+                pq = fma(ps[i], q, pq);
+            }
+            part[threadIdx.x] = pq;
+            __syncthreads();
+            if (threadIdx.x < 32) {
+                const double t = warp0_sum<BS>(part);
+                if (threadIdx.x == 0) {
+                    const bool bad = !(t > 0.0);
+                    s_code = bad ? kStepBreakdown : kStepGo;
+                    if (!bad) s_alpha = rho / t;
+                }
+            }
+            __syncthreads();
             ++iter;
-            if (!(pq > 0.0)) {
+            if (s_code == kStepBreakdown) {
                 status = GKO_ERR_BREAKDOWN;
                 break;
             }
-            const double alpha = rho / pq;
+            const double alpha = s_alpha;
             double rn = 0.0;
             for (int i = threadIdx.x; i < n; i += BS) {
-                xs[i] = fma(alpha, ps[i], xs[i]);
-                const double ri = fma(-alpha, qs[i], rs[i]);
-                rs[i] = ri;
+                xg[i] = fma(alpha, ps[i], xg[i]);
+                const double ri = fma(-alpha, qv[i], rg[i]);
+                rg[i] = ri;
                 rn = fma(ri, ri, rn);
             }
-            const double rho_new = block_dot_sum<BS>(rn, red);
-            if (!(rho_new == rho_new)) {
+            part[threadIdx.x] = rn;
+            __syncthreads();  // also: every gather of p done
+            if (threadIdx.x < 32) {
+                const double u = warp0_sum<BS>(part);
+                if (threadIdx.x == 0) {
+                    if (!(u == u)) {
+                        s_code = kStepBreakdown;
+                    } else {
+                        s_code = u <= thr2 ? kStepCheck : kStepGo;
+                        s_beta = u / rho;
+                        rho = u;
+                    }
+                }
+            }
+            __syncthreads();
+            const int code = s_code;
+            if (code == kStepBreakdown) {
                 status = GKO_ERR_BREAKDOWN;
                 break;
             }
-            if (rho_new <= thr2) {
-                // confirm with the true residual b - A x
-                __syncthreads();
-                sys_spmv(n, BS, rp, col, val, base, xs, qs);
+            if (code == kStepCheck) {
+                // confirm with the true residual: p parked in q's rows, x staged in ps
+                for (int i = threadIdx.x; i < n; i += BS) {
+                    qv[i] = ps[i];
+                    ps[i] = xg[i];
+                }
                 __syncthreads();
                 double tt = 0.0;
                 for (int i = threadIdx.x; i < n; i += BS) {
-                    const double ti = b[pm[i]] - qs[i];
+                    const double ti = b[pm[i]] - sys_row_dot(rp, col, val, base, i, ps);
                     tt = fma(ti, ti, tt);
                 }
-                true_res = sqrt(block_dot_sum<BS>(tt, red)) / bnorm;
+                true_res = sqrt(block_sum_bcast<BS>(tt, part, &s_bc)) / bnorm;  // every gather of x done
+                for (int i = threadIdx.x; i < n; i += BS) ps[i] = qv[i];
                 ++checks;
                 if (true_res <= tol) {
                     status = GKO_OK;
@@ -160,23 +243,21 @@ __global__ void __launch_bounds__(BS)
                 if (checks >= 4) break;
                 true_res = -1.0;
             }
-            const double beta = rho_new / rho;
-            rho = rho_new;
-            __syncthreads();
-            for (int i = threadIdx.x; i < n; i += BS) ps[i] = fma(beta, ps[i], rs[i]);
+            const double beta = s_beta;
+            for (int i = threadIdx.x; i < n; i += BS) ps[i] = fma(beta, ps[i], rg[i]);
         }
-        __syncthreads();
         if (true_res < 0.0) {
-            sys_spmv(n, BS, rp, col, val, base, xs, qs);
+            __syncthreads();  // no thread still gathers p
+            for (int i = threadIdx.x; i < n; i += BS) ps[i] = xg[i];
             __syncthreads();
             double tt = 0.0;
             for (int i = threadIdx.x; i < n; i += BS) {
-                const double ti = b[pm[i]] - qs[i];
+                const double ti = b[pm[i]] - sys_row_dot(rp, col, val, base, i, ps);
                 tt = fma(ti, ti, tt);
             }
-            true_res = sqrt(block_dot_sum<BS>(tt, red)) / bnorm;
+            true_res = sqrt(block_sum_bcast<BS>(tt, part, &s_bc)) / bnorm;
         }
-        for (int i = threadIdx.x; i < n; i += BS) x[pm[i]] = xs[i];
+        for (int i = threadIdx.x; i < n; i += BS) x[pm[i]] = xg[i];
         if (threadIdx.x == 0) {
             res_out[sys] = true_res;
             it_out[sys] = iter;
@@ -185,13 +266,47 @@ __global__ void __launch_bounds__(BS)
     }
 }
 
+// Launch of the layouts above.  NS < 4 needs a scratch of (4 - NS) vectors
+// of max_rows doubles per resident block: prepare = true only sizes it
+// (before a graph capture, where no allocation may run); prepare = false
+// launches.
+template <int BS, int NS>
+static int launch_batched(gko_batch* B, const double* b, double* x, double tol, int maxit, cudaStream_t st,
+                          bool prepare)
+{
+    const size_t smem = NS * static_cast<size_t>(B->max_rows) * sizeof(double);
+    GKO_CUDA(smem_limit_once(reinterpret_cast<const void*>(batched_cg_kernel<BS, NS>), static_cast<int>(smem)));
+    int per_sm = 0;
+    const int sms = device_sm_count();
+    GKO_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_cg_kernel<BS, NS>, BS, smem));
+    if (per_sm < 1) return fail(GKO_ERR_INVALID_ARG, "batched CG: block does not fit on an SM");
+    const int64_t grid = std::max<int64_t>(std::min<int64_t>(static_cast<int64_t>(per_sm) * sms, B->count), 1);
+    const int64_t need = NS == 4 ? 0 : grid * (4 - NS) * static_cast<int64_t>(B->max_rows);
+    if (prepare) {
+        if (B->scratch_len >= need) return GKO_OK;
+        dev_free(B->scratch);  // synchronises: no earlier solve still uses it
+        B->scratch = nullptr;
+        B->scratch_len = 0;
+        GKO_TRY(dev_alloc(&B->scratch, need));
+        B->scratch_len = need;
+        return GKO_OK;
+    }
+    if (B->scratch_len < need) return fail(GKO_ERR_INVALID_ARG, "batched CG: scratch not prepared");
+    GKO_CUDA(cudaMemsetAsync(B->queue, 0, sizeof(int32_t), st));
+    batched_cg_kernel<BS, NS><<<static_cast<unsigned>(grid), BS, smem, st>>>(
+        B->count, B->row_off, B->row_ptr, B->col, B->val, B->order, B->perm, B->queue, b, x, tol, maxit, B->res, B->iters,
+        B->status, B->scratch, B->max_rows);
+    GKO_CUDA(cudaGetLastError());
+    return GKO_OK;
+}
+
 // ---------------------------------------------------------------------------
 // Register-resident variant: thread t owns rows t, t + BS, ..., t + (R-1) BS
 // of its system (R rows per thread, BS * R >= the largest system), keeps x,
 // r and (A p) of those rows in registers and only the direction p, which
 // the product gathers, in shared memory (8 bytes per row instead of 32), so
 // more blocks share an SM.  Same recurrence, stops and outputs as
-// batched_cg_kernel; the autotuner times both layouts.
+// batched_cg_kernel; the autotuner times every layout.
 
 template <int BS, int R>
 __device__ __forceinline__ void sys_spmv_reg(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
@@ -403,46 +518,38 @@ static int launch_batched_reg(gko_batch* B, const double* b, double* x, double t
     return GKO_OK;
 }
 
-struct BatchLaunch {
-    const void* fn;
-    int bs;
-};
-
-template <int BS>
-static int launch_batched(gko_batch* B, const double* b, double* x, double tol, int maxit, cudaStream_t st)
-{
-    const size_t smem = 4 * static_cast<size_t>(B->max_rows) * sizeof(double);
-    GKO_CUDA(smem_limit_once(reinterpret_cast<const void*>(batched_cg_kernel<BS>), static_cast<int>(smem)));
-    int per_sm = 0;
-    const int sms = device_sm_count();
-    GKO_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_cg_kernel<BS>, BS, smem));
-    if (per_sm < 1) return fail(GKO_ERR_INVALID_ARG, "batched CG: block does not fit on an SM");
-    const int64_t grid = std::min<int64_t>(static_cast<int64_t>(per_sm) * sms, B->count);
-    GKO_CUDA(cudaMemsetAsync(B->queue, 0, sizeof(int32_t), st));
-    batched_cg_kernel<BS><<<static_cast<unsigned>(std::max<int64_t>(grid, 1)), BS, smem, st>>>(
-        B->count, B->row_off, B->row_ptr, B->col, B->val, B->order, B->perm, B->queue, b, x, tol, maxit, B->res, B->iters,
-        B->status, B->max_rows);
-    GKO_CUDA(cudaGetLastError());
-    return GKO_OK;
-}
 
 // Launch configurations: block sizes 64..1024 with the vectors in shared
 // memory; -BS for the register-resident layout of BS threads with R =
 // 1024 / BS rows per thread.
-static int launch_any(gko_batch* B, int bs, const double* b, double* x, double tol, int maxit, cudaStream_t st)
+static int launch_any(gko_batch* B, int bs, const double* b, double* x, double tol, int maxit, cudaStream_t st,
+                      bool prepare = false)
 {
+    constexpr int P = GKO_BATCH_SHARED_P, PQ = GKO_BATCH_SHARED_PQ;
+    switch (bs) {
+        case P | 32: return launch_batched<32, 1>(B, b, x, tol, maxit, st, prepare);
+        case P | 64: return launch_batched<64, 1>(B, b, x, tol, maxit, st, prepare);
+        case P | 128: return launch_batched<128, 1>(B, b, x, tol, maxit, st, prepare);
+        case P | 256: return launch_batched<256, 1>(B, b, x, tol, maxit, st, prepare);
+        case PQ | 32: return launch_batched<32, 2>(B, b, x, tol, maxit, st, prepare);
+        case PQ | 64: return launch_batched<64, 2>(B, b, x, tol, maxit, st, prepare);
+        case PQ | 128: return launch_batched<128, 2>(B, b, x, tol, maxit, st, prepare);
+        case PQ | 256: return launch_batched<256, 2>(B, b, x, tol, maxit, st, prepare);
+        case 64: return launch_batched<64, 4>(B, b, x, tol, maxit, st, prepare);
+        case 128: return launch_batched<128, 4>(B, b, x, tol, maxit, st, prepare);
+        case 256: return launch_batched<256, 4>(B, b, x, tol, maxit, st, prepare);
+        case 512: return launch_batched<512, 4>(B, b, x, tol, maxit, st, prepare);
+        case 1024: return launch_batched<1024, 4>(B, b, x, tol, maxit, st, prepare);
+    }
+    if (prepare) return GKO_OK;  // the register layout needs no scratch
     switch (bs) {
         case -128: return launch_batched_reg<128, 8>(B, b, x, tol, maxit, st);
         case -256: return launch_batched_reg<256, 4>(B, b, x, tol, maxit, st);
         case -512: return launch_batched_reg<512, 2>(B, b, x, tol, maxit, st);
         case -1024: return launch_batched_reg<1024, 1>(B, b, x, tol, maxit, st);
-        case 64: return launch_batched<64>(B, b, x, tol, maxit, st);
-        case 128: return launch_batched<128>(B, b, x, tol, maxit, st);
-        case 256: return launch_batched<256>(B, b, x, tol, maxit, st);
-        case 512: return launch_batched<512>(B, b, x, tol, maxit, st);
-        case 1024: return launch_batched<1024>(B, b, x, tol, maxit, st);
     }
-    return fail(GKO_ERR_INVALID_ARG, "block_size must be 0, 64, 128, 256, 512, 1024 or -128, -256, -512, -1024");
+    return fail(GKO_ERR_INVALID_ARG,
+                "block_size must be 0, 64..1024, -128..-1024, or GKO_BATCH_SHARED_P / _PQ | 32..256");
 }
 
 // run [queue reset + kernel] as a captured CUDA graph; the instantiated
@@ -459,6 +566,7 @@ static int run_graph(gko_batch* B, int bs, const double* b, double* x, double to
         cudaGraphExecDestroy(B->graph);
         B->graph = nullptr;
     }
+    GKO_TRY(launch_any(B, bs, b, x, tol, maxit, st, true));
     cudaStream_t cap;
     GKO_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
     cudaGraph_t g = nullptr;
@@ -618,6 +726,7 @@ int gko_batch_destroy(gko_batch* B)
     dev_free(B->status);
     dev_free(B->d_err);
     dev_free(B->perm);
+    dev_free(B->scratch);
     if (B->graph) cudaGraphExecDestroy(B->graph);
     delete B;
     return GKO_OK;
@@ -664,7 +773,10 @@ int gko_batch_autotune(gko_batch* B, const double* b, double* x, double tol, int
     GKO_CUDA(cudaEventCreate(&e1));
     float best_ms = 0.0f;
     int best_bs = 0;
-    const int cands[] = {64, 128, 256, 512, 1024, -128, -256, -512, -1024};
+    constexpr int P = GKO_BATCH_SHARED_P, PQ = GKO_BATCH_SHARED_PQ;
+    const int cands[] = {64,      128,      256,      512,     1024,     -128,     -256,    -512,
+                         -1024,   P | 32,   P | 64,   P | 128, P | 256,  PQ | 32,  PQ | 64, PQ | 128,
+                         PQ | 256};
     for (int bs : cands) {
         if (bs < 0 && B->max_rows > 1024) continue;  // R = 1024 / BS rows per thread must cover the systems
         float tot = 0.0f;

@@ -170,6 +170,8 @@ struct gko_batch {
     int32_t max_rows = 0;
     int best_block = 0;           // autotuned block size (0 = not tuned)
     uint32_t* d_err = nullptr;
+    double* scratch = nullptr;    // split layout: x, r (, A p) of each resident block
+    int64_t scratch_len = 0;      // doubles
     // instantiated graph of the last solve [queue reset + kernel], relaunched
     // while the launch arguments stay the same
     cudaGraphExec_t graph = nullptr;

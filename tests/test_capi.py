@@ -47,6 +47,23 @@ def test_binding_wraps_every_symbol_with_the_same_name(gko):
     assert set(declared_functions()) == set(gko.binding._SIGS)
 
 
+def test_header_macros_match_the_binding(gko):
+    text = open(HEADER).read()
+    macros = dict(re.findall(r"#define\s+(GKO_[A-Z0-9_]+)\s+(0x[0-9A-Fa-f]+|\d+)", text))
+    b = gko.binding
+    assert int(macros["GKO_BATCH_SHARED_P"], 0) == b.BATCH_SHARED_P
+    assert int(macros["GKO_BATCH_SHARED_PQ"], 0) == b.BATCH_SHARED_PQ
+    # the flags sit above every block size
+    assert b.BATCH_SHARED_P > 1024 and b.BATCH_SHARED_P & b.BATCH_SHARED_PQ == 0
+    assert b.batch_layout(b.BATCH_SHARED_P | 128) == "shared_p/128"
+    assert b.batch_layout(b.BATCH_SHARED_PQ | 64) == "shared_pq/64"
+    assert b.batch_layout(-256) == "registers/256" and b.batch_layout(64) == "shared_xrpq/64"
+    for code in (0, 64, 1024, -128, b.BATCH_SHARED_P | 32, b.BATCH_SHARED_PQ | 256):
+        assert b.batch_layout_code(b.batch_layout(code)) == code
+    with pytest.raises(ValueError):
+        b.batch_layout_code("shared_q/64")
+
+
 def test_status_strings_and_version(gko):
     assert gko.binding.status_name(0) == "GKO_OK"
     assert gko.binding.status_name(7) == "GKO_ERR_BREAKDOWN"

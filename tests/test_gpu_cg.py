@@ -375,8 +375,11 @@ def test_batched_cg_matches_oracle(gko, dev, orc):
     xo, st_o, it_o, res_o = orc.cg_batched(B, rhs, tol=1e-10)
     assert np.all(st_o == 0)
     G = gko.Batch(B)
-    # shared-memory layout (64..1024) and register-resident layout (-128..-1024)
-    for bs in (0, 64, 128, 256, 512, 1024, -128, -256, -512, -1024):
+    # shared-memory layout (64..1024), register-resident layout (-128..-1024)
+    # and the split layouts (p, or p and A p, in shared memory)
+    P, PQ = gko.binding.BATCH_SHARED_P, gko.binding.BATCH_SHARED_PQ
+    split = tuple(f | b for f in (P, PQ) for b in (32, 64, 128, 256))
+    for bs in (0, 64, 128, 256, 512, 1024, -128, -256, -512, -1024) + split:
         x = torch.zeros(len(rhs), dtype=torch.float64, device=dev)
         s, infos = G.cg(_t(rhs, dev), x, tol=1e-10, maxit=1000, block_size=bs)
         assert s == 0, bs
@@ -424,7 +427,9 @@ def test_batched_autotune_and_maxit(gko, dev, orc):
     G = gko.Batch(B)
     x = torch.zeros(len(B["rhs"]), dtype=torch.float64, device=dev)
     best = G.autotune(_t(B["rhs"], dev), x)
-    assert best in (64, 128, 256, 512, 1024, -128, -256, -512, -1024)
+    P, PQ = gko.binding.BATCH_SHARED_P, gko.binding.BATCH_SHARED_PQ
+    split = tuple(f | b for f in (P, PQ) for b in (32, 64, 128, 256))
+    assert best in (64, 128, 256, 512, 1024, -128, -256, -512, -1024) + split
     assert float(x.abs().max()) == 0.0  # autotune restores x
     s, infos = G.cg(_t(B["rhs"], dev), x, maxit=2)
     assert s == gko.binding.ERR_NOT_CONVERGED
