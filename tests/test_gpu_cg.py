@@ -410,6 +410,67 @@ def test_batched_cg_dense_cholesky_subset(gko, dev, orc):
         assert np.linalg.norm(xg[r0:r1] - xc) <= 1e-10 * np.linalg.norm(xc)
 
 
+def _concat_batch(systems, rhs_seed):
+    """One batch (the batched_spd layout) from a list of square CSR systems."""
+    ro, rps, cis, vs, base = [0], [], [], [], 0
+    for A in systems:
+        rps.append(np.asarray(A["row_ptr"][:-1], np.int64) + base)
+        cis.append(np.asarray(A["col_idx"], np.int32))
+        vs.append(np.asarray(A["val"], np.float64))
+        base += int(A["row_ptr"][-1])
+        ro.append(ro[-1] + A["n_rows"])
+    rp = np.concatenate(rps + [np.array([base], np.int64)]).astype(np.int32)
+    ro = np.array(ro, np.int64)
+    return dict(row_off=ro, row_ptr=rp, col_idx=np.concatenate(cis), val=np.concatenate(vs),
+                sizes=np.diff(ro), rhs=syn.vector(int(ro[-1]), rhs_seed))
+
+
+def _tiny(rows):
+    rows = np.asarray(rows, np.float64)
+    n = rows.shape[0]
+    nz = [(i, j) for i in range(n) for j in range(n) if rows[i, j] != 0.0]
+    rp = np.zeros(n + 1, np.int32)
+    for i, _ in nz:
+        rp[i + 1] += 1
+    return dict(n_rows=n, n_cols=n, row_ptr=np.cumsum(rp).astype(np.int32),
+                col_idx=np.array([j for _, j in nz], np.int32), val=np.array([rows[i, j] for i, j in nz]))
+
+
+def test_batched_extreme_sizes_every_layout(gko, dev, orc):
+    """Systems of 4,096 rows (the largest a batch takes), 2,025, 49, 2 and 1
+    rows, and one with b = 0, in every layout that accepts them, against the
+    oracle; the register layouts refuse systems above 1,024 rows."""
+    import torch
+    systems = [syn.laplace2d(64), _tiny([[2.0]]), _tiny([[2.0, -1.0], [-1.0, 2.0]]), syn.laplace2d(7),
+               _tiny([[3.0, 1.0], [1.0, 3.0]]), syn.laplace2d(45)]
+    B = _concat_batch(systems, 91)
+    zero = 4  # system with a zero right-hand side
+    r0z, r1z = B["row_off"][zero], B["row_off"][zero + 1]
+    B["rhs"][r0z:r1z] = 0.0
+    xo, st_o, it_o, _ = orc.cg_batched(B, B["rhs"], tol=1e-10, maxit=2000)
+    assert np.all(st_o == 0) and B["row_off"][1] == 4096
+    G = gko.Batch(B)
+    x = torch.zeros(len(B["rhs"]), dtype=torch.float64, device=dev)
+    with pytest.raises(gko.GkoError) as e:
+        G.cg(_t(B["rhs"], dev), x, tol=1e-10, maxit=2000, block_size=-128)
+    assert e.value.status == gko.binding.ERR_INVALID_ARG
+    P, PQ = gko.binding.BATCH_SHARED_P, gko.binding.BATCH_SHARED_PQ
+    for bs in (64, 128, 256, 512, 1024) + tuple(f | b for f in (P, PQ) for b in (32, 64, 128, 256)):
+        x = torch.zeros(len(B["rhs"]), dtype=torch.float64, device=dev)
+        x[r0z:r1z] = 0.5  # b = 0 returns x = 0 whatever the initial guess
+        s, infos = G.cg(_t(B["rhs"], dev), x, tol=1e-10, maxit=2000, block_size=bs)
+        assert s == 0, gko.binding.batch_layout(bs)
+        xg = x.cpu().numpy()
+        for k in range(len(systems)):
+            r0, r1 = B["row_off"][k], B["row_off"][k + 1]
+            if k == zero:
+                assert infos[k].iterations == 0 and infos[k].rel_residual == 0.0 and np.all(xg[r0:r1] == 0.0)
+                continue
+            assert infos[k].rel_residual <= 1e-10, (bs, k)
+            assert abs(infos[k].iterations - it_o[k]) <= max(5, 0.02 * it_o[k]), (bs, k, infos[k].iterations, it_o[k])
+            assert np.linalg.norm(xg[r0:r1] - xo[r0:r1]) <= 1e-8 * np.linalg.norm(xo[r0:r1]), (bs, k)
+
+
 def test_batched_rejects_column_outside_system(gko, dev):
     B = syn.batched_spd(3, seed=72, n_min=10, n_max=20)
     bad = dict(B)
