@@ -490,7 +490,8 @@ int gko_batch_destroy(gko_batch* B);
  * 128 or 256): bs threads with only p (or p and A p) in shared memory and
  * the rest of the system's vectors in a device scratch the batch allocates
  * and keeps (4 - 1 or 4 - 2 vectors of max_rows doubles per resident
- * block), so that more systems share an SM; 0 = the autotuned choice.
+ * block), so that more systems share an SM; 0 = the autotuned choice, or
+ * GKO_BATCH_SHARED_P | 128 before gko_batch_autotune has run.
  * b, x device vectors of row_off[count]
  * entries (x: initial guess in, solution out).  infos: host array of count
  * entries or NULL.  Returns the worst status.  Synchronises the stream. */
