@@ -802,11 +802,52 @@ def test_mixed_cg_jacobi_inner(orc, prec):
     assert r1[2] == r2[2] and abs(r1[3] - r2[3]) <= 2 and r2[4] <= 1e-10
 
 
+def _batch_dense(B, k):
+    r0, r1 = int(B["row_off"][k]), int(B["row_off"][k + 1])
+    D = np.zeros((r1 - r0, r1 - r0))
+    for i in range(r0, r1):
+        for e in range(B["row_ptr"][i], B["row_ptr"][i + 1]):
+            D[i - r0, B["col_idx"][e]] += B["val"][e]
+    return D, r0, r1
+
+
 def test_batched_cg(orc):
+    """Every system's solution against numpy's dense solve (the systems are
+    strictly diagonally dominant, so cond(A) is small and a relative residual
+    of 1e-10 bounds the error near 1e-10 too), and the reported residual
+    recomputed from x."""
     B = syn.batched_spd(12, seed=8)
     x, st, it, res = orc.cg_batched(B, B["rhs"], tol=1e-10)
     assert np.all(st == 0) and np.all(res <= 1e-10)
     assert np.all(it > 0)
+    for k in range(12):
+        D, r0, r1 = _batch_dense(B, k)
+        b = B["rhs"][r0:r1]
+        xs = np.linalg.solve(D, b)
+        assert np.linalg.norm(x[r0:r1] - xs) <= 1e-8 * np.linalg.norm(xs)
+        rr = np.linalg.norm(b - D @ x[r0:r1]) / np.linalg.norm(b)
+        assert abs(rr - res[k]) <= 1e-13
+
+
+def test_batched_cg_finite_termination_and_special_systems(orc):
+    """CG ends after at most m steps on a matrix with m distinct eigenvalues
+    (diagonal systems with 1, 2 and 3 distinct entries), takes one step on a
+    1x1 system, and returns x = 0 after no step when b = 0."""
+    diags = [np.full(7, 3.0), np.array([2.0, 5.0, 2.0, 5.0, 5.0]), np.array([1.0, 4.0, 9.0, 1.0, 4.0, 9.0]),
+             np.array([2.5]), np.array([3.0, 1.0, 2.0])]
+    ro = np.concatenate([[0], np.cumsum([len(d) for d in diags])]).astype(np.int64)
+    rp = np.arange(ro[-1] + 1, dtype=np.int32)
+    ci = np.concatenate([np.arange(len(d)) for d in diags]).astype(np.int32)
+    B = dict(row_off=ro, row_ptr=rp, col_idx=ci, val=np.concatenate(diags), sizes=np.diff(ro))
+    b = syn.vector(int(ro[-1]), 17)
+    b[ro[4]:ro[5]] = 0.0  # last system: b = 0
+    x, st, it, res = orc.cg_batched(B, b, tol=1e-12)
+    assert np.all(st == 0)
+    assert list(it) == [1, 2, 3, 1, 0]
+    for k in range(4):
+        r0, r1 = ro[k], ro[k + 1]
+        assert np.allclose(x[r0:r1], b[r0:r1] / diags[k], rtol=1e-12, atol=0)
+    assert np.all(x[ro[4]:ro[5]] == 0.0) and res[4] == 0.0
 
 
 # --------------------------------------------------------- mixed precision
